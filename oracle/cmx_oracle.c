@@ -1,0 +1,484 @@
+/*
+ * FP64 CPU oracle for the coupled LLG + N-cavity-mode system, integrated with an adaptive
+ * Dormand-Prince 5(4) scheme.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check and the CPU-baseline leg of the
+ * benchmark may load this library.  It shares no code, header or constant table with the CUDA
+ * path: everything below is written out again from the paper and from the published
+ * Dormand-Prince tableau.
+ *
+ * What it computes (paper = "Multimode cavity magnonics in mumax+", arXiv 2603.03706):
+ *   cavity ODEs      da_n/dt = (-i w_n - kappa_n) a_n + i g~_n <m^->_n          Eq. (12), (19)
+ *   overlap          <m^->_n = (1/N_c) sum_{r in mask} u_n(r) (m_x - i m_y)(r)  Eq. (2), (18)
+ *   feedback field   B_rf,x(r) = sum_n u_n(r) (2/gamma) Re[g~_n a_n]            Eq. (5), (13)
+ *   magnetisation    LLG with Gilbert damping (Sec. II A), Landau-Lifshitz form:
+ *                    dm/dt = -gamma/(1+alpha^2) [ m x B + alpha m x (m x B) ]
+ *   effective field  B = exchange (6 neighbours, free surface) + uniaxial anisotropy + Zeeman
+ *                    + diagonal demag + B_rf (+ inter-sublattice exchange -B_E m_other, AFM,
+ *                    Sec. II G); for two sublattices the cavity couples to (m1 + m2)/2.
+ *   time stepping    Dormand-Prince 5(4), FSAL; the paper only says "adaptive RK45" (Sec. III A).
+ *
+ * Readings where the paper is silent (each also listed in the design notes):
+ *   - coupling sign +i g~ (Eq. (1)); complex g~ = g - i g_d feeds back through Re[g~ a]
+ *   - the overlap is an average (1/N_c), Eq. (18)
+ *   - exchange neighbours outside the mask or the box contribute nothing (free surface)
+ *   - demag of a two-sublattice magnet acts on the total moment Ms (m1 + m2)
+ *   - error norm: err = max( max|e_m| / rtol , max_n |e_a,n| / (rtol max(a_ref, |a|max)) ),
+ *     accept iff err <= 1, dt *= clamp(0.9 err^(-1/5), 0.2, 5), no growth right after a reject
+ *   - on accept m is renormalised per cell; the FSAL slope k7 is the slope at the
+ *     un-normalised 5th-order point.
+ *
+ * Layout: dense box, x fastest, cell = x + nx*(y + ny*z).  m[(s*3 + c)*nbox + cell] for
+ * sublattice s and component c.  Cavity amplitudes a[2n] = Re a_n, a[2n+1] = Im a_n.
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_OK 0
+#define ORC_EINVAL 1
+#define ORC_ENOMEM 2
+#define ORC_ENAN 4
+#define ORC_ESTEPFAIL 5
+
+static const double ORC_MU0 = 4.0e-7 * 3.14159265358979323846;
+
+typedef struct {
+    int nx, ny, nz, nsub, nmodes;
+    double cx, cy, cz;
+    const unsigned char *mask;
+    double Ms, Aex, alpha, gamma, Ku, ku[3], B0[3], Nd[3], BE;
+    const double *u; /* nmodes * nbox, or NULL: every profile is 1 */
+    const double *omega, *kappa, *g_re, *g_im;
+} orc_problem;
+
+typedef struct {
+    double rtol, a_ref, dt_min, dt_max;
+} orc_solver;
+
+/* Per-attempt record written by the drivers below. */
+typedef struct {
+    int cap, n;
+    double *t;    /* time at the end of the attempt (accepted) or at its start (rejected) */
+    double *dt;
+    double *err;
+    int *accepted;
+    double *a;    /* cap * 2N: cavity amplitudes after the attempt (only for accepted) */
+    double *mm;   /* cap * 2N: <m^->_n at the stage-7 point y_{n+1} */
+} orc_log;
+
+typedef struct {
+    long nbox, nvar;     /* nvar = nsub*3*nbox */
+    int nm;              /* number of modes */
+    double *m, *a;       /* y_n */
+    double *km[7], *ka[7];
+    double *ym, *ya;     /* stage point */
+    double mm7[128];
+    int k1_valid, last_rejected;
+    double t, dt;
+    long n_attempts, n_accepted;
+} orc_state;
+
+/* ------------------------------------------------------------------------------------------- */
+/* Dormand & Prince (1980) 5(4) tableau, as published (also Hairer, Norsett & Wanner I, Table   */
+/* 5.2).  a[i][j] is the coupling of stage i+1 to slope j+1; b5 the 5th-order weights (equal to */
+/* the 7th row: FSAL), b4 the embedded 4th-order weights.                                       */
+/* ------------------------------------------------------------------------------------------- */
+static const double DP_A[7][6] = {
+    {0, 0, 0, 0, 0, 0},
+    {1.0 / 5, 0, 0, 0, 0, 0},
+    {3.0 / 40, 9.0 / 40, 0, 0, 0, 0},
+    {44.0 / 45, -56.0 / 15, 32.0 / 9, 0, 0, 0},
+    {19372.0 / 6561, -25360.0 / 2187, 64448.0 / 6561, -212.0 / 729, 0, 0},
+    {9017.0 / 3168, -355.0 / 33, 46732.0 / 5247, 49.0 / 176, -5103.0 / 18656, 0},
+    {35.0 / 384, 0, 500.0 / 1113, 125.0 / 192, -2187.0 / 6784, 11.0 / 84},
+};
+static const double DP_B5[7] = {35.0 / 384, 0, 500.0 / 1113, 125.0 / 192, -2187.0 / 6784,
+                                11.0 / 84, 0};
+static const double DP_B4[7] = {5179.0 / 57600, 0, 7571.0 / 16695, 393.0 / 640,
+                                -92097.0 / 339200, 187.0 / 2100, 1.0 / 40};
+
+/* Exported so the tests can check the order conditions of the oracle's own tableau. */
+void orc_tableau(double *a /*7*6*/, double *b5 /*7*/, double *b4 /*7*/)
+{
+    memcpy(a, DP_A, sizeof DP_A);
+    memcpy(b5, DP_B5, sizeof DP_B5);
+    memcpy(b4, DP_B4, sizeof DP_B4);
+}
+
+static int in_mask(const orc_problem *P, int x, int y, int z)
+{
+    if (x < 0 || y < 0 || z < 0 || x >= P->nx || y >= P->ny || z >= P->nz) return 0;
+    return P->mask[x + (long)P->nx * (y + (long)P->ny * z)] != 0;
+}
+
+static long count_cells(const orc_problem *P)
+{
+    long nbox = (long)P->nx * P->ny * P->nz, n = 0;
+    for (long i = 0; i < nbox; i++) n += P->mask[i] != 0;
+    return n;
+}
+
+static double profile(const orc_problem *P, int n, long cell)
+{
+    return P->u ? P->u[(long)n * P->nx * P->ny * P->nz + cell] : 1.0;
+}
+
+/*
+ * Overlap <m^->_n = (1/N_c) sum_mask u_n (m_x - i m_y), Eq. (18) with Eq. (2).  For two
+ * sublattices the cavity sees the net moment (m1 + m2)/2 (Sec. II G).
+ */
+void orc_overlap(const orc_problem *P, const double *m, double *mm)
+{
+    long nbox = (long)P->nx * P->ny * P->nz;
+    double inv_nc = 1.0 / (double)count_cells(P);
+    for (int n = 0; n < P->nmodes; n++) {
+        double re = 0.0, im = 0.0;
+        for (long c = 0; c < nbox; c++) {
+            if (!P->mask[c]) continue;
+            double mx = 0.0, my = 0.0;
+            for (int s = 0; s < P->nsub; s++) {
+                mx += m[(s * 3 + 0) * nbox + c];
+                my += m[(s * 3 + 1) * nbox + c];
+            }
+            mx /= P->nsub;
+            my /= P->nsub;
+            double un = profile(P, n, c);
+            re += un * mx;
+            im -= un * my;
+        }
+        mm[2 * n] = re * inv_nc;
+        mm[2 * n + 1] = im * inv_nc;
+    }
+}
+
+/*
+ * Right-hand side f(m, a) of the coupled system.  Writes dm (same layout as m; zero outside the
+ * mask), da (2N) and the overlaps mm (2N).
+ */
+int orc_rhs(const orc_problem *P, const double *m, const double *a, double *dm, double *da,
+            double *mm)
+{
+    const int nx = P->nx, ny = P->ny, nz = P->nz, ns = P->nsub, N = P->nmodes;
+    const long nbox = (long)nx * ny * nz;
+    const double pre = -P->gamma / (1.0 + P->alpha * P->alpha);
+    const double exch = 2.0 * P->Aex / P->Ms;           /* T m^2 */
+    const double wx = exch / (P->cx * P->cx), wy = exch / (P->cy * P->cy),
+                 wz = exch / (P->cz * P->cz);
+    const double anis = 2.0 * P->Ku / P->Ms;            /* T */
+    const double dmg = ORC_MU0 * P->Ms;                 /* T */
+    /* Feedback amplitude of each mode: B_rf,x = sum_n u_n (2/gamma) Re[g~_n a_n]. */
+    double hrf[64];
+    if (N > 64 || ns < 1 || ns > 2) return ORC_EINVAL;
+    for (int n = 0; n < N; n++) {
+        double re_ga = P->g_re[n] * a[2 * n] - P->g_im[n] * a[2 * n + 1];
+        hrf[n] = 2.0 / P->gamma * re_ga;
+    }
+
+#pragma omp parallel for schedule(static)
+    for (int z = 0; z < nz; z++) {
+        for (int y = 0; y < ny; y++) {
+            for (int x = 0; x < nx; x++) {
+                long c = x + (long)nx * (y + (long)ny * z);
+                if (!P->mask[c]) {
+                    for (int k = 0; k < 3 * ns; k++) dm[k * nbox + c] = 0.0;
+                    continue;
+                }
+                double brf = 0.0;
+                for (int n = 0; n < N; n++) brf += profile(P, n, c) * hrf[n];
+                double mtot[3] = {0, 0, 0};
+                for (int s = 0; s < ns; s++)
+                    for (int k = 0; k < 3; k++) mtot[k] += m[(s * 3 + k) * nbox + c];
+                for (int s = 0; s < ns; s++) {
+                    const double *ms = m + (long)s * 3 * nbox;
+                    double mi[3] = {ms[c], ms[nbox + c], ms[2 * nbox + c]};
+                    double B[3] = {0, 0, 0};
+                    /* exchange: sum over in-mask face neighbours of (m_j - m_i) / c_d^2 */
+                    const int dx[6] = {-1, 1, 0, 0, 0, 0}, dy[6] = {0, 0, -1, 1, 0, 0},
+                              dz[6] = {0, 0, 0, 0, -1, 1};
+                    for (int q = 0; q < 6; q++) {
+                        int xx = x + dx[q], yy = y + dy[q], zz = z + dz[q];
+                        if (!in_mask(P, xx, yy, zz)) continue;
+                        long j = xx + (long)nx * (yy + (long)ny * zz);
+                        double w = dx[q] ? wx : (dy[q] ? wy : wz);
+                        for (int k = 0; k < 3; k++) B[k] += w * (ms[k * nbox + j] - mi[k]);
+                    }
+                    /* uniaxial anisotropy (2 K_u / M_s)(m . k) k */
+                    double mk = mi[0] * P->ku[0] + mi[1] * P->ku[1] + mi[2] * P->ku[2];
+                    for (int k = 0; k < 3; k++) B[k] += anis * mk * P->ku[k];
+                    /* Zeeman and diagonal demag of the total moment */
+                    for (int k = 0; k < 3; k++) B[k] += P->B0[k] - dmg * P->Nd[k] * mtot[k];
+                    /* inter-sublattice exchange field */
+                    if (ns == 2) {
+                        const double *mo = m + (long)(1 - s) * 3 * nbox;
+                        for (int k = 0; k < 3; k++) B[k] -= P->BE * mo[k * nbox + c];
+                    }
+                    /* cavity feedback along x */
+                    B[0] += brf;
+                    /* Landau-Lifshitz-Gilbert torque */
+                    double t1[3] = {mi[1] * B[2] - mi[2] * B[1], mi[2] * B[0] - mi[0] * B[2],
+                                    mi[0] * B[1] - mi[1] * B[0]};
+                    double t2[3] = {mi[1] * t1[2] - mi[2] * t1[1], mi[2] * t1[0] - mi[0] * t1[2],
+                                    mi[0] * t1[1] - mi[1] * t1[0]};
+                    for (int k = 0; k < 3; k++)
+                        dm[(s * 3 + k) * nbox + c] = pre * (t1[k] + P->alpha * t2[k]);
+                }
+            }
+        }
+    }
+
+    orc_overlap(P, m, mm);
+    for (int n = 0; n < N; n++) {
+        double ar = a[2 * n], ai = a[2 * n + 1];
+        /* (-i w - kappa) a */
+        double r = -P->kappa[n] * ar + P->omega[n] * ai;
+        double i = -P->kappa[n] * ai - P->omega[n] * ar;
+        /* + i g~ <m^-> = i (g_re + i g_im)(mr + i mi) */
+        double gr = P->g_re[n], gi = P->g_im[n], mr = mm[2 * n], mi = mm[2 * n + 1];
+        double pr = gr * mr - gi * mi, pi = gr * mi + gi * mr; /* g~ <m^-> */
+        r += -pi;
+        i += pr;
+        da[2 * n] = r;
+        da[2 * n + 1] = i;
+    }
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------------------------- */
+/* integrator state                                                                            */
+/* ------------------------------------------------------------------------------------------- */
+void orc_state_free(orc_state *S)
+{
+    if (!S) return;
+    free(S->m);
+    free(S->a);
+    free(S->ym);
+    free(S->ya);
+    for (int j = 0; j < 7; j++) {
+        free(S->km[j]);
+        free(S->ka[j]);
+    }
+    free(S);
+}
+
+orc_state *orc_state_new(const orc_problem *P)
+{
+    orc_state *S = calloc(1, sizeof *S);
+    if (!S) return NULL;
+    S->nbox = (long)P->nx * P->ny * P->nz;
+    S->nvar = (long)P->nsub * 3 * S->nbox;
+    S->nm = P->nmodes;
+    long na = 2 * (long)(P->nmodes > 0 ? P->nmodes : 1);
+    S->m = calloc(S->nvar, sizeof(double));
+    S->ym = calloc(S->nvar, sizeof(double));
+    S->a = calloc(na, sizeof(double));
+    S->ya = calloc(na, sizeof(double));
+    int ok = S->m && S->ym && S->a && S->ya;
+    for (int j = 0; j < 7; j++) {
+        S->km[j] = calloc(S->nvar, sizeof(double));
+        S->ka[j] = calloc(na, sizeof(double));
+        ok = ok && S->km[j] && S->ka[j];
+    }
+    if (!ok) {
+        orc_state_free(S);
+        return NULL;
+    }
+    return S;
+}
+
+void orc_state_set(orc_state *S, const double *m, const double *a, double t, double dt)
+{
+    memcpy(S->m, m, S->nvar * sizeof(double));
+    memcpy(S->a, a, 2 * S->nm * sizeof(double));
+    S->t = t;
+    S->dt = dt;
+    S->k1_valid = 0;
+    S->last_rejected = 0;
+    S->n_attempts = S->n_accepted = 0;
+}
+
+void orc_state_get(const orc_state *S, double *m, double *a, double *t, double *dt,
+                   long *counts /*2: attempts, accepted*/)
+{
+    if (m) memcpy(m, S->m, S->nvar * sizeof(double));
+    if (a) memcpy(a, S->a, 2 * S->nm * sizeof(double));
+    if (t) *t = S->t;
+    if (dt) *dt = S->dt;
+    if (counts) {
+        counts[0] = S->n_attempts;
+        counts[1] = S->n_accepted;
+    }
+}
+
+/*
+ * One Dormand-Prince attempt of size h from (S->m, S->a).  On return the 5th-order point y7 is
+ * in (S->ym, S->ya), its slope in km[6]/ka[6] and the scaled error in *err.
+ */
+static int dp_attempt(const orc_problem *P, orc_state *S, const orc_solver *sv, double h,
+                      double *err)
+{
+    const long nv = S->nvar, nbox = S->nbox;
+    const int N = S->nm;
+    double mm[128];
+    if (!S->k1_valid) {
+        int rc = orc_rhs(P, S->m, S->a, S->km[0], S->ka[0], mm);
+        if (rc) return rc;
+        S->k1_valid = 1;
+    }
+    for (int s = 1; s < 7; s++) {
+        /* stage point y_s = y_n + h sum_{j<s} a_sj k_j */
+        for (long i = 0; i < nv; i++) {
+            double acc = S->m[i];
+            for (int j = 0; j < s; j++) acc += h * DP_A[s][j] * S->km[j][i];
+            S->ym[i] = acc;
+        }
+        for (int i = 0; i < 2 * N; i++) {
+            double acc = S->a[i];
+            for (int j = 0; j < s; j++) acc += h * DP_A[s][j] * S->ka[j][i];
+            S->ya[i] = acc;
+        }
+        int rc = orc_rhs(P, S->ym, S->ya, S->km[s], S->ka[s], mm);
+        if (rc) return rc;
+    }
+    memcpy(S->mm7, mm, 2 * N * sizeof(double));
+
+    /* error estimate e = h sum_j (b5_j - b4_j) k_j, taken from the slopes directly */
+    double em = 0.0;
+    for (int s = 0; s < P->nsub; s++)
+        for (int k = 0; k < 3; k++)
+            for (long c = 0; c < nbox; c++) {
+                if (!P->mask[c]) continue;
+                long i = (s * 3 + k) * nbox + c;
+                double e = 0.0;
+                for (int j = 0; j < 7; j++) e += (DP_B5[j] - DP_B4[j]) * S->km[j][i];
+                e = fabs(h * e);
+                if (e > em || isnan(e)) em = e;
+            }
+    double ea = 0.0, amax = 0.0;
+    for (int n = 0; n < N; n++) {
+        double er = 0.0, ei = 0.0;
+        for (int j = 0; j < 7; j++) {
+            er += (DP_B5[j] - DP_B4[j]) * S->ka[j][2 * n];
+            ei += (DP_B5[j] - DP_B4[j]) * S->ka[j][2 * n + 1];
+        }
+        double e = fabs(h) * sqrt(er * er + ei * ei);
+        if (e > ea || isnan(e)) ea = e;
+        double a0 = hypot(S->a[2 * n], S->a[2 * n + 1]);
+        double a1 = hypot(S->ya[2 * n], S->ya[2 * n + 1]);
+        if (a0 > amax) amax = a0;
+        if (a1 > amax) amax = a1;
+    }
+    double scale_a = sv->rtol * (amax > sv->a_ref ? amax : sv->a_ref);
+    double e1 = em / sv->rtol, e2 = ea / scale_a;
+    *err = (e1 > e2 || isnan(e1)) ? e1 : e2;
+    if (isnan(*err)) return ORC_ENAN;
+    return ORC_OK;
+}
+
+/* Accept the attempt held in S: y_{n+1} = y7 with m renormalised per cell; FSAL k1 <- k7. */
+static void dp_accept(const orc_problem *P, orc_state *S, double h)
+{
+    const long nbox = S->nbox;
+    for (int s = 0; s < P->nsub; s++)
+        for (long c = 0; c < nbox; c++) {
+            double *x = S->ym + (s * 3 + 0) * nbox + c, *y = x + nbox, *z = y + nbox;
+            if (!P->mask[c]) {
+                *x = *y = *z = 0.0;
+                continue;
+            }
+            double r = sqrt(*x * *x + *y * *y + *z * *z);
+            *x /= r;
+            *y /= r;
+            *z /= r;
+        }
+    double *tm = S->m;
+    S->m = S->ym;
+    S->ym = tm;
+    double *ta = S->a;
+    S->a = S->ya;
+    S->ya = ta;
+    double *k = S->km[0];
+    S->km[0] = S->km[6];
+    S->km[6] = k;
+    k = S->ka[0];
+    S->ka[0] = S->ka[6];
+    S->ka[6] = k;
+    S->t += h;
+    S->n_accepted++;
+}
+
+static void log_attempt(orc_log *L, const orc_state *S, double t, double h, double err, int acc)
+{
+    if (!L || L->n >= L->cap) {
+        if (L) L->n++;
+        return;
+    }
+    int i = L->n++;
+    L->t[i] = t;
+    L->dt[i] = h;
+    L->err[i] = err;
+    L->accepted[i] = acc;
+    for (int q = 0; q < 2 * S->nm; q++) {
+        if (L->a) L->a[(long)i * 2 * S->nm + q] = S->a[q];
+        if (L->mm) L->mm[(long)i * 2 * S->nm + q] = S->mm7[q];
+    }
+}
+
+/*
+ * Adaptive integration from S->t to T.  Step-size rule: err <= 1 accepts;
+ * factor = clamp(0.9 err^(-1/5), 0.2, 5) (5 when err = 0), capped at 1 right after a rejection;
+ * the next step is min(h * factor, dt_max); an attempt that would pass T is shortened to land on
+ * T exactly.  Stops after max_attempts attempts.
+ */
+int orc_run(const orc_problem *P, orc_state *S, const orc_solver *sv, double T,
+            long max_attempts, orc_log *L)
+{
+    long n = 0;
+    while (S->t < T && n < max_attempts) {
+        double h = S->dt;
+        if (h > sv->dt_max) h = sv->dt_max;
+        int last = 0;
+        if (S->t + h >= T) {
+            h = T - S->t;
+            last = 1;
+        }
+        double err;
+        int rc = dp_attempt(P, S, sv, h, &err);
+        S->n_attempts++;
+        n++;
+        if (rc) return rc;
+        double fac = (err > 0.0) ? 0.9 * pow(err, -0.2) : 5.0;
+        if (fac > 5.0) fac = 5.0;
+        if (fac < 0.2) fac = 0.2;
+        if (err <= 1.0) {
+            if (S->last_rejected && fac > 1.0) fac = 1.0;
+            dp_accept(P, S, h);
+            if (last) S->t = T;
+            log_attempt(L, S, S->t, h, err, 1);
+            S->last_rejected = 0;
+            double hn = h * fac;
+            S->dt = hn > sv->dt_max ? sv->dt_max : hn;
+        } else {
+            log_attempt(L, S, S->t, h, err, 0);
+            S->last_rejected = 1;
+            S->dt = h * fac;
+            if (S->dt < sv->dt_min) return ORC_ESTEPFAIL;
+        }
+    }
+    return ORC_OK;
+}
+
+/* Replay: take exactly the given step sizes, every step accepted (for parity checks). */
+int orc_replay(const orc_problem *P, orc_state *S, const orc_solver *sv, const double *dts,
+               long n, orc_log *L)
+{
+    for (long i = 0; i < n; i++) {
+        double err;
+        int rc = dp_attempt(P, S, sv, dts[i], &err);
+        S->n_attempts++;
+        if (rc) return rc;
+        dp_accept(P, S, dts[i]);
+        log_attempt(L, S, S->t, dts[i], err, 1);
+    }
+    return ORC_OK;
+}
