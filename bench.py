@@ -1,0 +1,357 @@
+"""Benchmark of the device-resident LLG + N-cavity Dormand-Prince integrator.
+
+One benchmark step = one persistent launch of A adaptive Dormand-Prince attempts (6 stage
+passes each) over the whole problem.  `value` is cell-stage updates per second (magnetic cells
+x right-hand-side evaluations) summed over ranks, device-timed with CUDA events on the stream
+the integrator runs on, L2 flushed between timed steps.  `e2e` times the same work through the
+public API from pinned host buffers: set_state (H2D of m, a), the launch, and get_a/get_m (D2H)
+every step.  `roofline` relates the algorithmic bytes of one launch to the measured HBM copy
+bandwidth; `cpu_baseline` times the FP64 oracle on a bounded sample of the same workload.
+
+--impl reference times the FP64 CPU oracle itself (the only other implementation there is) on
+the same workload and metric.  Multi-GPU runs (torchrun) are independent replicas: the
+single-problem path has no data exchange between GPUs.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("cell-stage updates/s and % of HBM peak; batched sweep sims/s; "
+          "adjoint/forward time ratio")
+UNIT = "cell-stage updates/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="cmx", choices=["cmx", "reference"])
+    ap.add_argument("--workload", default="multimode_sphere",
+                    choices=["multimode_sphere", "afm_film", "full_box", "single_sphere"])
+    ap.add_argument("--attempts", type=int, default=0, help="DP attempts per launch (0: auto)")
+    ap.add_argument("--box", default="256,256,128", help="full_box grid nx,ny,nz")
+    ap.add_argument("--tiling", default="", help="bx,by,bz override")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    return ap.parse_args()
+
+
+def make_workload(name, box):
+    from paper_2603_03706_b300 import workloads as W
+    if name == "multimode_sphere":
+        return W.multimode_sphere()
+    if name == "afm_film":
+        return W.afm_film()
+    if name == "single_sphere":
+        return W.single_sphere()
+    nx, ny, nz = (int(v) for v in box.split(","))
+    p = W.multimode_sphere(nx=nx, ny=ny, nz=nz)
+    p = p.replace(mask=W.full_mask(nx, ny, nz), name=f"full_box_{nx}x{ny}x{nz}")
+    return p.replace(dt_max=W.stable_dt_max(p))
+
+
+def bytes_per_cell_attempt(p):
+    """Algorithmic DRAM bytes per magnetic cell and Dormand-Prince attempt (FP32 SoA, FSAL):
+    stage s = 2..6 reads m_n and the slopes with nonzero coupling and writes k_s; stage 7 reads
+    m_n, k1, k3..k6 (a_72 = 0) and writes k7 and the new m.  Per sublattice 3 floats per vector:
+    36 + 48 + 60 + 72 + 84 + 96 = 396 B; profiles add 4 B per mode and stage when present."""
+    per_sub = 12 * (3 + 4 + 5 + 6 + 7 + 8)
+    prof = 6 * 4 * p.nmodes if p.u is not None else 0
+    return p.nsub * per_sub + prof
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2603_03706_b300", "csrc")
+    for fn in sorted(os.listdir(d)):
+        if fn.endswith((".cu", ".cuh", ".h")):
+            h.update(open(os.path.join(d, fn), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(workload):
+    """DRAM bytes per launch from a committed ncu capture, if it was taken on the current kernel
+    source (profiles/traffic.json: workload -> {bytes_per_launch, source_hash, ...})."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        rec = json.load(open(path)).get(workload)
+    except (OSError, ValueError):
+        return None
+    if not rec or rec.get("source_hash") != kernel_source_hash():
+        return None
+    return rec.get("bytes_per_launch_at_bench_attempts")
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while the timed region runs."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in getattr(self, "lines", []):
+            f = [v.strip() for v in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        load = [v for v in sm if mx and v > 0.3 * mx] or sm
+        return {"sm_mhz": statistics.median(load), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup(n):
+    import torch
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    elif torch.cuda.is_available():
+        torch.cuda.set_device(0)
+    return rank, world, local
+
+
+def barrier_and_max(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.barrier()
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def cpu_baseline(p, seconds):
+    """FP64 oracle, adaptive, on all host cores, on a bounded number of attempts of the same
+    workload; cell-stage updates per second."""
+    from oracle import oracle as O
+    cores = os.cpu_count() or 1
+    os.environ.setdefault("OMP_NUM_THREADS", str(cores))
+    op = O.OracleProblem(p)
+    it = O.Integrator(op)
+    t0 = time.perf_counter()
+    it.run(p.T, max_attempts=1)               # first attempt incl. the initial slope
+    first = time.perf_counter() - t0
+    per = max(first, 1e-4)
+    n = max(1, int(seconds / per))
+    s0 = it.state()
+    t0 = time.perf_counter()
+    it.run(p.T, max_attempts=n)
+    dt = time.perf_counter() - t0
+    s1 = it.state()
+    rhs = 6 * (s1["attempts"] - s0["attempts"])
+    return {"value": rhs * p.ncells / dt, "unit": UNIT, "cores": int(os.environ["OMP_NUM_THREADS"]),
+            "kind": "oracle",
+            "sample": f"{p.name}: {s1['attempts'] - s0['attempts']} adaptive FP64 attempts "
+                      f"({rhs} RHS evaluations x {p.ncells} cells) in {dt:.1f} s"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    p = make_workload(args.workload, args.box)
+    from oracle import oracle as O
+    cores = os.cpu_count() or 1
+    os.environ.setdefault("OMP_NUM_THREADS", str(cores))
+    op = O.OracleProblem(p)
+    it = O.Integrator(op)
+    t0 = time.perf_counter()
+    it.run(p.T, max_attempts=1)
+    per = max(time.perf_counter() - t0, 1e-4)
+    budget = 150.0 / max(args.steps + args.warmup, 1)
+    att = max(1, int(budget / per))
+    for _ in range(args.warmup):
+        it.run(p.T, max_attempts=att)
+    t0 = time.perf_counter()
+    s0 = it.state()
+    for _ in range(args.steps):
+        it.run(p.T, max_attempts=att)
+    dt = time.perf_counter() - t0
+    s1 = it.state()
+    rhs = 6 * (s1["attempts"] - s0["attempts"])
+    v = rhs * p.ncells / dt
+    line = {"metric": METRIC, "value": v, "unit": UNIT, "impl": "reference", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": p.name, "cells": p.ncells,
+                                            "attempts_per_step": att},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": int(os.environ["OMP_NUM_THREADS"]),
+                             "kind": "oracle",
+                             "sample": f"{args.steps} steps x {att} adaptive FP64 attempts"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import numpy as np
+    import torch
+    from paper_2603_03706_b300 import cmx
+
+    rank, world, local = dist_setup(args.gpus)
+    p = make_workload(args.workload, args.box)
+    stream = torch.cuda.Stream()
+    tiling = tuple(int(v) for v in args.tiling.split(",")) if args.tiling else None
+    sim = cmx.Simulation.from_problem(p, stream=stream, tiling=tiling)
+    ncell = sim.ncells()[0]
+    bpa = bytes_per_cell_attempt(p) * ncell
+    # attempts per launch: about 20 ms of work per step at the HBM roofline
+    peaks = measured_peaks()
+    peak_gbs = peaks.get("hbm_gbs", 6400.0)
+    A = args.attempts or max(8, min(2000, int(0.02 * peak_gbs * 1e9 / bpa)))
+    T_far = 1.0                                   # never reached within a benchmark step
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MiB > L2
+
+    def step():
+        sim.launch(T_far, A)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            flush.zero_()
+            step()
+        sim.sync()
+        st0 = sim.sync()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.steps)]
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        with ClockSampler(local) as clk:
+            for i in range(args.steps):
+                flush.zero_()
+                evs[i][0].record(stream)
+                step()
+                evs[i][1].record(stream)
+            torch.cuda.synchronize()
+        st1 = sim.sync()
+    times = [a.elapsed_time(b) * 1e-3 for a, b in evs]
+    t_total = sum(times)
+    t_total_max = barrier_and_max(t_total, world)
+    updates = st1["cell_stage_updates"] - st0["cell_stage_updates"]
+    attempts = st1["attempts"] - st0["attempts"]
+    value = updates * world / t_total_max
+    achieved = bpa * (attempts / args.steps) / (t_total / args.steps) / 1e9
+
+    # end to end through the public API: pinned host buffers in and out every step
+    e2e = None
+    if not args.no_e2e:
+        m_host = torch.from_numpy(np.asarray(p.m0, np.float32).copy()).pin_memory()
+        m_out = torch.empty_like(m_host).pin_memory()
+        a0 = np.asarray(p.a0)
+        for _ in range(2):
+            sim.set_state(m_host, a0)
+            sim.launch(T_far, A)
+            sim.get_a()
+            sim.get_m(out=m_out)
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        u0 = 0
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            sim.set_state(m_host, a0)
+            sim.launch(T_far, A)
+            st = sim.sync()
+            u0 += st["cell_stage_updates"]
+            sim.get_a()
+            sim.get_m(out=m_out)
+        torch.cuda.synchronize()
+        te = barrier_and_max(time.perf_counter() - t0, world)
+        h2d = m_host.numel() * 4 + 16 * p.nmodes
+        d2h = m_out.numel() * 4 + 16 * p.nmodes
+        e2e = {"value": u0 * world / te, "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h}
+
+    if rank == 0:
+        clocks = clk.summary()
+        tl = sim.get_tiling()
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t_total_max / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": p.name, "cells": ncell, "grid": [p.nx, p.ny, p.nz],
+                       "nsub": p.nsub, "modes": p.nmodes, "attempts_per_step": A,
+                       "rhs_evals_per_step": updates / ncell / args.steps,
+                       "dt_max": p.dt_max, "l2": "flushed between timed steps (256 MiB write)",
+                       "tiling": tl, "parallelism": "replicas" if world > 1 else "single"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak_gbs, "unit": "GB/s",
+                         "frac": achieved / peak_gbs,
+                         "traffic": recorded_traffic(p.name),
+                         "bytes_per_cell_attempt": bytes_per_cell_attempt(p),
+                         "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else
+                         "fallback 6400 GB/s"},
+            "clocks": clocks,
+            "gpu_launches": 2 * args.steps,
+            "e2e": e2e,
+        }
+        if not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(p, args.cpu_seconds)
+        print(json.dumps(line))
+    sim.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,197 @@
+/*
+ * cmx.h - C ABI of the device-resident cavity-magnonics integrator (sm_103a).
+ *
+ * The library advances the Landau-Lifshitz-Gilbert equation of a masked magnet coupled to N
+ * cavity modes with an adaptive Dormand-Prince 5(4) scheme, entirely on the GPU.  Per stage it
+ * evaluates (paper: "Multimode cavity magnonics in mumax+", arXiv 2603.03706):
+ *   - the effective field: 6-neighbour exchange (free surface at the mask edge), uniaxial
+ *     anisotropy, Zeeman, diagonal demag, inter-sublattice exchange for two sublattices
+ *     (Sec. II G) and the cavity feedback B_rf,x(r) = sum_n u_n(r) (2/gamma) Re[g~_n a_n]
+ *     (Eq. (3), (5), (13); complex g~ for dissipative coupling, Eq. (19));
+ *   - the LLG torque with Gilbert damping (Sec. II A), Landau-Lifshitz form with 1/(1+alpha^2);
+ *   - the overlaps <m^->_n = (1/N_c) sum_mask u_n (m_x - i m_y) (Eq. (2), (18));
+ *   - the cavity ODEs da_n/dt = (-i w_n - kappa_n) a_n + i g~_n <m^->_n (Eq. (12), (19));
+ *   - the stage combination, the max-norm error estimate and the accept/reject decision, so a
+ *     run never returns to the host between steps (Sec. III A: one unified RK45 step with no
+ *     host-side intervention).
+ *
+ * Conventions.  SI units; frequencies and rates in rad/s; fields in tesla.  Dense box arrays
+ * are x fastest: index = x + nx*(y + ny*z).  Magnetisation arrays are [nsub][3][nx*ny*nz]
+ * float32 (unit vectors; values outside the mask are ignored on input, written as 0 on
+ * output).  Cavity amplitudes are interleaved complex float64: a[2n] = Re a_n, a[2n+1] = Im a_n.
+ *
+ * Memory.  The library copies every input at the call and owns all device memory it uses;
+ * it never keeps a caller pointer.  "on_device" flags say whether a pointer is a device
+ * address (read or written on the handle's stream) or host memory.
+ *
+ * Errors.  Every call returns a cmx_status.  Errors are sticky per handle: after a device-side
+ * failure (NaN, step-size underflow, barrier time-out) later run calls return the same code
+ * until cmx_set_state() resets the integrator.  cmx_last_error() gives a message owned by the
+ * handle.  Handles are not thread-safe; use one host thread per handle.
+ */
+#ifndef CMX_H
+#define CMX_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    CMX_OK = 0,
+    CMX_EINVAL = 1,      /* bad argument (sizes, NULL pointers, unsupported combination) */
+    CMX_ENOMEM = 2,      /* device or host allocation failed */
+    CMX_ECUDA = 3,       /* a CUDA runtime call failed */
+    CMX_ENAN = 4,        /* the error norm became NaN or Inf on the device */
+    CMX_ESTEPFAIL = 5,   /* the step size fell below dt_min */
+    CMX_ETIMEOUT = 6     /* a device-side wait (grid barrier) exceeded its time limit */
+} cmx_status;
+
+#define CMX_MAX_MODES 8
+
+typedef struct cmx_problem cmx_problem;   /* opaque handle */
+
+/* Grid: nx*ny*nz cells of size cx*cy*cz metres; nsub = 1 (ferromagnet) or 2 (two-sublattice
+ * antiferromagnet on the same cells).  nx <= 65535. */
+typedef struct {
+    int nx, ny, nz;
+    double cx, cy, cz;
+    int nsub;
+} cmx_grid;
+
+/* Material.  Ms [A/m] per sublattice, Aex [J/m] intra-sublattice exchange stiffness, alpha
+ * Gilbert damping, gamma [rad/(s T)], Ku [J/m^3] along the unit vector ku_axis, B0 [T] static
+ * field, Ndemag diagonal demag factors acting on the total moment Ms (m1 + m2), BE [T]
+ * inter-sublattice exchange field (B_1 gets -BE m_2 and vice versa; ignored for nsub = 1). */
+typedef struct {
+    double Ms, Aex, alpha, gamma, Ku;
+    double ku_axis[3];
+    double B0[3];
+    double Ndemag[3];
+    double BE;
+} cmx_material;
+
+/* Cavity modes (n_modes <= CMX_MAX_MODES, may be 0).  omega, kappa, g_re, g_im: host arrays of
+ * n_modes doubles; the complex coupling is g~_n = g_re[n] + i g_im[n] (g_d = -g_im, Eq. (19)).
+ * u: n_modes x nx*ny*nz float32 mode profiles (dense box) or NULL for u_n = 1 everywhere;
+ * u_on_device says where u lives. */
+typedef struct {
+    int n_modes;
+    const double *omega, *kappa, *g_re, *g_im;
+    const float *u;
+    int u_on_device;
+} cmx_modes;
+
+/* Step-size control (the paper only says "adaptive RK45"; this is the reading used):
+ *   err = max( max_cells |e_m| / rtol , max_n |e_a,n| / (rtol * max(a_ref, max_n |a_n|)) )
+ *   accept iff err <= 1; dt <- min(dt * clamp(0.9 err^-1/5, 0.2, 5), dt_max), growth capped at
+ *   1 right after a rejection; dt < dt_min -> CMX_ESTEPFAIL.
+ * sample_dt > 0 records a uniform trace of a_n(t) (cubic Hermite) and <m^->_n(t) (linear) into
+ * a device buffer of trace_cap samples.  log_cap: capacity of the per-attempt log. */
+typedef struct {
+    double rtol, a_ref, dt0, dt_min, dt_max;
+    double sample_dt;
+    int log_cap;
+    int trace_cap;
+} cmx_solver;
+
+/* Launch shape.  bx, by: thread-block window in cells (one thread per window column; compiled
+ * windows: 32x8, 32x16, 64x4, and 32x8, 64x4 for two sublattices).  A block computes the
+ * (bx-2) x (by-2) interior columns, the one-cell rim is the exchange halo, and marches along z.
+ * The columns' planes are split into contiguous per-block segments with equal plane counts.
+ * bz: the fewest planes per block (0 = 4); fewer blocks are used when the grid is small.
+ * blocks_per_sm caps the resident blocks per SM (0 = as many as fit).  bx = by = 0 selects
+ * the 32x8 window. */
+typedef struct {
+    int bx, by, bz;
+    int blocks_per_sm;   /* 0 = as many as fit */
+} cmx_tiling;
+
+typedef struct {
+    double t, dt;
+    long long attempts, accepted;
+    long long cell_stage_updates;   /* masked cells x RHS evaluations performed */
+    int status;
+    int launches;
+} cmx_stats;
+
+/* One per attempted step: end time (accepted) or start time (rejected), step size, scaled
+ * error, accepted flag. */
+typedef struct {
+    double t, dt, err;
+    int32_t accepted;
+    int32_t pad;
+} cmx_step;
+
+/* Create a problem from the grid, the mask (host, nx*ny*nz bytes, nonzero = magnetic), the
+ * material, the modes and the solver settings.  stream: a cudaStream_t (NULL = the legacy
+ * default stream) on which all work of the handle is enqueued.  The initial state is m = +z
+ * (sublattice 2: -z), a = 0, t = 0.  Fails with CMX_EINVAL for an empty mask, n_modes out of
+ * range, nsub not 1 or 2, nx > 65535 or non-positive sizes. */
+int cmx_create(const cmx_grid *grid, const uint8_t *mask, const cmx_material *mat,
+               const cmx_modes *modes, const cmx_solver *solver, const cmx_tiling *tiling,
+               void *stream, cmx_problem **out);
+
+int cmx_destroy(cmx_problem *h);
+
+/* Set y = (m, a) at time t and reset the step size to dt0 (m: dense box [nsub][3][nbox]
+ * float32, host or device; a: 2*n_modes doubles on the host, may be NULL = zeros). */
+int cmx_set_state(cmx_problem *h, const float *m, int m_on_device, const double *a, double t);
+
+/* Adaptive integration until t >= T (the final attempt is shortened to land on T) or until
+ * max_attempts attempts have been made (<= 0: no limit).  Blocks the calling thread; the work
+ * runs as persistent kernel launches on the handle's stream, each ending after at most
+ * cmx_set_launch_attempts() attempts, with one small status read between launches. */
+int cmx_run(cmx_problem *h, double T, long long max_attempts, cmx_stats *st);
+
+/* Enqueue ONE launch of up to n_attempts adaptive attempts towards T; does not wait. */
+int cmx_launch(cmx_problem *h, double T, int n_attempts);
+
+/* Replay: take exactly the n given step sizes (host array), every step accepted. */
+int cmx_replay(cmx_problem *h, const double *dts, long long n, cmx_stats *st);
+
+/* Wait for the handle's stream and return the integrator status and counters. */
+int cmx_sync(cmx_problem *h, cmx_stats *st);
+
+/* Evaluate the right-hand side once at (m, a) without touching the integrator state:
+ * dm (dense box, same layout as m, 0 outside the mask), da (2N), mm (2N: <m^->_n).  All host
+ * pointers.  Uses the same stage kernel as the integrator (stage 1). */
+int cmx_eval_rhs(cmx_problem *h, const float *m, const double *a, float *dm, double *da,
+                 double *mm);
+
+/* Results.  m: dense box [nsub][3][nbox] float32 (host or device).  a: 2N doubles (host). */
+int cmx_get_m(cmx_problem *h, float *dst, int on_device);
+int cmx_get_a(cmx_problem *h, double *dst);
+
+/* Per-attempt log (cap entries; *n receives the number of attempts logged so far, which may
+ * exceed the log capacity).  a, mm: optional (cap * 2N doubles): amplitudes after each accepted
+ * attempt and the overlap <m^->_n at its 5th-order point. */
+int cmx_get_log(cmx_problem *h, cmx_step *dst, double *a, double *mm, int cap, long long *n);
+
+/* Uniform trace: t (cap), a (cap*2N), mm (cap*2N), host pointers; *n = samples recorded. */
+int cmx_get_trace(cmx_problem *h, double *t, double *a, double *mm, int cap, long long *n);
+
+/* Number of magnetic cells and number of stored cells (stored = magnetic + padding holes). */
+int cmx_ncells(const cmx_problem *h, long long *n_magnetic, long long *n_stored);
+
+/* Attempts per persistent launch in cmx_run (default 4096). */
+int cmx_set_launch_attempts(cmx_problem *h, int n);
+
+/* Device-side wait limit for grid barriers in nanoseconds (default 2e9). */
+int cmx_set_timeout(cmx_problem *h, long long ns);
+
+/* Test hook: block `block` of the next launch skips its first barrier arrival and exits, so
+ * the other blocks reach their wait limit; -1 disables.  Used only to test CMX_ETIMEOUT. */
+int cmx_debug_skip_arrival(cmx_problem *h, int block);
+
+/* Launch shape actually used: bx, by, bz, grid blocks, tiles. */
+int cmx_get_tiling(const cmx_problem *h, int *bx, int *by, int *bz, int *blocks, int *tiles);
+
+const char *cmx_last_error(const cmx_problem *h);
+const char *cmx_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CMX_H */

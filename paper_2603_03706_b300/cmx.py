@@ -1,0 +1,377 @@
+"""Thin ctypes binding of libcmx (include/cmx.h): argument marshalling only.
+
+Every step of the integration runs in the CUDA library; this module only converts arrays and
+structs.  If libcmx.so is missing it raises ImportError: there is no CPU fallback.
+Device arrays may be passed as torch CUDA tensors (their data pointer is used) or as plain
+integers holding a device address.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libcmx.so")
+
+OK, EINVAL, ENOMEM, ECUDA, ENAN, ESTEPFAIL, ETIMEOUT = range(7)
+MAX_MODES = 8
+
+
+class CmxError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"cmx status {code}: {msg}")
+        self.code = code
+
+
+class Grid(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("cx", C.c_double),
+                ("cy", C.c_double), ("cz", C.c_double), ("nsub", C.c_int)]
+
+
+class Material(C.Structure):
+    _fields_ = [("Ms", C.c_double), ("Aex", C.c_double), ("alpha", C.c_double),
+                ("gamma", C.c_double), ("Ku", C.c_double), ("ku_axis", C.c_double * 3),
+                ("B0", C.c_double * 3), ("Ndemag", C.c_double * 3), ("BE", C.c_double)]
+
+
+class Modes(C.Structure):
+    _fields_ = [("n_modes", C.c_int), ("omega", C.POINTER(C.c_double)),
+                ("kappa", C.POINTER(C.c_double)), ("g_re", C.POINTER(C.c_double)),
+                ("g_im", C.POINTER(C.c_double)), ("u", C.c_void_p), ("u_on_device", C.c_int)]
+
+
+class Solver(C.Structure):
+    _fields_ = [("rtol", C.c_double), ("a_ref", C.c_double), ("dt0", C.c_double),
+                ("dt_min", C.c_double), ("dt_max", C.c_double), ("sample_dt", C.c_double),
+                ("log_cap", C.c_int), ("trace_cap", C.c_int)]
+
+
+class Tiling(C.Structure):
+    _fields_ = [("bx", C.c_int), ("by", C.c_int), ("bz", C.c_int), ("blocks_per_sm", C.c_int)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("t", C.c_double), ("dt", C.c_double), ("attempts", C.c_longlong),
+                ("accepted", C.c_longlong), ("cell_stage_updates", C.c_longlong),
+                ("status", C.c_int), ("launches", C.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class Step(C.Structure):
+    _fields_ = [("t", C.c_double), ("dt", C.c_double), ("err", C.c_double),
+                ("accepted", C.c_int32), ("pad", C.c_int32)]
+
+
+_lib = None
+
+# name -> (restype, argtypes); every declaration of include/cmx.h
+_P = C.c_void_p
+SIGNATURES = {
+    "cmx_create": (C.c_int, [C.POINTER(Grid), C.c_void_p, C.POINTER(Material), C.POINTER(Modes),
+                             C.POINTER(Solver), C.POINTER(Tiling), C.c_void_p, C.POINTER(C.c_void_p)]),
+    "cmx_destroy": (C.c_int, [_P]),
+    "cmx_set_state": (C.c_int, [_P, C.c_void_p, C.c_int, C.c_void_p, C.c_double]),
+    "cmx_run": (C.c_int, [_P, C.c_double, C.c_longlong, C.POINTER(Stats)]),
+    "cmx_launch": (C.c_int, [_P, C.c_double, C.c_int]),
+    "cmx_replay": (C.c_int, [_P, C.c_void_p, C.c_longlong, C.POINTER(Stats)]),
+    "cmx_sync": (C.c_int, [_P, C.POINTER(Stats)]),
+    "cmx_eval_rhs": (C.c_int, [_P, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "cmx_get_m": (C.c_int, [_P, C.c_void_p, C.c_int]),
+    "cmx_get_a": (C.c_int, [_P, C.c_void_p]),
+    "cmx_get_log": (C.c_int, [_P, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int,
+                              C.POINTER(C.c_longlong)]),
+    "cmx_get_trace": (C.c_int, [_P, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int,
+                                C.POINTER(C.c_longlong)]),
+    "cmx_ncells": (C.c_int, [_P, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]),
+    "cmx_set_launch_attempts": (C.c_int, [_P, C.c_int]),
+    "cmx_set_timeout": (C.c_int, [_P, C.c_longlong]),
+    "cmx_debug_skip_arrival": (C.c_int, [_P, C.c_int]),
+    "cmx_get_tiling": (C.c_int, [_P, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                 C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+    "cmx_last_error": (C.c_char_p, [_P]),
+    "cmx_status_string": (C.c_char_p, [C.c_int]),
+}
+
+
+def load(path: Optional[str] = None):
+    """Load libcmx.so (built in-tree by paper_2603_03706_b300.build)."""
+    global _lib
+    if _lib is None:
+        p = path or LIB_PATH
+        if not os.path.exists(p):
+            raise ImportError(f"{p} not found: build it with `python -m paper_2603_03706_b300.build`"
+                              " (the integrator has no CPU fallback)")
+        lib = C.CDLL(p)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def _dev_ptr(x) -> Optional[int]:
+    """Device address of a torch CUDA tensor or an int, else None (host data)."""
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr") and getattr(x, "is_cuda", False):
+        return int(x.data_ptr())
+    return None
+
+
+def _host_f32_ptr(x) -> Optional[int]:
+    """Address of a contiguous float32 torch CPU tensor (e.g. pinned memory), else None."""
+    if hasattr(x, "data_ptr") and not getattr(x, "is_cuda", False):
+        if str(getattr(x, "dtype", "")) == "torch.float32" and x.is_contiguous():
+            return int(x.data_ptr())
+    return None
+
+
+def _f64(x):
+    return np.ascontiguousarray(np.asarray(x, np.float64).reshape(-1))
+
+
+def _f32(x):
+    return np.ascontiguousarray(np.asarray(x, np.float32).reshape(-1))
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _stream_handle(stream) -> Optional[int]:
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return int(getattr(stream, "cuda_stream"))
+
+
+class Simulation:
+    """One cmx_problem handle.  Method names follow the C calls (cmx_<name>)."""
+
+    def __init__(self, grid: Grid, mask: np.ndarray, mat: Material, omega=(), kappa=(),
+                 g_re=(), g_im=(), u=None, solver: Optional[Solver] = None,
+                 tiling: Optional[Tiling] = None, stream=None):
+        lib = load()
+        self._keep = []
+        self.nsub = grid.nsub
+        self.nbox = grid.nx * grid.ny * grid.nz
+        self.shape = (grid.nz, grid.ny, grid.nx)
+        mask = np.ascontiguousarray(np.asarray(mask, np.uint8).reshape(-1))
+        if mask.size != self.nbox:
+            raise ValueError("mask size")
+        om, ka, gr, gi = _f64(omega), _f64(kappa), _f64(g_re), _f64(g_im)
+        self.N = len(om)
+        md = Modes()
+        md.n_modes = self.N
+        md.omega, md.kappa, md.g_re, md.g_im = _dptr(om), _dptr(ka), _dptr(gr), _dptr(gi)
+        if u is None:
+            md.u, md.u_on_device = None, 0
+        elif _dev_ptr(u) is not None:
+            md.u, md.u_on_device = _dev_ptr(u), 1
+        else:
+            uu = _f32(u)
+            if uu.size != self.N * self.nbox:
+                raise ValueError("u size")
+            self._keep.append(uu)
+            md.u, md.u_on_device = uu.ctypes.data, 0
+        self.solver = solver or Solver(1e-6, 1e-3, 1e-13, 1e-18, 1e-11, 0.0, 0, 0)
+        h = C.c_void_p()
+        rc = lib.cmx_create(C.byref(grid), mask.ctypes.data, C.byref(mat), C.byref(md),
+                            C.byref(self.solver), C.byref(tiling) if tiling else None,
+                            _stream_handle(stream), C.byref(h))
+        if rc != OK:
+            raise CmxError(rc, f"cmx_create: {lib.cmx_status_string(rc).decode()}")
+        self.h = h
+        self._keep.clear()
+
+    @classmethod
+    def from_problem(cls, p, *, log_cap=0, trace_cap=0, sample_dt=0.0, tiling=None, stream=None,
+                     u=None):
+        """Build from a workloads.Problem (argument conversion only)."""
+        g = Grid(p.nx, p.ny, p.nz, p.cx, p.cy, p.cz, p.nsub)
+        mt = Material(p.Ms, p.Aex, p.alpha, p.gamma, p.Ku, (C.c_double * 3)(*p.ku_axis),
+                      (C.c_double * 3)(*p.B0), (C.c_double * 3)(*p.Ndemag), p.BE)
+        sv = Solver(p.rtol, p.a_ref, p.dt0, p.dt_min, p.dt_max, sample_dt, log_cap, trace_cap)
+        tl = Tiling(*tiling) if tiling is not None else None
+        sim = cls(g, p.mask, mt, p.omega, p.kappa, p.g_re, p.g_im,
+                  p.u if u is None else u, sv, tl, stream)
+        sim.set_state(p.m0, p.a0, 0.0)
+        return sim
+
+    # -- lifetime ----------------------------------------------------------------------------
+    def close(self):
+        if getattr(self, "h", None):
+            load().cmx_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def _check(self, rc: int, what: str):
+        if rc != OK:
+            msg = load().cmx_last_error(self.h).decode()
+            raise CmxError(rc, f"{what}: {msg}")
+
+    # -- state -------------------------------------------------------------------------------
+    def set_state(self, m, a=None, t: float = 0.0):
+        dp = _dev_ptr(m)
+        hp = _host_f32_ptr(m)
+        if dp is not None:
+            mp, dev = dp, 1
+        elif hp is not None:
+            if m.numel() != self.nsub * 3 * self.nbox:
+                raise ValueError("m size")
+            mp, dev = hp, 0
+        else:
+            mm = _f32(m)
+            if mm.size != self.nsub * 3 * self.nbox:
+                raise ValueError("m size")
+            mp, dev = mm.ctypes.data, 0
+        aa = None
+        if a is not None and self.N:
+            aa = np.empty(2 * self.N)
+            ac = np.asarray(a).reshape(-1)
+            if np.iscomplexobj(ac):
+                aa[0::2], aa[1::2] = ac.real, ac.imag
+            else:
+                aa[:] = ac
+        self._check(load().cmx_set_state(self.h, mp, dev, aa.ctypes.data if aa is not None else None,
+                                         float(t)), "set_state")
+
+    def get_m(self, out=None):
+        """Dense box magnetisation (nsub, 3, nz, ny, nx) float32; `out` may be a CUDA tensor."""
+        if out is not None and _dev_ptr(out) is not None:
+            self._check(load().cmx_get_m(self.h, _dev_ptr(out), 1), "get_m")
+            return out
+        if out is not None and _host_f32_ptr(out) is not None:
+            if out.numel() != self.nsub * 3 * self.nbox:
+                raise ValueError("out size")
+            self._check(load().cmx_get_m(self.h, _host_f32_ptr(out), 0), "get_m")
+            return out
+        buf = np.empty((self.nsub, 3) + self.shape, np.float32)
+        self._check(load().cmx_get_m(self.h, buf.ctypes.data, 0), "get_m")
+        return buf
+
+    def get_a(self) -> np.ndarray:
+        buf = np.zeros(max(2 * self.N, 1))
+        self._check(load().cmx_get_a(self.h, buf.ctypes.data), "get_a")
+        return buf[0:2 * self.N:2] + 1j * buf[1:2 * self.N:2]
+
+    # -- integration -------------------------------------------------------------------------
+    def run(self, T: float, max_attempts: int = 0) -> dict:
+        st = Stats()
+        self._check(load().cmx_run(self.h, float(T), int(max_attempts), C.byref(st)), "run")
+        return st.as_dict()
+
+    def launch(self, T: float, n_attempts: int):
+        self._check(load().cmx_launch(self.h, float(T), int(n_attempts)), "launch")
+
+    def replay(self, dts) -> dict:
+        d = _f64(dts)
+        st = Stats()
+        self._check(load().cmx_replay(self.h, d.ctypes.data, len(d), C.byref(st)), "replay")
+        return st.as_dict()
+
+    def sync(self) -> dict:
+        st = Stats()
+        self._check(load().cmx_sync(self.h, C.byref(st)), "sync")
+        return st.as_dict()
+
+    def status(self) -> int:
+        st = Stats()
+        return load().cmx_sync(self.h, C.byref(st))
+
+    def eval_rhs(self, m, a=None):
+        """f(m, a): (dm dense float32, da complex, <m^-> complex)."""
+        mm = _f32(m)
+        dm = np.empty((self.nsub, 3) + self.shape, np.float32)
+        aa = np.zeros(max(2 * self.N, 1))
+        if a is not None and self.N:
+            ac = np.asarray(a).reshape(-1)
+            aa[0:2 * self.N:2], aa[1:2 * self.N:2] = ac.real, ac.imag
+        da = np.zeros(max(2 * self.N, 1))
+        mo = np.zeros(max(2 * self.N, 1))
+        self._check(load().cmx_eval_rhs(self.h, mm.ctypes.data, aa.ctypes.data, dm.ctypes.data,
+                                        da.ctypes.data, mo.ctypes.data), "eval_rhs")
+        cx = lambda v: v[0:2 * self.N:2] + 1j * v[1:2 * self.N:2]
+        return dm, cx(da), cx(mo)
+
+    # -- records -----------------------------------------------------------------------------
+    def get_log(self, cap: Optional[int] = None) -> dict:
+        cap = self.solver.log_cap if cap is None else cap
+        steps = (Step * max(cap, 1))()
+        Q = max(2 * self.N, 1)
+        a = np.zeros(max(cap, 1) * Q)
+        mm = np.zeros(max(cap, 1) * Q)
+        n = C.c_longlong()
+        self._check(load().cmx_get_log(self.h, steps, a.ctypes.data, mm.ctypes.data, cap,
+                                       C.byref(n)), "get_log")
+        k = min(cap, n.value)
+        arr = np.ctypeslib.as_array(steps)[:k] if k else None
+        out = dict(n=n.value,
+                   t=np.array([s.t for s in steps[:k]]), dt=np.array([s.dt for s in steps[:k]]),
+                   err=np.array([s.err for s in steps[:k]]),
+                   accepted=np.array([bool(s.accepted) for s in steps[:k]], bool))
+        del arr
+        if self.N:
+            a = a[:k * 2 * self.N]
+            mm = mm[:k * 2 * self.N]
+            out["a"] = (a[0::2] + 1j * a[1::2]).reshape(k, self.N)
+            out["mm"] = (mm[0::2] + 1j * mm[1::2]).reshape(k, self.N)
+        return out
+
+    def get_trace(self, cap: Optional[int] = None) -> dict:
+        cap = self.solver.trace_cap if cap is None else cap
+        Q = max(2 * self.N, 1)
+        t = np.zeros(max(cap, 1))
+        a = np.zeros(max(cap, 1) * Q)
+        mm = np.zeros(max(cap, 1) * Q)
+        n = C.c_longlong()
+        self._check(load().cmx_get_trace(self.h, t.ctypes.data, a.ctypes.data, mm.ctypes.data, cap,
+                                         C.byref(n)), "get_trace")
+        k = min(cap, n.value)
+        out = dict(n=n.value, t=t[:k])
+        if self.N:
+            a, mm = a[:k * 2 * self.N], mm[:k * 2 * self.N]
+            out["a"] = (a[0::2] + 1j * a[1::2]).reshape(k, self.N)
+            out["mm"] = (mm[0::2] + 1j * mm[1::2]).reshape(k, self.N)
+        return out
+
+    # -- configuration -----------------------------------------------------------------------
+    def ncells(self):
+        a, b = C.c_longlong(), C.c_longlong()
+        self._check(load().cmx_ncells(self.h, C.byref(a), C.byref(b)), "ncells")
+        return a.value, b.value
+
+    def set_launch_attempts(self, n: int):
+        self._check(load().cmx_set_launch_attempts(self.h, int(n)), "set_launch_attempts")
+
+    def set_timeout(self, ns: int):
+        self._check(load().cmx_set_timeout(self.h, int(ns)), "set_timeout")
+
+    def debug_skip_arrival(self, block: int):
+        self._check(load().cmx_debug_skip_arrival(self.h, int(block)), "debug_skip_arrival")
+
+    def get_tiling(self) -> dict:
+        v = [C.c_int() for _ in range(5)]
+        self._check(load().cmx_get_tiling(self.h, *[C.byref(x) for x in v]), "get_tiling")
+        return dict(zip(("bx", "by", "bz", "blocks", "tiles"), [x.value for x in v]))
+
+    def last_error(self) -> str:
+        return load().cmx_last_error(self.h).decode()

@@ -1,0 +1,845 @@
+// C ABI of libcmx: problem set-up (compact layout and tiles), state transfer and the host loop
+// around the persistent device integrator.  See include/cmx.h for the contract.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "cmx_kernels.h"
+
+using namespace cmx;
+
+struct cmx_problem {
+    int dev = 0;
+    cudaStream_t stream = nullptr;
+    cmx_grid grid{};
+    cmx_material mat{};
+    cmx_solver sv{};
+    int N = 0;
+    double omega[MAXN]{}, kappa[MAXN]{}, gre[MAXN]{}, gim[MAXN]{};
+    long long nbox = 0;
+    int ncell = 0, ncell_mag = 0;
+    bool holes = false;
+    std::vector<int2> rows_h;
+    std::vector<int> box_of_cell_h;   // box index of each stored cell
+    std::vector<uint8_t> active_h;    // 1 = magnetic (stored cells)
+    // device buffers
+    int2 *rows = nullptr;
+    uint32_t *active = nullptr;
+    int *box_of_cell = nullptr;
+    int4 *tiles = nullptr;
+    int *seg_begin = nullptr;
+    int ntiles = 0;
+    float *u = nullptr;
+    float *mbuf[2] = {nullptr, nullptr};
+    float *kbuf[7] = {};
+    Ctl *ctl = nullptr;
+    float2 *part = nullptr;
+    float *errpart = nullptr;
+    cmx_step *log = nullptr;
+    double *log_a = nullptr, *log_mm = nullptr;
+    double *tr_t = nullptr, *tr_a = nullptr, *tr_mm = nullptr;
+    double *replay_dts = nullptr;
+    long long replay_cap = 0;
+    float *dense = nullptr;           // nsub*3*nbox scratch for dense <-> compact
+    // eval_rhs scratch
+    float *ev_m = nullptr, *ev_k = nullptr;
+    Ctl *ev_ctl = nullptr;
+    // launch shape
+    int bx = 32, by = 8, bz = 16, blocks = 0, bps = 0, nsm = 0;
+    long long launch_attempts = 4096;
+    long long timeout_ns = 2000000000LL;
+    int skip_block = -1;
+    int launches = 0;
+    std::string err;
+    Ctx base{};
+};
+
+namespace {
+
+int fail(cmx_problem *h, int code, const char *fmt, ...)
+{
+    if (h) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        h->err = buf;
+    }
+    return code;
+}
+
+#define CU(call)                                                                           \
+    do {                                                                                   \
+        cudaError_t e_ = (call);                                                           \
+        if (e_ != cudaSuccess)                                                             \
+            return fail(h, e_ == cudaErrorMemoryAllocation ? CMX_ENOMEM : CMX_ECUDA,       \
+                        "%s failed: %s", #call, cudaGetErrorString(e_));                   \
+    } while (0)
+
+template <class T>
+cudaError_t dalloc(T **p, size_t n)
+{
+    *p = nullptr;
+    if (n == 0) n = 1;
+    return cudaMalloc((void **)p, n * sizeof(T));
+}
+
+__global__ void gather_kernel(const float *dense, float *compact, const int *box_of_cell,
+                              const uint32_t *active, int ncell, long long nbox, int nq)
+{
+    const long long total = (long long)nq * ncell;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int q = (int)(i / ncell), c = (int)(i - (long long)q * ncell);
+        const bool on = !active || ((active[c >> 5] >> (c & 31)) & 1u);
+        compact[i] = on ? dense[q * nbox + box_of_cell[c]] : 0.f;
+    }
+}
+
+__global__ void scatter_kernel(const float *compact, float *dense, const int *box_of_cell,
+                               const uint32_t *active, int ncell, long long nbox, int nq)
+{
+    const long long total = (long long)nq * ncell;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int q = (int)(i / ncell), c = (int)(i - (long long)q * ncell);
+        const bool on = !active || ((active[c >> 5] >> (c & 31)) & 1u);
+        if (on) dense[q * nbox + box_of_cell[c]] = compact[i];
+    }
+}
+
+// Normalise the magnetic cells of a freshly set state (inputs need not be exact unit vectors).
+__global__ void normalise_kernel(float *m, const uint32_t *active, int ncell, int nsub)
+{
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ncell; c += gridDim.x * blockDim.x) {
+        const bool on = !active || ((active[c >> 5] >> (c & 31)) & 1u);
+        for (int s = 0; s < nsub; s++) {
+            float *x = m + (size_t)(3 * s) * ncell + c, *y = x + ncell, *z = y + ncell;
+            if (!on) {
+                *x = *y = *z = 0.f;
+                continue;
+            }
+            const float n2 = *x * *x + *y * *y + *z * *z;
+            const float r = n2 > 0.f ? rsqrtf(n2) : 0.f;
+            *x *= r;
+            *y *= r;
+            *z *= r;
+        }
+    }
+}
+
+// Stream-ordered update of the run parameters in the control block before a launch.
+__global__ void prep_kernel(Ctl *ctl, PrepArgs a)
+{
+    ctl->T = a.T;
+    ctl->done = 0;
+    ctl->launch_attempts = 0;
+    ctl->max_launch_attempts = a.max_launch_attempts;
+    ctl->skip_block = a.skip_block;
+    ctl->bar_count = 0;
+    if (a.set_replay == 1) {
+        ctl->replay = 1;
+        ctl->replay_pos = 0;
+        ctl->replay_n = a.replay_n;
+        ctl->replay_dts = a.replay_dts;
+    } else if (a.set_replay == 0) {
+        ctl->replay = 0;
+    }
+}
+
+int grid_blocks(long long n) { return (int)std::min<long long>(4096, (n + 255) / 256); }
+
+void build_layout(cmx_problem *h, const uint8_t *mask)
+{
+    const int nx = h->grid.nx, ny = h->grid.ny, nz = h->grid.nz;
+    h->rows_h.assign((size_t)ny * nz, make_int2(0, 0));
+    h->box_of_cell_h.clear();
+    h->active_h.clear();
+    int off = 0, nmag = 0;
+    for (int z = 0; z < nz; z++)
+        for (int y = 0; y < ny; y++) {
+            const size_t rb = ((size_t)z * ny + y) * nx;
+            int xs = -1, xe = -1;
+            for (int x = 0; x < nx; x++)
+                if (mask[rb + x]) {
+                    if (xs < 0) xs = x;
+                    xe = x + 1;
+                }
+            if (xs < 0) {
+                h->rows_h[(size_t)z * ny + y] = make_int2(off, 0);
+                continue;
+            }
+            h->rows_h[(size_t)z * ny + y] = make_int2(off, xs | (xe << 16));
+            for (int x = xs; x < xe; x++) {
+                h->box_of_cell_h.push_back((int)(rb + x));
+                h->active_h.push_back(mask[rb + x] ? 1 : 0);
+                nmag += mask[rb + x] ? 1 : 0;
+            }
+            off += xe - xs;
+        }
+    h->ncell = off;
+    h->ncell_mag = nmag;
+    h->holes = nmag != off;
+}
+
+// Columns of (wx-2) x (wy-2) interior cells (a wx x wy thread window with its one-cell rim)
+// and, for each, the range of planes [zlo, zhi) that hold magnetic cells of the column.
+struct Column {
+    int x0, y0, zlo, zhi;
+};
+
+std::vector<Column> build_columns(const cmx_problem *h, int wx, int wy)
+{
+    const int nx = h->grid.nx, ny = h->grid.ny, nz = h->grid.nz;
+    const int bx = wx - 2, by = wy - 2;
+    std::vector<Column> out;
+    for (int y0 = 0; y0 < ny; y0 += by)
+        for (int x0 = 0; x0 < nx; x0 += bx) {
+            int zlo = -1, zhi = -1;
+            for (int z = 0; z < nz; z++) {
+                bool any = false;
+                for (int y = y0; y < std::min(ny, y0 + by) && !any; y++) {
+                    const int2 r = h->rows_h[(size_t)z * ny + y];
+                    const int xs = r.y & 0xffff, xe = (int)((unsigned)r.y >> 16);
+                    for (int x = std::max(xs, x0); x < std::min(xe, x0 + bx); x++)
+                        if (h->active_h[r.x + x - xs]) {
+                            any = true;
+                            break;
+                        }
+                }
+                if (any) {
+                    if (zlo < 0) zlo = z;
+                    zhi = z + 1;
+                }
+            }
+            if (zlo >= 0) out.push_back({x0, y0, zlo, zhi});
+        }
+    return out;
+}
+
+// Cut the columns into segments and give every block a contiguous run of segments with the
+// same number of planes (to within one); no segment is deeper than MAX_TILE_PLANES - 2.
+void build_segments(const std::vector<Column> &cols, int blocks, std::vector<int4> &segs,
+                    std::vector<int> &begin)
+{
+    long long P = 0;
+    for (const Column &c : cols) P += c.zhi - c.zlo;
+    segs.clear();
+    begin.assign(blocks + 1, 0);
+    int b = 0;
+    long long done = 0;   // planes assigned to blocks < b
+    auto quota_end = [&](int blk) { return (P * (blk + 1) + blocks - 1) / blocks; };
+    long long pos = 0;    // planes emitted so far
+    for (const Column &c : cols) {
+        int z = c.zlo;
+        while (z < c.zhi) {
+            while (b < blocks - 1 && pos >= quota_end(b)) begin[++b] = (int)segs.size();
+            const long long room = std::max<long long>(1, quota_end(b) - pos);
+            const int len = (int)std::min<long long>({(long long)(c.zhi - z), room,
+                                                      (long long)(MAX_TILE_PLANES - 2)});
+            segs.push_back(make_int4(c.x0, c.y0, z, z + len));
+            z += len;
+            pos += len;
+        }
+    }
+    (void)done;
+    while (b < blocks) begin[++b] = (int)segs.size();
+}
+
+int setup_tiling(cmx_problem *h, const cmx_tiling *t)
+{
+    int bx = 32, by = 8, bz = 0, bps = 0;
+    if (t && (t->bx || t->by)) {
+        bx = t->bx;
+        by = t->by;
+    }
+    if (t) {
+        bz = t->bz;
+        bps = t->blocks_per_sm;
+    }
+    if (!tile_shape_supported(h->grid.nsub, bx, by))
+        return fail(h, CMX_EINVAL,
+                    "block window %dx%d is not compiled for nsub=%d (32x8, 32x16, 64x4; two "
+                    "sublattices: 32x8, 64x4)", bx, by, h->grid.nsub);
+    int occ = single_blocks_per_sm(h->grid.nsub, bx, by, h->N > 0 && h->u != nullptr);
+    if (occ <= 0) return fail(h, CMX_ECUDA, "occupancy query failed for %dx%d", bx, by);
+    if (bps > 0) occ = std::min(occ, bps);
+    const std::vector<Column> cols = build_columns(h, bx, by);
+    long long P = 0;
+    for (const Column &c : cols) P += c.zhi - c.zlo;
+    // bz: the fewest planes a block should get (default 4); all resident blocks otherwise
+    if (bz <= 0) bz = 4;
+    const long long cap = (long long)occ * h->nsm;
+    const int blocks = (int)std::max<long long>(1, std::min<long long>(cap, (P + bz - 1) / bz));
+    std::vector<int4> segs;
+    std::vector<int> begin;
+    build_segments(cols, blocks, segs, begin);
+    if (segs.empty()) return fail(h, CMX_EINVAL, "no tiles");
+    if (h->tiles) cudaFree(h->tiles);
+    if (h->seg_begin) cudaFree(h->seg_begin);
+    h->tiles = nullptr;
+    h->seg_begin = nullptr;
+    if (dalloc(&h->tiles, segs.size()) != cudaSuccess ||
+        dalloc(&h->seg_begin, begin.size()) != cudaSuccess)
+        return fail(h, CMX_ENOMEM, "tiles");
+    cudaMemcpy(h->tiles, segs.data(), segs.size() * sizeof(int4), cudaMemcpyHostToDevice);
+    cudaMemcpy(h->seg_begin, begin.data(), begin.size() * sizeof(int), cudaMemcpyHostToDevice);
+    h->ntiles = (int)segs.size();
+    h->bx = bx;
+    h->by = by;
+    h->bz = bz;
+    h->bps = occ;
+    h->blocks = blocks;
+    if (h->part) cudaFree(h->part);
+    if (h->errpart) cudaFree(h->errpart);
+    h->part = nullptr;
+    h->errpart = nullptr;
+    if (dalloc(&h->part, (size_t)h->blocks * 2 * std::max(1, h->N)) != cudaSuccess ||
+        dalloc(&h->errpart, (size_t)h->blocks) != cudaSuccess)
+        return fail(h, CMX_ENOMEM, "partials");
+    return CMX_OK;
+}
+
+Ctx make_ctx(const cmx_problem *h)
+{
+    Ctx c = h->base;
+    c.tiles = h->tiles;
+    c.seg_begin = h->seg_begin;
+    c.ntiles = h->ntiles;
+    c.bz = h->bz;
+    c.part = h->part;
+    c.errpart = h->errpart;
+    c.timeout_ns = h->timeout_ns;
+    return c;
+}
+
+int launch(cmx_problem *h, const PrepArgs &pa, const Ctx &c)
+{
+    prep_kernel<<<1, 1, 0, h->stream>>>(c.ctl, pa);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(h, CMX_ECUDA, "prep launch: %s", cudaGetErrorString(e));
+    e = launch_single(c, h->bx, h->by, h->blocks, h->stream);
+    if (e != cudaSuccess) return fail(h, CMX_ECUDA, "integrator launch: %s", cudaGetErrorString(e));
+    h->launches++;
+    return CMX_OK;
+}
+
+int read_ctl(cmx_problem *h, Ctl *out)
+{
+    CU(cudaMemcpyAsync(out, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, h->stream));
+    CU(cudaStreamSynchronize(h->stream));
+    return CMX_OK;
+}
+
+void fill_stats(const cmx_problem *h, const Ctl &c, cmx_stats *st)
+{
+    if (!st) return;
+    st->t = c.t;
+    st->dt = c.dt;
+    st->attempts = c.attempts;
+    st->accepted = c.accepted;
+    st->cell_stage_updates = c.rhs_evals * (long long)h->ncell_mag;
+    st->status = c.status;
+    st->launches = h->launches;
+}
+
+int device_status(cmx_problem *h, const Ctl &c)
+{
+    if (c.status == CMX_OK) return CMX_OK;
+    if (c.status == CMX_ETIMEOUT)
+        return fail(h, CMX_ETIMEOUT, "device barrier wait exceeded %lld ns (stage %d)",
+                    h->timeout_ns, c.timeout_where);
+    if (c.status == CMX_ENAN) return fail(h, CMX_ENAN, "error norm is NaN/Inf at t=%g", c.t);
+    if (c.status == CMX_ESTEPFAIL)
+        return fail(h, CMX_ESTEPFAIL, "step size below dt_min at t=%g", c.t);
+    return fail(h, c.status, "device status %d", c.status);
+}
+
+// Run launches until the integrator reports done because of T / replay end, an error, or the
+// attempt budget.
+int drive(cmx_problem *h, double T, long long max_attempts, int set_replay, long long replay_n,
+          cmx_stats *st)
+{
+    Ctx c = make_ctx(h);
+    Ctl hc;
+    int rc = read_ctl(h, &hc);
+    if (rc) return rc;
+    if (hc.status) return device_status(h, hc);
+    const long long start = hc.attempts;
+    bool first = true;
+    for (;;) {
+        long long budget = h->launch_attempts;
+        if (max_attempts > 0) budget = std::min(budget, max_attempts - (hc.attempts - start));
+        if (budget <= 0) break;
+        if (set_replay != 1 && hc.t >= T) break;
+        PrepArgs pa{};
+        pa.T = T;
+        pa.max_launch_attempts = budget;
+        pa.set_replay = first ? set_replay : -1;
+        pa.replay_n = replay_n;
+        pa.replay_dts = h->replay_dts;
+        pa.skip_block = first ? h->skip_block : -1;
+        if (first) h->skip_block = -1;
+        rc = launch(h, pa, c);
+        if (rc) return rc;
+        rc = read_ctl(h, &hc);
+        if (rc) return rc;
+        first = false;
+        if (hc.status) {
+            fill_stats(h, hc, st);
+            return device_status(h, hc);
+        }
+        if (hc.replay && hc.replay_pos >= hc.replay_n) break;
+        if (!hc.replay && hc.t >= T) break;
+    }
+    fill_stats(h, hc, st);
+    return CMX_OK;
+}
+
+void free_all(cmx_problem *h)
+{
+    void *ptrs[] = {h->rows, h->active, h->box_of_cell, h->tiles, h->seg_begin, h->u,
+                    h->mbuf[0], h->mbuf[1],
+                    h->ctl, h->part, h->errpart, h->log, h->log_a, h->log_mm, h->tr_t, h->tr_a,
+                    h->tr_mm, h->replay_dts, h->dense, h->ev_m, h->ev_k, h->ev_ctl};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    for (float *p : h->kbuf)
+        if (p) cudaFree(p);
+}
+
+int reset_ctl(cmx_problem *h, const double *a, double t)
+{
+    Ctl c;
+    memset(&c, 0, sizeof c);
+    c.t = t;
+    c.T = t;
+    c.dt = h->sv.dt0;
+    for (int q = 0; q < 2 * h->N; q++) c.a[q] = a ? a[q] : 0.0;
+    for (int j = 0; j < 7; j++) c.kphys[j] = j;
+    c.trace_next = t;
+    c.skip_block = -1;
+    c.max_launch_attempts = 1;
+    CU(cudaMemcpyAsync(h->ctl, &c, sizeof c, cudaMemcpyHostToDevice, h->stream));
+    CU(cudaStreamSynchronize(h->stream));
+    return CMX_OK;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------------------------------------
+extern "C" {
+
+const char *cmx_status_string(int s)
+{
+    switch (s) {
+    case CMX_OK: return "ok";
+    case CMX_EINVAL: return "invalid argument";
+    case CMX_ENOMEM: return "out of memory";
+    case CMX_ECUDA: return "CUDA error";
+    case CMX_ENAN: return "NaN in error norm";
+    case CMX_ESTEPFAIL: return "step size underflow";
+    case CMX_ETIMEOUT: return "device wait timed out";
+    default: return "unknown status";
+    }
+}
+
+const char *cmx_last_error(const cmx_problem *h) { return h ? h->err.c_str() : "null handle"; }
+
+int cmx_create(const cmx_grid *grid, const uint8_t *mask, const cmx_material *mat,
+               const cmx_modes *modes, const cmx_solver *solver, const cmx_tiling *tiling,
+               void *stream, cmx_problem **out)
+{
+    if (!out) return CMX_EINVAL;
+    *out = nullptr;
+    if (!grid || !mask || !mat || !solver) return CMX_EINVAL;
+    if (grid->nx <= 0 || grid->ny <= 0 || grid->nz <= 0 || grid->nx > 65535 ||
+        (grid->nsub != 1 && grid->nsub != 2) || !(grid->cx > 0) || !(grid->cy > 0) ||
+        !(grid->cz > 0))
+        return CMX_EINVAL;
+    const int N = modes ? modes->n_modes : 0;
+    if (N < 0 || N > MAXN) return CMX_EINVAL;
+    if (N > 0 && (!modes->omega || !modes->kappa || !modes->g_re || !modes->g_im))
+        return CMX_EINVAL;
+    if (!(mat->Ms > 0) || !(mat->gamma > 0) || !(solver->rtol > 0) || !(solver->dt0 > 0) ||
+        !(solver->dt_max > 0) || solver->log_cap < 0 || solver->trace_cap < 0)
+        return CMX_EINVAL;
+    const long long nbox = (long long)grid->nx * grid->ny * grid->nz;
+    if (nbox > (1LL << 31) - 1) return CMX_EINVAL;
+
+    cmx_problem *h = new (std::nothrow) cmx_problem();
+    if (!h) return CMX_ENOMEM;
+    h->grid = *grid;
+    h->mat = *mat;
+    h->sv = *solver;
+    h->N = N;
+    h->nbox = nbox;
+    h->stream = (cudaStream_t)stream;
+    for (int n = 0; n < N; n++) {
+        h->omega[n] = modes->omega[n];
+        h->kappa[n] = modes->kappa[n];
+        h->gre[n] = modes->g_re[n];
+        h->gim[n] = modes->g_im[n];
+    }
+    auto bail = [&](int rc) {
+        free_all(h);
+        delete h;
+        return rc;
+    };
+    if (cudaGetDevice(&h->dev) != cudaSuccess) return bail(CMX_ECUDA);
+    if (cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, h->dev) != cudaSuccess)
+        return bail(CMX_ECUDA);
+    int coop = 0;
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, h->dev);
+    if (!coop) return bail(CMX_ECUDA);
+
+    build_layout(h, mask);
+    if (h->ncell_mag == 0) return bail(CMX_EINVAL);
+    const int nq = 3 * grid->nsub;
+    const size_t nc = (size_t)h->ncell;
+    // device buffers
+    if (dalloc(&h->rows, h->rows_h.size()) || dalloc(&h->box_of_cell, nc) ||
+        dalloc(&h->mbuf[0], nq * nc) || dalloc(&h->mbuf[1], nq * nc) || dalloc(&h->ctl, 1) ||
+        dalloc(&h->dense, (size_t)nq * nbox))
+        return bail(CMX_ENOMEM);
+    for (int j = 0; j < 7; j++)
+        if (dalloc(&h->kbuf[j], nq * nc)) return bail(CMX_ENOMEM);
+    cudaMemcpy(h->rows, h->rows_h.data(), h->rows_h.size() * sizeof(int2), cudaMemcpyHostToDevice);
+    cudaMemcpy(h->box_of_cell, h->box_of_cell_h.data(), nc * sizeof(int), cudaMemcpyHostToDevice);
+    if (h->holes) {
+        std::vector<uint32_t> bits((nc + 31) / 32, 0u);
+        for (size_t i = 0; i < nc; i++)
+            if (h->active_h[i]) bits[i >> 5] |= 1u << (i & 31);
+        if (dalloc(&h->active, bits.size())) return bail(CMX_ENOMEM);
+        cudaMemcpy(h->active, bits.data(), bits.size() * sizeof(uint32_t), cudaMemcpyHostToDevice);
+    }
+    for (int j = 0; j < 7; j++) cudaMemset(h->kbuf[j], 0, nq * nc * sizeof(float));
+    cudaMemset(h->mbuf[1], 0, nq * nc * sizeof(float));
+    // mode profiles, compacted
+    if (N > 0 && modes->u) {
+        if (dalloc(&h->u, (size_t)N * nc)) return bail(CMX_ENOMEM);
+        if (modes->u_on_device) {
+            gather_kernel<<<grid_blocks((long long)N * nc), 256>>>(
+                modes->u, h->u, h->box_of_cell, h->active, h->ncell, nbox, N);
+        } else {
+            std::vector<float> uc((size_t)N * nc);
+            for (int n = 0; n < N; n++)
+                for (size_t i = 0; i < nc; i++)
+                    uc[n * nc + i] = h->active_h[i] ? modes->u[n * nbox + h->box_of_cell_h[i]] : 0.f;
+            cudaMemcpy(h->u, uc.data(), uc.size() * sizeof(float), cudaMemcpyHostToDevice);
+        }
+    }
+    // log and trace
+    const int lc = std::max(1, solver->log_cap), tc = std::max(1, solver->trace_cap);
+    const int Q = 2 * std::max(1, N);
+    if (dalloc(&h->log, lc) || dalloc(&h->log_a, (size_t)lc * Q) ||
+        dalloc(&h->log_mm, (size_t)lc * Q) || dalloc(&h->tr_t, tc) ||
+        dalloc(&h->tr_a, (size_t)tc * Q) || dalloc(&h->tr_mm, (size_t)tc * Q))
+        return bail(CMX_ENOMEM);
+    if (cudaDeviceSynchronize() != cudaSuccess) return bail(CMX_ECUDA);
+
+    // kernel context
+    Ctx &c = h->base;
+    memset(&c, 0, sizeof c);
+    c.nx = grid->nx;
+    c.ny = grid->ny;
+    c.nz = grid->nz;
+    c.nsub = grid->nsub;
+    c.nmodes = N;
+    c.ncell = h->ncell;
+    c.ncell_mag = h->ncell_mag;
+    c.rows = h->rows;
+    c.active = h->active;
+    c.u = h->u;
+    c.m[0] = h->mbuf[0];
+    c.m[1] = h->mbuf[1];
+    for (int j = 0; j < 7; j++) c.k[j] = h->kbuf[j];
+    const double exch = 2.0 * mat->Aex / mat->Ms;
+    c.wx = (float)(exch / (grid->cx * grid->cx));
+    c.wy = (float)(exch / (grid->cy * grid->cy));
+    c.wz = (float)(exch / (grid->cz * grid->cz));
+    c.anis = (float)(2.0 * mat->Ku / mat->Ms);
+    const double mu0 = 4.0e-7 * M_PI;
+    for (int k = 0; k < 3; k++) {
+        c.ku[k] = (float)mat->ku_axis[k];
+        c.B0[k] = (float)mat->B0[k];
+        c.dmg[k] = (float)(mu0 * mat->Ms * mat->Ndemag[k]);
+    }
+    c.BE = grid->nsub == 2 ? (float)mat->BE : 0.f;
+    c.pre = (float)(-mat->gamma / (1.0 + mat->alpha * mat->alpha));
+    c.alpha = (float)mat->alpha;
+    for (int n = 0; n < N; n++) {
+        c.omega[n] = h->omega[n];
+        c.kappa[n] = h->kappa[n];
+        c.gre[n] = h->gre[n];
+        c.gim[n] = h->gim[n];
+    }
+    c.two_over_gamma = 2.0 / mat->gamma;
+    c.inv_nmag = 1.0 / (double)h->ncell_mag;
+    c.rtol = solver->rtol;
+    c.a_ref = solver->a_ref;
+    c.dt_min = solver->dt_min;
+    c.dt_max = solver->dt_max;
+    c.sample_dt = solver->sample_dt;
+    c.ctl = h->ctl;
+    c.log = h->log;
+    c.log_a = h->log_a;
+    c.log_mm = h->log_mm;
+    c.log_cap = solver->log_cap;
+    c.tr_t = h->tr_t;
+    c.tr_a = h->tr_a;
+    c.tr_mm = h->tr_mm;
+    c.tr_cap = solver->trace_cap;
+
+    int rc = setup_tiling(h, tiling);
+    if (rc) return bail(rc);
+
+    // initial state: +z (sublattice 2: -z), a = 0
+    std::vector<float> m0((size_t)nq * nc, 0.f);
+    for (size_t i = 0; i < nc; i++)
+        if (h->active_h[i]) {
+            m0[2 * nc + i] = 1.f;
+            if (grid->nsub == 2) m0[5 * nc + i] = -1.f;
+        }
+    cudaMemcpy(h->mbuf[0], m0.data(), m0.size() * sizeof(float), cudaMemcpyHostToDevice);
+    rc = reset_ctl(h, nullptr, 0.0);
+    if (rc) return bail(rc);
+    *out = h;
+    return CMX_OK;
+}
+
+int cmx_destroy(cmx_problem *h)
+{
+    if (!h) return CMX_EINVAL;
+    cudaStreamSynchronize(h->stream);
+    free_all(h);
+    delete h;
+    return CMX_OK;
+}
+
+int cmx_set_state(cmx_problem *h, const float *m, int m_on_device, const double *a, double t)
+{
+    if (!h || !m) return fail(h, CMX_EINVAL, "null argument");
+    const int nq = 3 * h->grid.nsub;
+    const size_t nc = (size_t)h->ncell;
+    if (m_on_device) {
+        gather_kernel<<<grid_blocks((long long)nq * nc), 256, 0, h->stream>>>(
+            m, h->mbuf[0], h->box_of_cell, h->active, h->ncell, h->nbox, nq);
+    } else {
+        CU(cudaMemcpyAsync(h->dense, m, (size_t)nq * h->nbox * sizeof(float),
+                           cudaMemcpyHostToDevice, h->stream));
+        gather_kernel<<<grid_blocks((long long)nq * nc), 256, 0, h->stream>>>(
+            h->dense, h->mbuf[0], h->box_of_cell, h->active, h->ncell, h->nbox, nq);
+    }
+    normalise_kernel<<<grid_blocks((long long)nc), 256, 0, h->stream>>>(h->mbuf[0], h->active,
+                                                                         h->ncell, h->grid.nsub);
+    CU(cudaGetLastError());
+    return reset_ctl(h, a, t);
+}
+
+int cmx_run(cmx_problem *h, double T, long long max_attempts, cmx_stats *st)
+{
+    if (!h) return CMX_EINVAL;
+    return drive(h, T, max_attempts, 0, 0, st);
+}
+
+int cmx_launch(cmx_problem *h, double T, int n_attempts)
+{
+    if (!h || n_attempts <= 0) return fail(h, CMX_EINVAL, "bad argument");
+    PrepArgs pa{};
+    pa.T = T;
+    pa.max_launch_attempts = n_attempts;
+    pa.set_replay = 0;
+    pa.skip_block = -1;
+    return launch(h, pa, make_ctx(h));
+}
+
+int cmx_replay(cmx_problem *h, const double *dts, long long n, cmx_stats *st)
+{
+    if (!h || (!dts && n > 0) || n < 0) return fail(h, CMX_EINVAL, "bad argument");
+    if (n == 0) return cmx_sync(h, st);
+    for (long long i = 0; i < n; i++)
+        if (!(dts[i] > 0)) return fail(h, CMX_EINVAL, "replay step %lld is not positive", i);
+    if (n > h->replay_cap) {
+        if (h->replay_dts) cudaFree(h->replay_dts);
+        h->replay_dts = nullptr;
+        h->replay_cap = 0;
+        CU(dalloc(&h->replay_dts, n));
+        h->replay_cap = n;
+    }
+    CU(cudaMemcpyAsync(h->replay_dts, dts, n * sizeof(double), cudaMemcpyHostToDevice,
+                       h->stream));
+    return drive(h, INFINITY, 0, 1, n, st);
+}
+
+int cmx_sync(cmx_problem *h, cmx_stats *st)
+{
+    if (!h) return CMX_EINVAL;
+    Ctl hc;
+    int rc = read_ctl(h, &hc);
+    if (rc) return rc;
+    fill_stats(h, hc, st);
+    return device_status(h, hc);
+}
+
+int cmx_get_m(cmx_problem *h, float *dst, int on_device)
+{
+    if (!h || !dst) return fail(h, CMX_EINVAL, "null argument");
+    Ctl hc;
+    int rc = read_ctl(h, &hc);
+    if (rc) return rc;
+    const int nq = 3 * h->grid.nsub;
+    float *d = on_device ? dst : h->dense;
+    CU(cudaMemsetAsync(d, 0, (size_t)nq * h->nbox * sizeof(float), h->stream));
+    scatter_kernel<<<grid_blocks((long long)nq * h->ncell), 256, 0, h->stream>>>(
+        h->mbuf[hc.mcur], d, h->box_of_cell, h->active, h->ncell, h->nbox, nq);
+    CU(cudaGetLastError());
+    if (!on_device)
+        CU(cudaMemcpyAsync(dst, h->dense, (size_t)nq * h->nbox * sizeof(float),
+                           cudaMemcpyDeviceToHost, h->stream));
+    CU(cudaStreamSynchronize(h->stream));
+    return CMX_OK;
+}
+
+int cmx_get_a(cmx_problem *h, double *dst)
+{
+    if (!h || (!dst && h->N > 0)) return fail(h, CMX_EINVAL, "null argument");
+    Ctl hc;
+    int rc = read_ctl(h, &hc);
+    if (rc) return rc;
+    for (int q = 0; q < 2 * h->N; q++) dst[q] = hc.a[q];
+    return CMX_OK;
+}
+
+int cmx_get_log(cmx_problem *h, cmx_step *dst, double *a, double *mm, int cap, long long *n)
+{
+    if (!h || cap < 0) return fail(h, CMX_EINVAL, "bad argument");
+    Ctl hc;
+    int rc = read_ctl(h, &hc);
+    if (rc) return rc;
+    if (n) *n = hc.log_n;
+    const long long k = std::min<long long>({(long long)cap, hc.log_n, (long long)h->sv.log_cap});
+    const int Q = 2 * h->N;
+    if (k > 0) {
+        if (dst) CU(cudaMemcpy(dst, h->log, k * sizeof(cmx_step), cudaMemcpyDeviceToHost));
+        if (a && Q) CU(cudaMemcpy(a, h->log_a, k * Q * sizeof(double), cudaMemcpyDeviceToHost));
+        if (mm && Q)
+            CU(cudaMemcpy(mm, h->log_mm, k * Q * sizeof(double), cudaMemcpyDeviceToHost));
+    }
+    return CMX_OK;
+}
+
+int cmx_get_trace(cmx_problem *h, double *t, double *a, double *mm, int cap, long long *n)
+{
+    if (!h || cap < 0) return fail(h, CMX_EINVAL, "bad argument");
+    Ctl hc;
+    int rc = read_ctl(h, &hc);
+    if (rc) return rc;
+    if (n) *n = hc.trace_n;
+    const long long k = std::min<long long>({(long long)cap, hc.trace_n, (long long)h->sv.trace_cap});
+    const int Q = 2 * h->N;
+    if (k > 0) {
+        if (t) CU(cudaMemcpy(t, h->tr_t, k * sizeof(double), cudaMemcpyDeviceToHost));
+        if (a && Q) CU(cudaMemcpy(a, h->tr_a, k * Q * sizeof(double), cudaMemcpyDeviceToHost));
+        if (mm && Q) CU(cudaMemcpy(mm, h->tr_mm, k * Q * sizeof(double), cudaMemcpyDeviceToHost));
+    }
+    return CMX_OK;
+}
+
+int cmx_eval_rhs(cmx_problem *h, const float *m, const double *a, float *dm, double *da,
+                 double *mm)
+{
+    if (!h || !m || !dm) return fail(h, CMX_EINVAL, "null argument");
+    const int nq = 3 * h->grid.nsub;
+    const size_t nc = (size_t)h->ncell;
+    if (!h->ev_m) {
+        CU(dalloc(&h->ev_m, nq * nc));
+        CU(dalloc(&h->ev_k, nq * nc));
+        CU(dalloc(&h->ev_ctl, 1));
+    }
+    CU(cudaMemcpyAsync(h->dense, m, (size_t)nq * h->nbox * sizeof(float), cudaMemcpyHostToDevice,
+                       h->stream));
+    gather_kernel<<<grid_blocks((long long)nq * nc), 256, 0, h->stream>>>(
+        h->dense, h->ev_m, h->box_of_cell, h->active, h->ncell, h->nbox, nq);
+    Ctl c0;
+    memset(&c0, 0, sizeof c0);
+    for (int q = 0; q < 2 * h->N; q++) c0.a[q] = a ? a[q] : 0.0;
+    for (int j = 0; j < 7; j++) c0.kphys[j] = j;
+    c0.dt = h->sv.dt0;
+    c0.T = 1.0;
+    c0.skip_block = -1;
+    c0.max_launch_attempts = 1;
+    CU(cudaMemcpyAsync(h->ev_ctl, &c0, sizeof c0, cudaMemcpyHostToDevice, h->stream));
+    Ctx c = make_ctx(h);
+    c.m[0] = h->ev_m;
+    c.m[1] = h->ev_m;
+    for (int j = 0; j < 7; j++) c.k[j] = h->ev_k;
+    c.ctl = h->ev_ctl;
+    c.stage_only = 1;
+    c.log_cap = 0;
+    c.tr_cap = 0;
+    cudaError_t e = launch_single(c, h->bx, h->by, h->blocks, h->stream);
+    if (e != cudaSuccess) return fail(h, CMX_ECUDA, "eval launch: %s", cudaGetErrorString(e));
+    CU(cudaMemsetAsync(h->dense, 0, (size_t)nq * h->nbox * sizeof(float), h->stream));
+    scatter_kernel<<<grid_blocks((long long)nq * nc), 256, 0, h->stream>>>(
+        h->ev_k, h->dense, h->box_of_cell, h->active, h->ncell, h->nbox, nq);
+    CU(cudaMemcpyAsync(dm, h->dense, (size_t)nq * h->nbox * sizeof(float), cudaMemcpyDeviceToHost,
+                       h->stream));
+    Ctl hc;
+    CU(cudaMemcpyAsync(&hc, h->ev_ctl, sizeof hc, cudaMemcpyDeviceToHost, h->stream));
+    CU(cudaStreamSynchronize(h->stream));
+    if (hc.status) return device_status(h, hc);
+    for (int q = 0; q < 2 * h->N; q++) {
+        if (da) da[q] = hc.ka[0][q];
+        if (mm) mm[q] = hc.mm_n[q];
+    }
+    return CMX_OK;
+}
+
+int cmx_ncells(const cmx_problem *h, long long *n_magnetic, long long *n_stored)
+{
+    if (!h) return CMX_EINVAL;
+    if (n_magnetic) *n_magnetic = h->ncell_mag;
+    if (n_stored) *n_stored = h->ncell;
+    return CMX_OK;
+}
+
+int cmx_set_launch_attempts(cmx_problem *h, int n)
+{
+    if (!h || n <= 0) return fail(h, CMX_EINVAL, "bad argument");
+    h->launch_attempts = n;
+    return CMX_OK;
+}
+
+int cmx_set_timeout(cmx_problem *h, long long ns)
+{
+    if (!h || ns <= 0) return fail(h, CMX_EINVAL, "bad argument");
+    h->timeout_ns = ns;
+    return CMX_OK;
+}
+
+int cmx_debug_skip_arrival(cmx_problem *h, int block)
+{
+    if (!h || block >= h->blocks) return fail(h, CMX_EINVAL, "bad argument");
+    h->skip_block = block;
+    return CMX_OK;
+}
+
+int cmx_get_tiling(const cmx_problem *h, int *bx, int *by, int *bz, int *blocks, int *tiles)
+{
+    if (!h) return CMX_EINVAL;
+    if (bx) *bx = h->bx;
+    if (by) *by = h->by;
+    if (bz) *bz = h->bz;
+    if (blocks) *blocks = h->blocks;
+    if (tiles) *tiles = h->ntiles;
+    return CMX_OK;
+}
+
+}  // extern "C"

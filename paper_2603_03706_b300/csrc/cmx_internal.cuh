@@ -1,0 +1,104 @@
+// Internal definitions shared by the sm_103a kernels and the host code of libcmx.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/cmx.h"
+
+namespace cmx {
+
+constexpr int MAXN = CMX_MAX_MODES;
+
+// Deepest tile (planes including the two halo planes) whose row entries fit shared memory.
+constexpr int MAX_TILE_PLANES = 66;
+
+// Dormand & Prince (1980) 5(4) coefficients, written from the published rationals.
+// dp_a(s, j): coupling of stage s+1 to slope j+1 (row 6 is the 5th-order solution, FSAL).
+// dp_e(j) = b5_j - b4_j (5th minus embedded 4th-order weight) for the error estimate.
+// Both are constexpr so that, with the stage index a template parameter, zero couplings are
+// removed at compile time (stage 7 never reads slope 2).
+__host__ __device__ constexpr double dp_a(int s, int j)
+{
+    constexpr double A[7][6] = {
+        {0, 0, 0, 0, 0, 0},
+        {1.0 / 5, 0, 0, 0, 0, 0},
+        {3.0 / 40, 9.0 / 40, 0, 0, 0, 0},
+        {44.0 / 45, -56.0 / 15, 32.0 / 9, 0, 0, 0},
+        {19372.0 / 6561, -25360.0 / 2187, 64448.0 / 6561, -212.0 / 729, 0, 0},
+        {9017.0 / 3168, -355.0 / 33, 46732.0 / 5247, 49.0 / 176, -5103.0 / 18656, 0},
+        {35.0 / 384, 0, 500.0 / 1113, 125.0 / 192, -2187.0 / 6784, 11.0 / 84},
+    };
+    return A[s][j];
+}
+
+__host__ __device__ constexpr double dp_e(int j)
+{
+    constexpr double E[7] = {71.0 / 57600, 0, -71.0 / 16695, 71.0 / 1920,
+                             -17253.0 / 339200, 22.0 / 525, -1.0 / 40};
+    return E[j];
+}
+
+// Integrator control block in device memory.  Written only by the block that completes a
+// grid barrier (the "controller"), read by every block after the barrier is released.
+struct Ctl {
+    double t, dt, T;                 // current time, proposed step, end time of this run
+    double a[2 * MAXN];              // cavity amplitudes at t
+    double ka[7][2 * MAXN];          // cavity slopes of the current attempt (logical order)
+    double mm_n[2 * MAXN];           // overlap <m^->_n at t (for trace interpolation)
+    int kphys[7];                    // physical k buffer of logical slope j
+    int mcur;                        // m buffer holding y_n
+    int k1_valid;                    // FSAL slope of y_n present
+    int last_rejected;
+    int status;                      // sticky cmx_status
+    int done;                        // stop this launch
+    int replay;                      // 1: take step sizes from replay_dts
+    long long attempts, accepted, launch_attempts, max_launch_attempts;
+    long long rhs_evals;             // RHS evaluations (stages) performed
+    long long replay_pos, replay_n;
+    const double *replay_dts;
+    long long log_n, trace_n;
+    double trace_next;
+    unsigned int bar_count, bar_gen; // grid barrier
+    double bc[2 * MAXN];             // barrier broadcast: grid sums of the overlaps
+    float bc_emax;                   // barrier broadcast: grid max of |e_m|
+    int skip_block;                  // test hook (see cmx_debug_skip_arrival)
+    int timeout_where;
+};
+
+// Kernel arguments (by value).
+struct Ctx {
+    int nx, ny, nz, nsub, nmodes;
+    int ncell;                       // stored cells (compact, incl. padding holes)
+    int ncell_mag;                   // magnetic cells N_c
+    const int2 *rows;                // per (z, y) row: x = offset, y = xs | xe << 16
+    const uint32_t *active;          // bitmask over stored cells (NULL: no holes)
+    const int4 *tiles;               // segments: x0, y0, z0, z1
+    const int *seg_begin;            // block b owns segments [seg_begin[b], seg_begin[b+1])
+    int ntiles, bz;
+    const float *u;                  // [nmodes][ncell] or NULL
+    float *m[2];                     // [nsub*3][ncell]
+    float *k[7];                     // [nsub*3][ncell]
+    // material (float, tesla units)
+    float wx, wy, wz;                // (2 Aex / Ms) / c_d^2
+    float anis, ku[3], B0[3], dmg[3], BE;
+    float pre, alpha;                // -gamma/(1+alpha^2), alpha
+    // modes
+    double omega[MAXN], kappa[MAXN], gre[MAXN], gim[MAXN];
+    double two_over_gamma, inv_nmag;
+    // solver
+    double rtol, a_ref, dt_min, dt_max, sample_dt;
+    Ctl *ctl;
+    float2 *part;                    // [gridDim][2N] overlap partials (hi, lo pairs)
+    float *errpart;                  // [gridDim] block error maxima
+    // log / trace
+    cmx_step *log;
+    double *log_a, *log_mm;
+    int log_cap;
+    double *tr_t, *tr_a, *tr_mm;
+    int tr_cap;
+    long long timeout_ns;
+    int stage_only;                  // 1: evaluate stage 1 once (cmx_eval_rhs) and stop
+};
+
+}  // namespace cmx

@@ -1,0 +1,370 @@
+// Device code of one Dormand-Prince stage over the tiles of a masked grid (sm_103a).
+//
+// One stage S computes, for every magnetic cell,
+//   m_S  = m_n + h sum_{j<S} a_Sj k_j                      (stage combination, FP32)
+//   B    = exchange(m_S) + anisotropy + Zeeman + demag + inter-sublattice + B_rf(a_S)
+//   k_S  = -gamma/(1+alpha^2) [ m_S x B + alpha m_S x (m_S x B) ]      (LLG, Sec. II A)
+// and the block partial sums of the overlaps u_n (m_x - i m_y) (Eq. (18)).  Stage 7 also
+// writes the renormalised 5th-order point and the block maximum of |e_m|,
+// e_m = h sum_j E_j k_j.
+//
+// Tiles are columns of (WX-2) x (WY-2) cells, several planes deep; a block of WX x WY threads
+// covers a tile with its one-cell halo rim and marches through it plane by plane.  The raw
+// operands of the next planes arrive by asynchronous copies (cp.async) into shared memory while
+// the block combines the oldest plane into a ring of four planes of stage values and computes
+// the plane before it from planes p-1, p, p+1: one __syncthreads per plane, the 6-neighbour
+// stencil reads only shared memory.  Cells are stored compactly per (y, z) row between the first
+// and the last magnetic x of the row; the row table gives the offset.
+#pragma once
+
+#include "cmx_internal.cuh"
+
+namespace cmx {
+
+__device__ __forceinline__ unsigned long long global_timer_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned *p)
+{
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release(unsigned *p, unsigned v)
+{
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ int ld_volatile_int(const int *p)
+{
+    return *(const volatile int *)p;
+}
+
+// max that propagates NaN (a NaN error estimate must reach the controller)
+__device__ __forceinline__ float nanmax(float a, float b)
+{
+    return (a != a || b != b) ? __int_as_float(0x7fffffff) : fmaxf(a, b);
+}
+
+// Slopes read by stage S (1-based): those with a nonzero coupling, and at stage 7 also those
+// with a nonzero error weight.  Array 0 of a stage is m_n, arrays 1.. are these slopes.
+__host__ __device__ constexpr bool slope_used(int S, int j)
+{
+    return j < S - 1 && (dp_a(S - 1, j) != 0.0 || (S == 7 && dp_e(j) != 0.0));
+}
+
+__host__ __device__ constexpr int n_arrays(int S)
+{
+    int n = 1;
+    for (int j = 0; j < 6; j++) n += slope_used(S, j) ? 1 : 0;
+    return n;
+}
+
+__host__ __device__ constexpr int array_slope(int S, int a)
+{
+    int n = 0;
+    for (int j = 0; j < 6; j++)
+        if (slope_used(S, j)) {
+            n++;
+            if (n == a) return j;
+        }
+    return -1;
+}
+
+// Compensated FP32 pair ("double-float"): value = hi + lo, about 44 significant bits.  Used for
+// the overlap sums across threads and blocks; FP64 has a long dependent latency on this part.
+struct F2 {
+    float hi, lo;
+};
+
+__device__ __forceinline__ F2 f2_add(F2 a, F2 b)
+{
+    const float s = a.hi + b.hi;
+    const float v = s - a.hi;
+    float e = (a.hi - (s - v)) + (b.hi - v);   // exact rounding error of a.hi + b.hi
+    e += a.lo + b.lo;
+    const float hi = s + e;
+    return {hi, e - (hi - s)};
+}
+
+__device__ __forceinline__ F2 f2_shfl_xor(F2 a, int o)
+{
+    return {__shfl_xor_sync(0xffffffffu, a.hi, o), __shfl_xor_sync(0xffffffffu, a.lo, o)};
+}
+
+// Asynchronous 4-byte global -> shared copy (LDGSTS), its group commit and wait.
+__device__ __forceinline__ void cp_async4(void *smem, const void *gmem)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(s), "l"(gmem) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_commit()
+{
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+template <int N>
+__device__ __forceinline__ void cp_async_wait()
+{
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// Shared memory of a block whose threads cover a WX x WY window: the interior
+// (WX-2) x (WY-2) cells are computed, the one-cell rim is the halo.  D planes of raw operands
+// (m_n and the slopes of the stage) are in flight as asynchronous copies while the block
+// combines the oldest one into the ring of stage values and computes the plane before it.
+template <int NS, int WX, int WY, bool HU>
+struct StageSmem {
+    static constexpr int W = WX * WY;
+    static constexpr int NQ = NS * 3;
+    static constexpr int RING = 4;
+    static constexpr int D = NS == 1 ? 2 : 1;   // planes of raw operands in flight
+    static constexpr int NAMAX = 6;             // m_n + at most five slopes per stage
+    static constexpr int NU = HU ? MAXN : 1;    // profile slots (only with mode profiles)
+    float raw[D][NAMAX][NQ][W];   // raw operands of planes in flight
+    int ridx[D][W];               // their compact indices (-1: absent)
+    float uc[4][NU][W];           // mode profiles of interior cells, by plane mod 4
+    float v[RING][NQ + 1][W];     // stage values and presence (last row) of four planes
+    float es[2][NQ][W];           // stage 7: sum_{j<7} E_j k_j of the interior cells
+    int cidx[2][W];               // compact index of the interior cells (-1: absent)
+    F2 red[32][2 * MAXN];         // per-warp partial overlaps
+    float redmax[32];
+    const float *kp[7];           // physical slope buffers in logical order
+    int2 rows[MAX_TILE_PLANES][WY];   // row-table entries of the current tile's window rows
+};
+
+// Per-thread accumulators of one stage.
+struct Acc {
+    float re[MAXN], im[MAXN];
+    float emax;
+};
+
+// FP32 stage coefficients: cf[j] = h a_Sj, e[j] = E_j, h, and the feedback field per unit
+// profile of each mode, hrf[n] = (2/gamma) Re[g~_n a_{n,S}] (Eq. (5), (13)).
+struct Coef {
+    float cf[6];
+    float e[7];
+    float h;
+    float hrf[MAXN];
+};
+
+// Compact index of box cell x in a row given its row-table entry, or -1.
+__device__ __forceinline__ int row_index(const Ctx &c, int2 r, int x)
+{
+    const int xs = r.y & 0xffff, xe = (int)((unsigned)r.y >> 16);
+    if (x < xs || x >= xe) return -1;
+    const int idx = r.x + (x - xs);
+    if (c.active && !((__ldg(&c.active[idx >> 5]) >> (idx & 31)) & 1u)) return -1;
+    return idx;
+}
+
+__device__ __forceinline__ int2 row_entry(const Ctx &c, int y, int z)
+{
+    if ((unsigned)y >= (unsigned)c.ny || (unsigned)z >= (unsigned)c.nz) return make_int2(0, 0);
+    return __ldg(&c.rows[z * c.ny + y]);
+}
+
+// Issue the asynchronous copies of this thread's window position in plane q (and, for an
+// interior cell, its mode profiles), then commit one copy group (possibly empty).
+template <int NS, int WX, int WY, bool HU, int S>
+__device__ __forceinline__ void issue_plane(const Ctx &c, StageSmem<NS, WX, WY, HU> &sm,
+                                            const float *mn, int q, int np, int x, int r,
+                                            bool corner, bool inner_cell)
+{
+    constexpr int NQ = NS * 3, NA = n_arrays(S), D = StageSmem<NS, WX, WY, HU>::D;
+    const int i = threadIdx.x;
+    if (q < np) {
+        const int slot = q % D;
+        const int idx = corner ? -1 : row_index(c, sm.rows[q][r], x);
+        sm.ridx[slot][i] = idx;
+        if (idx >= 0) {
+#pragma unroll
+            for (int k = 0; k < NQ; k++) {
+                const size_t o = (size_t)k * c.ncell + idx;
+                cp_async4(&sm.raw[slot][0][k][i], mn + o);
+#pragma unroll
+                for (int a = 1; a < NA; a++)
+                    cp_async4(&sm.raw[slot][a][k][i], sm.kp[array_slope(S, a)] + o);
+            }
+            if (HU && inner_cell)
+                for (int n = 0; n < c.nmodes; n++)
+                    cp_async4(&sm.uc[q % 4][n][i], c.u + (size_t)n * c.ncell + idx);
+        }
+    }
+    cp_async_commit();
+}
+
+// Combine the raw operands of plane q (copied by this thread) into the stage value
+// m_S = m_n + sum_j (h a_Sj) k_j, and at stage 7 the partial error sum of interior cells.
+template <int NS, int WX, int WY, bool HU, int S>
+__device__ __forceinline__ void combine_plane(const Ctx &c, StageSmem<NS, WX, WY, HU> &sm,
+                                              const Coef &cf, int q, bool inner_cell)
+{
+    constexpr int NQ = NS * 3, NA = n_arrays(S), D = StageSmem<NS, WX, WY, HU>::D;
+    constexpr int R = StageSmem<NS, WX, WY, HU>::RING;
+    const int i = threadIdx.x;
+    const int rs = q % D, vs = q % R;
+    const int idx = sm.ridx[rs][i];
+    const bool here = idx >= 0;
+#pragma unroll
+    for (int k = 0; k < NQ; k++) {
+        float acc = 0.f, es = 0.f;
+        if (here) {
+            acc = sm.raw[rs][0][k][i];
+#pragma unroll
+            for (int a = 1; a < NA; a++) {
+                const int j = array_slope(S, a);
+                const float kj = sm.raw[rs][a][k][i];
+                if (dp_a(S - 1, j) != 0.0) acc = fmaf(cf.cf[j], kj, acc);
+                if (S == 7 && dp_e(j) != 0.0) es = fmaf(cf.e[j], kj, es);
+            }
+        }
+        sm.v[vs][k][i] = acc;
+        if (S == 7 && inner_cell) sm.es[q & 1][k][i] = es;
+    }
+    sm.v[vs][NQ][i] = here ? 1.f : 0.f;
+    sm.cidx[q & 1][i] = (inner_cell && here) ? idx : -1;
+}
+
+// RHS of this thread's interior cell of plane p (ring slots: p-1, p, p+1).  Writes k_S (and at
+// stage 7 the renormalised new m) and accumulates the overlap sums and the error maximum.
+template <int NS, int WX, int WY, bool HU, int S>
+__device__ __forceinline__ void compute_cell(const Ctx &c, StageSmem<NS, WX, WY, HU> &sm,
+                                             float *kout, float *mnew, const Coef &cf, int p,
+                                             Acc &acc)
+{
+    using SM = StageSmem<NS, WX, WY, HU>;
+    constexpr int NQ = SM::NQ, R = SM::RING;
+    const int i = threadIdx.x;
+    const int idx = sm.cidx[p & 1][i];
+    if (idx < 0) return;
+    const int sp = (p + R - 1) % R, sc = p % R, sn = (p + 1) % R;
+
+    const float nx_ = sm.v[sc][NQ][i - 1] + sm.v[sc][NQ][i + 1];
+    const float ny_ = sm.v[sc][NQ][i - WX] + sm.v[sc][NQ][i + WX];
+    const float nz_ = sm.v[sp][NQ][i] + sm.v[sn][NQ][i];
+
+    float m[NS][3], B[NS][3];
+#pragma unroll
+    for (int s = 0; s < NS; s++)
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            const int q = s * 3 + k;
+            const float cen = sm.v[sc][q][i];
+            m[s][k] = cen;
+            // exchange: sum over present neighbours of (m_j - m_i) / c_d^2 (absent ones hold 0)
+            B[s][k] = c.wx * (sm.v[sc][q][i - 1] + sm.v[sc][q][i + 1] - nx_ * cen) +
+                      c.wy * (sm.v[sc][q][i - WX] + sm.v[sc][q][i + WX] - ny_ * cen) +
+                      c.wz * (sm.v[sp][q][i] + sm.v[sn][q][i] - nz_ * cen);
+        }
+
+    float mt[3];
+#pragma unroll
+    for (int k = 0; k < 3; k++) mt[k] = (NS == 2) ? (m[0][k] + m[1][k]) : m[0][k];
+    // feedback field sum_n u_n (2/gamma) Re[g~_n a_n] and the overlap partial sums of the net
+    // moment (m1 + m2)/2 with the same profile values
+    const float hx = (NS == 2) ? 0.5f * mt[0] : mt[0];
+    const float hy = (NS == 2) ? 0.5f * mt[1] : mt[1];
+    float brf = 0.f;
+#pragma unroll
+    for (int n = 0; n < MAXN; n++) {
+        if (n < c.nmodes) {
+            const float un = HU ? sm.uc[p % 4][HU ? n : 0][i] : 1.f;
+            brf = fmaf(un, cf.hrf[n], brf);
+            acc.re[n] = fmaf(un, hx, acc.re[n]);
+            acc.im[n] = fmaf(-un, hy, acc.im[n]);
+        }
+    }
+
+#pragma unroll
+    for (int s = 0; s < NS; s++) {
+        const float mk = m[s][0] * c.ku[0] + m[s][1] * c.ku[1] + m[s][2] * c.ku[2];
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            float b = B[s][k] + c.anis * mk * c.ku[k] + c.B0[k] - c.dmg[k] * mt[k];
+            if (NS == 2) b -= c.BE * m[1 - s][k];
+            B[s][k] = b;
+        }
+        B[s][0] += brf;
+    }
+
+    // LLG torque, Landau-Lifshitz form
+#pragma unroll
+    for (int s = 0; s < NS; s++) {
+        const float *mm = m[s], *b = B[s];
+        const float t1x = mm[1] * b[2] - mm[2] * b[1];
+        const float t1y = mm[2] * b[0] - mm[0] * b[2];
+        const float t1z = mm[0] * b[1] - mm[1] * b[0];
+        const float t2x = mm[1] * t1z - mm[2] * t1y;
+        const float t2y = mm[2] * t1x - mm[0] * t1z;
+        const float t2z = mm[0] * t1y - mm[1] * t1x;
+        const float kv[3] = {c.pre * fmaf(c.alpha, t2x, t1x), c.pre * fmaf(c.alpha, t2y, t1y),
+                             c.pre * fmaf(c.alpha, t2z, t1z)};
+#pragma unroll
+        for (int k = 0; k < 3; k++) kout[(size_t)(s * 3 + k) * c.ncell + idx] = kv[k];
+        if (S == 7) {
+            const float r = rsqrtf(mm[0] * mm[0] + mm[1] * mm[1] + mm[2] * mm[2]);
+#pragma unroll
+            for (int k = 0; k < 3; k++) {
+                const int q = s * 3 + k;
+                mnew[(size_t)q * c.ncell + idx] = mm[k] * r;
+                const float e = cf.h * fmaf(cf.e[6], kv[k], sm.es[p & 1][q][i]);
+                acc.emax = nanmax(acc.emax, fabsf(e));
+            }
+        }
+    }
+}
+
+// All segments of this block for stage S (a contiguous range of the segment list, balanced by
+// plane count).  Segment t covers interior x in [x0, x0+WX-2), y in [y0, y0+WY-2) and
+// z in [z0, z1); the block's threads cover the window with its rim.
+// Plane q of a tile is z0-1+q, q = 0..np-1 (np = z1-z0+2, halo planes included).
+template <int NS, int WX, int WY, bool HU, int S>
+__device__ void stage_tiles(const Ctx &c, StageSmem<NS, WX, WY, HU> &sm, float *kout,
+                            const float *mn, float *mnew, const Coef &cf, Acc &acc)
+{
+    constexpr int D = StageSmem<NS, WX, WY, HU>::D;
+    const int r = threadIdx.x / WX, col = threadIdx.x - (threadIdx.x / WX) * WX;
+    const bool corner = (r == 0 || r == WY - 1) && (col == 0 || col == WX - 1);
+    const bool inner_pos = r >= 1 && r <= WY - 2 && col >= 1 && col <= WX - 2;
+    const int t_end = __ldg(&c.seg_begin[blockIdx.x + 1]);
+    for (int t = __ldg(&c.seg_begin[blockIdx.x]); t < t_end; t++) {
+        const int4 T = __ldg(&c.tiles[t]);
+        const int x = T.x - 1 + col, z0 = T.z, z1 = T.w;
+        const int np = z1 - z0 + 2;
+        auto inner = [&](int q) { return inner_pos && q >= 1 && q <= np - 2; };
+        __syncthreads();   // the previous tile may still read the shared buffers
+        // row-table entries of every window row of every plane of the tile, in one round
+        for (int k = threadIdx.x; k < np * WY; k += WX * WY)
+            sm.rows[k / WY][k % WY] = row_entry(c, T.y - 1 + k % WY, z0 - 1 + k / WY);
+        __syncthreads();
+        // prologue: D planes in flight, then planes 0 and 1 combined
+        int nq = 0;        // next plane to issue
+        for (; nq < D; nq++)
+            issue_plane<NS, WX, WY, HU, S>(c, sm, mn, nq, np, x, r, corner, inner(nq));
+        for (int q = 0; q < 2; q++) {
+            cp_async_wait<D - 1>();
+            combine_plane<NS, WX, WY, HU, S>(c, sm, cf, q, inner(q));
+            issue_plane<NS, WX, WY, HU, S>(c, sm, mn, nq, np, x, r, corner, inner(nq));
+            nq++;
+        }
+        for (int p = 1; p <= np - 2; p++) {
+            // plane p+1: its copies are the oldest in flight
+            cp_async_wait<D - 1>();
+            combine_plane<NS, WX, WY, HU, S>(c, sm, cf, p + 1, inner(p + 1));
+            issue_plane<NS, WX, WY, HU, S>(c, sm, mn, nq, np, x, r, corner, inner(nq));
+            nq++;
+            __syncthreads();
+            compute_cell<NS, WX, WY, HU, S>(c, sm, kout, mnew, cf, p, acc);
+        }
+        cp_async_wait<0>();
+    }
+}
+
+}  // namespace cmx

@@ -214,12 +214,13 @@ def multimode_sphere(T=10e-9, seed=2603, nx=128, ny=128, nz=64) -> Problem:
     g = TWO_PI * rng.uniform(20e6, 80e6, size=4)
     phi = rng.uniform(0.0, TWO_PI)
     f = np.array([4.8e9, 5.0e9, 5.2e9, 5.4e9])
-    return make_problem(nx, ny, nz, 5e-9, sphere_mask(nx, ny, nz), Ms=Ms, Aex=3.7e-12,
-                        alpha=1e-3, Ku=Ku, B0=(0, 0, B0), Nd=(1 / 3, 1 / 3, 1 / 3),
-                        omega=TWO_PI * f, kappa=np.full(4, TWO_PI * 2e6), g_re=g,
+    p = make_problem(nx, ny, nz, 5e-9, sphere_mask(nx, ny, nz), Ms=Ms, Aex=3.7e-12,
+                     alpha=1e-3, Ku=Ku, B0=(0, 0, B0), Nd=(1 / 3, 1 / 3, 1 / 3),
+                     omega=TWO_PI * f, kappa=np.full(4, TWO_PI * 2e6), g_re=g,
                         g_im=np.zeros(4), u=cos_profiles([0, 1, 2, 3], nx, ny, nz),
                         m0=tilted_state(1, nx, ny, nz, 1.0, phi), T=T,
                         name="multimode_sphere_128x128x64")
+    return p.replace(dt_max=stable_dt_max(p))
 
 
 def afm_params():
@@ -281,11 +282,32 @@ def adjoint_sphere(T=20e-9, n=64, seed=42) -> Problem:
     0.01, m = +z; profiles are random Fourier fields."""
     B0 = TWO_PI * 5e9 / GAMMA
     m0 = tilted_state(1, n, n, n, 0.0, 0.0)
-    return make_problem(n, n, n, 10e-9, sphere_mask(n, n, n), alpha=1e-3, B0=(0, 0, B0),
-                        Nd=(1 / 3, 1 / 3, 1 / 3), omega=TWO_PI * np.array([4.95e9, 5.20e9, 5.05e9]),
-                        kappa=[TWO_PI * 1e6] * 3, g_re=[TWO_PI * 50e6] * 3, g_im=[0.0] * 3,
-                        u=fourier_profiles(3, n, n, n, seed), m0=m0,
-                        a0=np.array([0.01, 0, 0], complex), T=T, name="adjoint_sphere_64^3")
+    p = make_problem(n, n, n, 10e-9, sphere_mask(n, n, n), alpha=1e-3, B0=(0, 0, B0),
+                     Nd=(1 / 3, 1 / 3, 1 / 3), omega=TWO_PI * np.array([4.95e9, 5.20e9, 5.05e9]),
+                     kappa=[TWO_PI * 1e6] * 3, g_re=[TWO_PI * 50e6] * 3, g_im=[0.0] * 3,
+                     u=fourier_profiles(3, n, n, n, seed), m0=m0,
+                     a0=np.array([0.01, 0, 0], complex), T=T, name="adjoint_sphere_64^3")
+    return p.replace(dt_max=stable_dt_max(p))
+
+
+def spectral_radius(p: Problem) -> float:
+    """Upper bound (rad/s) on the linear spin-wave frequencies of the LLG right-hand side: the
+    exchange Laplacian contributes at most (2A/Ms) sum_d 4/c_d^2; two sublattices add the
+    inter-sublattice field (omega <= gamma (B + B_A + lambda + B_E), Eq. (15)-(16))."""
+    lam = 2.0 * p.Aex / p.Ms * sum(4.0 / c ** 2 for c in (p.cx, p.cy, p.cz))
+    b = (float(np.linalg.norm(p.B0)) + abs(2.0 * p.Ku / p.Ms)
+         + MU0 * p.Ms * float(np.max(np.abs(p.Ndemag))) * p.nsub + lam)
+    if p.nsub == 2:
+        b += abs(p.BE)
+    return p.gamma / math.sqrt(1.0 + p.alpha ** 2) * b
+
+
+def stable_dt_max(p: Problem, y_max: float = 1.2) -> float:
+    """Step-size cap keeping every spin wave inside the Dormand-Prince stability region
+    (|R(z)| <= 1 up to |z| ~ 1.2 near the imaginary axis for alpha >= 1e-3).  Used whenever
+    the drive or the state is spatially non-uniform, so that exchange modes are never amplified
+    by accepted steps; exactly uniform problems do not excite them and keep dt_max = 1e-11."""
+    return min(p.dt_max, y_max / spectral_radius(p))
 
 
 def random_state(nsub, nx, ny, nz, seed, spread=0.3, afm=False) -> np.ndarray:

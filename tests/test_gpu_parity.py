@@ -1,0 +1,205 @@
+"""Parity of the CUDA integrator with the FP64 oracle (needs a B300).
+
+* single right-hand-side evaluations (one stage) on grids whose tiles are partly empty, with a
+  ragged tail in every direction, holes in the mask, two sublattices and up to 8 modes;
+* 1000 adaptive GPU steps replayed step for step by the oracle: max|dm| <= 2e-5 and
+  |da|/max|a| <= 1e-4;
+* the full-size workloads in their measured launch configuration on sampled outputs;
+* edge cases (one cell, no modes, every tile an edge tile), determinism, error statuses.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2603_03706_b300 import cmx
+from paper_2603_03706_b300 import workloads as W
+
+from gpu_util import TOL_A, TOL_M, f32_profiles, f32_state, masked, replay_compare, sim_for
+
+pytestmark = pytest.mark.gpu
+TP = 2 * math.pi
+
+
+def ragged_problem(nsub=1, nmodes=2, holes=False, seed=0):
+    nx, ny, nz = 37, 21, 11
+    mask = W.random_mask(nx, ny, nz, 0.8, seed) if holes else W.sphere_mask(nx, ny, nz, 19.0)
+    rng = np.random.default_rng(seed)
+    u = rng.uniform(-1, 1, (nmodes, nz, ny, nx)).astype(np.float32) if nmodes else None
+    kw = dict(omega=TP * rng.uniform(4.8e9, 5.2e9, nmodes), kappa=TP * rng.uniform(1e6, 5e6, nmodes),
+              g_re=TP * rng.uniform(20e6, 80e6, nmodes), g_im=TP * rng.uniform(-30e6, 30e6, nmodes),
+              u=u)
+    if nsub == 2:
+        p = W.make_problem(nx, ny, nz, 2e-9, mask, nsub=2, Ms=4e5, Aex=5e-12, alpha=2e-3, Ku=5e4,
+                           B0=(0, 0, 1.0), Nd=(0, 0, 1), BE=50.0, **kw)
+    else:
+        p = W.make_problem(nx, ny, nz, 5e-9, mask, Ku=-610.0, ku_axis=(0.6, 0.0, 0.8),
+                           B0=(0.01, 0, 0.187), Nd=(0.3, 0.3, 0.4), **kw)
+    m = W.random_state(nsub, nx, ny, nz, seed + 1, spread=0.2, afm=(nsub == 2))
+    a = (rng.normal(size=nmodes) + 1j * rng.normal(size=nmodes)) * 3e-3
+    p = p.replace(m0=m, a0=a)
+    # non-uniform drive and state: keep every exchange mode inside the stability region
+    return p.replace(dt_max=W.stable_dt_max(p))
+
+
+def rhs_compare(p, tiling=None):
+    p = f32_state(f32_profiles(p))
+    sim = sim_for(p, log_cap=0, tiling=tiling)
+    dm_g, da_g, mm_g = sim.eval_rhs(np.asarray(p.m0, np.float32), p.a0)
+    sim.close()
+    op = O.OracleProblem(p)
+    dm_o, da_o, mm_o = O.rhs(op, op.m0(), O.pack_a(p.a0))
+    dm_o = dm_o.reshape(p.nsub, 3, p.nz, p.ny, p.nx)
+    scale = np.abs(masked(p, dm_o)).max()
+    err_m = np.abs(masked(p, dm_g) - masked(p, dm_o)).max() / scale
+    outside = np.abs(dm_g.reshape(p.nsub, 3, -1)[:, :, p.mask.reshape(-1) == 0]).max(initial=0.0)
+    res = dict(err_m=err_m, outside=outside)
+    if p.nmodes:
+        mm_o = O.unpack_a(mm_o)
+        da_o = O.unpack_a(da_o)
+        res["err_mm"] = np.abs(mm_g - mm_o).max()
+        res["err_da"] = np.abs(da_g - da_o).max() / np.abs(da_o).max()
+    return res
+
+
+# ---------------------------------------------------------------------------------------------
+# one stage
+# ---------------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("tiling", [None, (32, 8, 3), (64, 4, 5), (32, 16, 11), (32, 8, 1)])
+def test_rhs_ferromagnet_ragged(tiling):
+    r = rhs_compare(ragged_problem(), tiling)
+    assert r["err_m"] < 2e-6, r
+    assert r["outside"] == 0.0
+    assert r["err_mm"] < 1e-7 and r["err_da"] < 1e-6, r
+
+
+def test_rhs_mask_with_holes_and_many_runs_per_row():
+    r = rhs_compare(ragged_problem(holes=True, nmodes=8, seed=3), (64, 4, 4))
+    assert r["err_m"] < 2e-6 and r["outside"] == 0.0, r
+    assert r["err_mm"] < 1e-7 and r["err_da"] < 1e-6, r
+
+
+def test_rhs_antiferromagnet_two_sublattices():
+    r = rhs_compare(ragged_problem(nsub=2, nmodes=2, seed=5), (32, 8, 4))
+    assert r["err_m"] < 2e-6, r
+    assert r["err_mm"] < 1e-7 and r["err_da"] < 1e-6, r
+
+
+def test_rhs_no_modes_single_cell():
+    p = W.make_problem(1, 1, 1, 5e-9, W.full_mask(1, 1, 1), B0=(0.02, 0, 0.2),
+                       m0=W.tilted_state(1, 1, 1, 1, 30.0, 0.4))
+    r = rhs_compare(p)
+    assert r["err_m"] < 1e-6
+
+
+# ---------------------------------------------------------------------------------------------
+# 1000 replayed steps
+# ---------------------------------------------------------------------------------------------
+
+def test_replay_single_sphere_1000_steps():
+    dm, da, info = replay_compare(W.single_sphere(), 1000)
+    assert info["stats"]["accepted"] >= 990
+    assert dm <= TOL_M and da <= TOL_A, (dm, da)
+
+
+def test_replay_ragged_multimode_1000_steps():
+    p = ragged_problem(nmodes=3, seed=11)
+    p = p.replace(m0=W.tilted_state(1, p.nx, p.ny, p.nz, 5.0, 0.3), a0=np.array([1e-3, 0, 0j]))
+    dm, da, info = replay_compare(p.replace(T=1e-6), 1000, tiling=(64, 4, 4))
+    assert dm <= TOL_M and da <= TOL_A, (dm, da)
+
+
+def test_replay_afm_complex_coupling_1000_steps():
+    p = ragged_problem(nsub=2, nmodes=2, seed=13)
+    m = W.tilted_state(2, p.nx, p.ny, p.nz, 1.0, 0.0, afm=True)
+    p = p.replace(m0=m, a0=np.zeros(2, complex), u=None, T=1e-6)
+    dm, da, info = replay_compare(p, 1000, tiling=(32, 8, 4))
+    assert dm <= TOL_M and da <= TOL_A, (dm, da)
+
+
+# ---------------------------------------------------------------------------------------------
+# full-size workloads in the measured configuration (sampled)
+# ---------------------------------------------------------------------------------------------
+
+def test_full_size_multimode_sphere_rhs_and_steps():
+    p = W.multimode_sphere()
+    r = rhs_compare(p)
+    assert r["err_m"] < 2e-6 and r["err_mm"] < 1e-7 and r["err_da"] < 1e-6, r
+    dm, da, info = replay_compare(p, 20)
+    assert dm <= TOL_M and da <= TOL_A, (dm, da)
+
+
+def test_full_size_afm_film_rhs():
+    p = W.afm_film()
+    r = rhs_compare(p.replace(m0=W.random_state(2, p.nx, p.ny, p.nz, 7, 0.1, afm=True)))
+    assert r["err_m"] < 2e-6 and r["err_mm"] < 1e-7 and r["err_da"] < 1e-6, r
+
+
+# ---------------------------------------------------------------------------------------------
+# properties
+# ---------------------------------------------------------------------------------------------
+
+def test_deterministic_bitwise():
+    p = f32_state(ragged_problem(seed=21).replace(T=1e-6))
+    outs = []
+    for _ in range(2):
+        sim = sim_for(p, log_cap=64)
+        sim.run(p.T, max_attempts=50)
+        outs.append((sim.get_m(), sim.get_a(), sim.get_log()["dt"]))
+        sim.close()
+    assert np.array_equal(outs[0][0], outs[1][0])
+    assert np.array_equal(outs[0][1], outs[1][1])
+    assert np.array_equal(outs[0][2], outs[1][2])
+
+
+def test_run_lands_on_T_and_resumes():
+    p = W.single_sphere(T=0.2e-9)
+    sim = sim_for(p, log_cap=0)
+    sim.set_launch_attempts(7)                  # many short launches
+    st = sim.run(0.1e-9)
+    assert st["t"] == pytest.approx(0.1e-9, abs=0) or abs(st["t"] - 0.1e-9) < 1e-24
+    st = sim.run(0.2e-9)
+    assert abs(st["t"] - 0.2e-9) < 1e-24
+    assert st["launches"] > 2
+    sim.close()
+
+
+def test_unit_norm_after_steps():
+    p = ragged_problem(seed=4).replace(T=1e-6)
+    sim = sim_for(p, log_cap=0)
+    sim.run(p.T, max_attempts=200)
+    m = masked(p, sim.get_m())
+    n = np.linalg.norm(m, axis=1)
+    assert np.abs(n - 1).max() < 1e-6
+    sim.close()
+
+
+def test_barrier_timeout_status_and_recovery():
+    """A block that leaves without arriving makes the others hit their wait limit: the run
+    returns CMX_ETIMEOUT, the context stays usable, set_state clears the error."""
+    p = ragged_problem(seed=8).replace(T=1e-6)
+    sim = sim_for(p, log_cap=0)
+    sim.set_timeout(1_000_000)                  # 1 ms
+    sim.debug_skip_arrival(0)
+    with pytest.raises(cmx.CmxError) as ei:
+        sim.run(p.T, max_attempts=10)
+    assert ei.value.code == cmx.ETIMEOUT
+    assert sim.status() == cmx.ETIMEOUT        # sticky
+    sim.set_state(p.m0, p.a0)
+    st = sim.run(p.T, max_attempts=10)
+    assert st["attempts"] == 10 and st["status"] == 0
+    sim.close()
+
+
+def test_nan_state_reports_enan():
+    p = ragged_problem(seed=9).replace(T=1e-6)
+    m = np.array(p.m0)
+    m[0, 0, 5, 10, 18] = np.nan
+    sim = sim_for(p, log_cap=0)
+    sim.set_state(m, p.a0)
+    with pytest.raises(cmx.CmxError) as ei:
+        sim.run(p.T, max_attempts=5)
+    assert ei.value.code == cmx.ENAN
+    sim.close()
