@@ -188,68 +188,108 @@ void build_layout(cmx_problem *h, const uint8_t *mask)
     h->holes = nmag != off;
 }
 
-// Columns of (wx-2) x (wy-2) interior cells (a wx x wy thread window with its one-cell rim)
-// and, for each, the range of planes [zlo, zhi) that hold magnetic cells of the column.
+// Columns of (wx-2) x (wy-2) interior cells (a wx x wy thread window with its one-cell rim):
+// the range of planes [zlo, zhi) that hold magnetic cells of the column, and per plane a work
+// weight (1: a plane iteration is latency-bound and costs about the same whatever its cells).
 struct Column {
     int x0, y0, zlo, zhi;
+    std::vector<float> w;   // weight of plane zlo + i
 };
 
 std::vector<Column> build_columns(const cmx_problem *h, int wx, int wy)
 {
     const int nx = h->grid.nx, ny = h->grid.ny, nz = h->grid.nz;
     const int bx = wx - 2, by = wy - 2;
+    auto count = [&](int x0, int x1, int y0, int y1, int z) {
+        int n = 0;
+        if (z < 0 || z >= nz) return 0;
+        for (int y = std::max(0, y0); y < std::min(ny, y1); y++) {
+            const int2 r = h->rows_h[(size_t)z * ny + y];
+            const int xs = r.y & 0xffff, xe = (int)((unsigned)r.y >> 16);
+            for (int x = std::max(xs, x0); x < std::min(xe, x1); x++) n += h->active_h[r.x + x - xs];
+        }
+        return n;
+    };
     std::vector<Column> out;
     for (int y0 = 0; y0 < ny; y0 += by)
         for (int x0 = 0; x0 < nx; x0 += bx) {
-            int zlo = -1, zhi = -1;
+            Column c{x0, y0, -1, -1, {}};
+            std::vector<float> w(nz);
             for (int z = 0; z < nz; z++) {
-                bool any = false;
-                for (int y = y0; y < std::min(ny, y0 + by) && !any; y++) {
-                    const int2 r = h->rows_h[(size_t)z * ny + y];
-                    const int xs = r.y & 0xffff, xe = (int)((unsigned)r.y >> 16);
-                    for (int x = std::max(xs, x0); x < std::min(xe, x0 + bx); x++)
-                        if (h->active_h[r.x + x - xs]) {
-                            any = true;
-                            break;
-                        }
+                const int inner = count(x0, x0 + bx, y0, y0 + by, z);
+                if (inner > 0) {
+                    if (c.zlo < 0) c.zlo = z;
+                    c.zhi = z + 1;
                 }
-                if (any) {
-                    if (zlo < 0) zlo = z;
-                    zhi = z + 1;
-                }
+                w[z] = 1.0f;   // a plane iteration costs about the same whatever its cells
             }
-            if (zlo >= 0) out.push_back({x0, y0, zlo, zhi});
+            if (c.zlo >= 0) {
+                c.w.assign(w.begin() + c.zlo, w.begin() + c.zhi);
+                out.push_back(std::move(c));
+            }
         }
     return out;
 }
 
-// Cut the columns into segments and give every block a contiguous run of segments with the
-// same number of planes (to within one); no segment is deeper than MAX_TILE_PLANES - 2.
-void build_segments(const std::vector<Column> &cols, int blocks, std::vector<int4> &segs,
-                    std::vector<int> &begin)
+// Greedy fill of blocks with capacity `cap` (plane weights plus two halo planes per segment):
+// each block takes planes of consecutive columns until the next plane would exceed its
+// capacity; columns are cut into segments at block boundaries and every MAX_TILE_PLANES - 2
+// planes.  Returns the number of blocks used (segments and block starts in segs / begin).
+int fill_blocks(const std::vector<Column> &cols, double cap, int max_blocks,
+                std::vector<int4> &segs, std::vector<int> &begin)
 {
-    long long P = 0;
-    for (const Column &c : cols) P += c.zhi - c.zlo;
     segs.clear();
-    begin.assign(blocks + 1, 0);
-    int b = 0;
-    long long done = 0;   // planes assigned to blocks < b
-    auto quota_end = [&](int blk) { return (P * (blk + 1) + blocks - 1) / blocks; };
-    long long pos = 0;    // planes emitted so far
+    begin.assign(1, 0);
+    double load = 0.0;
+    int nseg_block = 0;
     for (const Column &c : cols) {
         int z = c.zlo;
         while (z < c.zhi) {
-            while (b < blocks - 1 && pos >= quota_end(b)) begin[++b] = (int)segs.size();
-            const long long room = std::max<long long>(1, quota_end(b) - pos);
-            const int len = (int)std::min<long long>({(long long)(c.zhi - z), room,
-                                                      (long long)(MAX_TILE_PLANES - 2)});
+            // a new segment costs its two halo planes plus at least one plane
+            if (nseg_block > 0 && (load + 2.0 + c.w[z - c.zlo] > cap ||
+                                   nseg_block >= MAX_BLOCK_SEGMENTS)) {
+                begin.push_back((int)segs.size());
+                if ((int)begin.size() - 1 >= max_blocks) return max_blocks + 1;
+                load = 0.0;
+                nseg_block = 0;
+            }
+            load += 2.0;
+            int len = 0;
+            while (z + len < c.zhi && len < MAX_TILE_PLANES - 2 &&
+                   (len == 0 || load + c.w[z + len - c.zlo] <= cap)) {
+                load += c.w[z + len - c.zlo];
+                len++;
+            }
             segs.push_back(make_int4(c.x0, c.y0, z, z + len));
+            nseg_block++;
             z += len;
-            pos += len;
         }
     }
-    (void)done;
-    while (b < blocks) begin[++b] = (int)segs.size();
+    begin.push_back((int)segs.size());
+    return (int)begin.size() - 1;
+}
+
+// Smallest per-block capacity (binary search) whose greedy fill needs at most `blocks`
+// blocks; the partition then has no block above that capacity.
+void build_segments(const std::vector<Column> &cols, int blocks, std::vector<int4> &segs,
+                    std::vector<int> &begin)
+{
+    double total = 0.0, wmax = 0.0;
+    for (const Column &c : cols)
+        for (float v : c.w) {
+            total += v;
+            wmax = std::max(wmax, (double)v);
+        }
+    double lo = std::max(total / blocks, 2.0 + wmax), hi = total + 2.0 * (total + cols.size());
+    for (int it = 0; it < 60 && hi - lo > 0.5; it++) {
+        const double mid = 0.5 * (lo + hi);
+        if (fill_blocks(cols, mid, blocks, segs, begin) <= blocks)
+            hi = mid;
+        else
+            lo = mid;
+    }
+    fill_blocks(cols, hi, blocks, segs, begin);
+    while ((int)begin.size() < blocks + 1) begin.push_back((int)segs.size());
 }
 
 int setup_tiling(cmx_problem *h, const cmx_tiling *t)

@@ -10,8 +10,9 @@ namespace cmx {
 
 constexpr int MAXN = CMX_MAX_MODES;
 
-// Deepest tile (planes including the two halo planes) whose row entries fit shared memory.
+// Longest segment (planes including its two halo planes) and most segments per block.
 constexpr int MAX_TILE_PLANES = 66;
+constexpr int MAX_BLOCK_SEGMENTS = 64;
 
 // Dormand & Prince (1980) 5(4) coefficients, written from the published rationals.
 // dp_a(s, j): coupling of stage s+1 to slope j+1 (row 6 is the 5th-order solution, FSAL).

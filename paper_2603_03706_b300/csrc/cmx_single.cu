@@ -24,6 +24,7 @@ struct Local {
     const double *replay_dts;
     double mm[2 * MAXN], as[2 * MAXN];   // overlaps and cavity stage value of this stage
     double err_n[MAXN], amax_n[MAXN];    // per-mode error and amplitude (stage 7)
+    double mc[4 * MAXN];                 // mode constants: w, kappa, Re g~, Im g~
     unsigned bar_target;                 // arrival count that completes the next barrier
     int skip_block;
     int kphys[7];
@@ -107,11 +108,12 @@ __device__ void attempt_size(const Ctx &c, Local &L)
     }
 }
 
-// Cavity right-hand side (-i w - kappa) a + i g~ mm for one mode (Eq. (12), (19)).
-__device__ __forceinline__ void cavity_rhs(const Ctx &c, int n, double ar, double ai, double mr,
-                                           double mi, double &dr, double &di)
+// Cavity right-hand side (-i w - kappa) a + i g~ mm for one mode (Eq. (12), (19)); the mode
+// constants come from the block's shared copy (w, kappa, Re g~, Im g~).
+__device__ __forceinline__ void cavity_rhs(const double *mc, int n, double ar, double ai,
+                                           double mr, double mi, double &dr, double &di)
 {
-    const double w = c.omega[n], k = c.kappa[n], gr = c.gre[n], gi = c.gim[n];
+    const double w = mc[4 * n], k = mc[4 * n + 1], gr = mc[4 * n + 2], gi = mc[4 * n + 3];
     const double pr = gr * mr - gi * mi, pi = gr * mi + gi * mr;   // g~ <m^->
     dr = -k * ar + w * ai - pi;
     di = -k * ai - w * ar + pr;
@@ -130,8 +132,8 @@ __device__ void controller(const Ctx &c, Local &L, const double *sum, float emax
     __syncthreads();
     if (tid < N) {
         double dr, di;
-        cavity_rhs(c, tid, L.as[2 * tid], L.as[2 * tid + 1], L.mm[2 * tid], L.mm[2 * tid + 1],
-                   dr, di);
+        cavity_rhs(L.mc, tid, L.as[2 * tid], L.as[2 * tid + 1], L.mm[2 * tid],
+                   L.mm[2 * tid + 1], dr, di);
         L.ka[S - 1][2 * tid] = dr;
         L.ka[S - 1][2 * tid + 1] = di;
         if (S == 7) {
@@ -304,36 +306,40 @@ __device__ __forceinline__ void red_add_release(unsigned *p, unsigned v)
 
 // Fixed-order sum over all blocks of the overlap partials (compensated pairs) and max of the
 // error partials, done identically by every block after the barrier, so every block holds the
-// same values.
+// same values.  Thread t sums component q = t mod QP of blocks b = t/QP, t/QP + NT/QP, ...
+// (QP = 2N rounded up to a power of two); lanes of equal q are then combined by shuffles and
+// the warps in order.
 template <int NS, int WX, int WY, bool HU>
 __device__ void grid_reduce(const Ctx &c, StageSmem<NS, WX, WY, HU> &sm, double *out, float *emax)
 {
     constexpr int NT = WX * WY, NW = NT / 32;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int Q = 2 * c.nmodes, G = gridDim.x;
-    F2 s[2 * MAXN];
-#pragma unroll
-    for (int q = 0; q < 2 * MAXN; q++) s[q] = {0.f, 0.f};
-    float e = 0.f;
-    for (int b = threadIdx.x; b < G; b += NT) {
-        const float2 *pb = c.part + (size_t)b * Q;
-#pragma unroll
-        for (int q = 0; q < 2 * MAXN; q++)
-            if (q < Q) {
-                const float2 v = __ldcg(pb + q);
-                s[q] = f2_add(s[q], {v.x, v.y});
-            }
-        e = nanmax(e, __ldcg(c.errpart + b));
-    }
-#pragma unroll
-    for (int q = 0; q < 2 * MAXN; q++) {
-        if (q < Q) {
-            F2 v = s[q];
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) v = f2_add(v, f2_shfl_xor(v, o));
-            if (lane == 0) sm.red[warp][q] = v;
+    int QP = 1;
+    while (QP < Q) QP <<= 1;
+    const int q = threadIdx.x & (QP - 1), grp = threadIdx.x / QP, ngrp = NT / QP;
+    F2 s = {0.f, 0.f};
+    if (q < Q) {
+        int b = grp;
+        for (; b + 3 * ngrp < G; b += 4 * ngrp) {
+            const float2 v0 = __ldcg(c.part + (size_t)b * Q + q);
+            const float2 v1 = __ldcg(c.part + (size_t)(b + ngrp) * Q + q);
+            const float2 v2 = __ldcg(c.part + (size_t)(b + 2 * ngrp) * Q + q);
+            const float2 v3 = __ldcg(c.part + (size_t)(b + 3 * ngrp) * Q + q);
+            s = f2_add(s, {v0.x, v0.y});
+            s = f2_add(s, {v1.x, v1.y});
+            s = f2_add(s, {v2.x, v2.y});
+            s = f2_add(s, {v3.x, v3.y});
+        }
+        for (; b < G; b += ngrp) {
+            const float2 v = __ldcg(c.part + (size_t)b * Q + q);
+            s = f2_add(s, {v.x, v.y});
         }
     }
+    for (int o = 16; o >= QP; o >>= 1) s = f2_add(s, f2_shfl_xor(s, o));
+    if (lane < QP && lane < Q) sm.red[warp][lane] = s;
+    float e = 0.f;
+    for (int b = threadIdx.x; b < G; b += NT) e = nanmax(e, __ldcg(c.errpart + b));
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) e = nanmax(e, __shfl_xor_sync(0xffffffffu, e, o));
     if (lane == 0) sm.redmax[warp] = e;
@@ -391,12 +397,33 @@ __device__ bool grid_barrier(const Ctx &c, Local &L, int where)
     return s_ok > 0;
 }
 
+// Physical buffer of logical slope j (select rather than index the kernel-parameter array,
+// which keeps it out of local memory).
+__device__ __forceinline__ const float *slope_buffer(const Ctx &c, int kj)
+{
+    const float *p = c.k[0];
+#pragma unroll
+    for (int u = 1; u < 7; u++)
+        if (kj == u) p = c.k[u];
+    return p;
+}
+
+// One stage.  If `begun`, the copy pipeline of this stage was started by the previous stage
+// (right after its barrier).  After the barrier this stage starts the next one (S < 7) before
+// it reduces the partials and updates the cavity, so those latencies overlap the first copies.
 template <int NS, int WX, int WY, bool HU, int S>
 __device__ bool run_stage(const Ctx &c, StageSmem<NS, WX, WY, HU> &sm, Local &L, Coef &cf,
-                          double *s_sum, float *s_emax)
+                          double *s_sum, float *s_emax, Pipe &pp, bool begun)
 {
     const int tid = threadIdx.x, N = c.nmodes;
     const double h = L.h;
+    const float *mn = L.mcur ? c.m[1] : c.m[0];
+    float *mnew = L.mcur ? c.m[0] : c.m[1];
+    if (!begun) {
+        if (tid < 7) sm.kp[tid] = slope_buffer(c, L.kphys[tid]);
+        __syncthreads();
+        tiles_begin<NS, WX, WY, HU, S>(c, sm, mn, pp);
+    }
     // cavity stage value a_S = a_n + h sum_j a_Sj k^a_j (FP64, one thread per real component)
     if (tid < 2 * N) {
         double v = L.a[tid];
@@ -408,19 +435,19 @@ __device__ bool run_stage(const Ctx &c, StageSmem<NS, WX, WY, HU> &sm, Local &L,
     if (tid >= 32 && tid < 38) cf.cf[tid - 32] = (float)(h * (tid - 32 < S - 1 ? dp_a(S - 1, tid - 32) : 0.0));
     if (tid >= 64 && tid < 71) cf.e[tid - 64] = (float)dp_e(tid - 64);
     if (tid == 96) cf.h = (float)h;
-    if (tid >= 128 && tid < 135) sm.kp[tid - 128] = c.k[L.kphys[tid - 128]];
     __syncthreads();
     if (tid < N)
-        cf.hrf[tid] = (float)(c.two_over_gamma * (c.gre[tid] * L.as[2 * tid] -
-                                                  c.gim[tid] * L.as[2 * tid + 1]));
+        cf.hrf[tid] = (float)(c.two_over_gamma * (L.mc[4 * tid + 2] * L.as[2 * tid] -
+                                                  L.mc[4 * tid + 3] * L.as[2 * tid + 1]));
     __syncthreads();
     Acc acc;
 #pragma unroll
     for (int n = 0; n < MAXN; n++) acc.re[n] = acc.im[n] = 0.f;
     acc.emax = 0.f;
-    stage_tiles<NS, WX, WY, HU, S>(c, sm, c.k[L.kphys[S - 1]], c.m[L.mcur], c.m[L.mcur ^ 1], cf, acc);
+    tiles_run<NS, WX, WY, HU, S>(c, sm, (float *)sm.kp[S - 1], mn, mnew, cf, pp, acc);
     block_reduce<NS, WX, WY, HU>(c, sm, acc);
     if (!grid_barrier<NS, WX, WY, HU>(c, L, S)) return false;
+    if (S >= 2 && S < 7 && !c.stage_only) tiles_begin<NS, WX, WY, HU, (S < 7 ? S + 1 : 7)>(c, sm, mn, pp);
     grid_reduce<NS, WX, WY, HU>(c, sm, s_sum, s_emax);
     controller<S>(c, L, s_sum, *s_emax);
     __syncthreads();
@@ -445,8 +472,30 @@ __global__ void __launch_bounds__(WX *WY, (MinBlocks<NS, WX * WY>::value)) run_k
     __shared__ float s_emax;
     __shared__ int s_stop;
     if (threadIdx.x == 0) load_local(c, L);
+    if (threadIdx.x < c.nmodes) {
+        const int n = threadIdx.x;
+        double w = c.omega[0], ka = c.kappa[0], gr = c.gre[0], gi = c.gim[0];
+#pragma unroll
+        for (int u = 1; u < MAXN; u++)
+            if (n == u) {
+                w = c.omega[u];
+                ka = c.kappa[u];
+                gr = c.gre[u];
+                gi = c.gim[u];
+            }
+        L.mc[4 * n] = w;
+        L.mc[4 * n + 1] = ka;
+        L.mc[4 * n + 2] = gr;
+        L.mc[4 * n + 3] = gi;
+    }
+    {
+        const int sb = __ldg(&c.seg_begin[blockIdx.x]), se = __ldg(&c.seg_begin[blockIdx.x + 1]);
+        if (threadIdx.x == 0) sm.nseg = se - sb;
+        for (int t = threadIdx.x; t < se - sb; t += WX * WY) sm.seg[t] = __ldg(&c.tiles[sb + t]);
+    }
     __syncthreads();
     bool ok = true;
+    Pipe pp;
     for (;;) {
         if (threadIdx.x == 0) {
             s_stop = L.status != 0 || L.done || ld_volatile_int(&c.ctl->status) != 0 ||
@@ -456,15 +505,16 @@ __global__ void __launch_bounds__(WX *WY, (MinBlocks<NS, WX * WY>::value)) run_k
         __syncthreads();
         if (s_stop) break;
         if (!L.k1_valid) {
-            if (!(ok = run_stage<NS, WX, WY, HU, 1>(c, sm, L, cf, s_sum, &s_emax))) break;
+            if (!(ok = run_stage<NS, WX, WY, HU, 1>(c, sm, L, cf, s_sum, &s_emax, pp, false)))
+                break;
             if (c.stage_only) break;
         }
-        if (!(ok = run_stage<NS, WX, WY, HU, 2>(c, sm, L, cf, s_sum, &s_emax))) break;
-        if (!(ok = run_stage<NS, WX, WY, HU, 3>(c, sm, L, cf, s_sum, &s_emax))) break;
-        if (!(ok = run_stage<NS, WX, WY, HU, 4>(c, sm, L, cf, s_sum, &s_emax))) break;
-        if (!(ok = run_stage<NS, WX, WY, HU, 5>(c, sm, L, cf, s_sum, &s_emax))) break;
-        if (!(ok = run_stage<NS, WX, WY, HU, 6>(c, sm, L, cf, s_sum, &s_emax))) break;
-        if (!(ok = run_stage<NS, WX, WY, HU, 7>(c, sm, L, cf, s_sum, &s_emax))) break;
+        if (!(ok = run_stage<NS, WX, WY, HU, 2>(c, sm, L, cf, s_sum, &s_emax, pp, false))) break;
+        if (!(ok = run_stage<NS, WX, WY, HU, 3>(c, sm, L, cf, s_sum, &s_emax, pp, true))) break;
+        if (!(ok = run_stage<NS, WX, WY, HU, 4>(c, sm, L, cf, s_sum, &s_emax, pp, true))) break;
+        if (!(ok = run_stage<NS, WX, WY, HU, 5>(c, sm, L, cf, s_sum, &s_emax, pp, true))) break;
+        if (!(ok = run_stage<NS, WX, WY, HU, 6>(c, sm, L, cf, s_sum, &s_emax, pp, true))) break;
+        if (!(ok = run_stage<NS, WX, WY, HU, 7>(c, sm, L, cf, s_sum, &s_emax, pp, true))) break;
     }
     if (ok && blockIdx.x == 0 && threadIdx.x == 0) store_local(c, L);
 }
@@ -503,7 +553,7 @@ static int occupancy_variant()
 // Compiled block windows (with and without mode profiles): four for one sublattice, the
 // 256-thread ones for two (larger two-sublattice windows would not leave room for two blocks).
 #define CMX_VARIANTS(X) \
-    X(1, 32, 8) X(1, 32, 16) X(1, 64, 4) X(2, 32, 8) X(2, 64, 4)
+    X(1, 32, 8) X(1, 32, 16) X(1, 64, 4) X(2, 32, 8) X(2, 32, 16) X(2, 64, 4)
 
 bool tile_shape_supported(int nsub, int bx, int by)
 {

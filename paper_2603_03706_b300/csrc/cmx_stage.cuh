@@ -124,20 +124,56 @@ struct StageSmem {
     static constexpr int W = WX * WY;
     static constexpr int NQ = NS * 3;
     static constexpr int RING = 4;
-    static constexpr int D = NS == 1 ? 2 : 1;   // planes of raw operands in flight
     static constexpr int NAMAX = 6;             // m_n + at most five slopes per stage
-    static constexpr int NU = HU ? MAXN : 1;    // profile slots (only with mode profiles)
-    float raw[D][NAMAX][NQ][W];   // raw operands of planes in flight
-    int ridx[D][W];               // their compact indices (-1: absent)
-    float uc[4][NU][W];           // mode profiles of interior cells, by plane mod 4
+    static constexpr int POOL = (NS == 1 ? 2 : 1) * NAMAX * NQ * W;   // raw operand floats
+    static constexpr int DMAX = 4;
+    // Planes in flight at stage S: as many plane slots of n_arrays(S) x NQ x W floats as the
+    // pool holds (at most 4).
+    template <int S>
+    __host__ __device__ static constexpr int depth()
+    {
+        const int d = POOL / (n_arrays(S) * NQ * W);
+        return d < 1 ? 1 : (d > DMAX ? DMAX : d);
+    }
+    float raw[POOL];              // raw operands of planes in flight, [slot][array][q][W]
+    int ridx[DMAX][W];            // their compact indices (-1: absent)
     float v[RING][NQ + 1][W];     // stage values and presence (last row) of four planes
     float es[2][NQ][W];           // stage 7: sum_{j<7} E_j k_j of the interior cells
     int cidx[2][W];               // compact index of the interior cells (-1: absent)
     F2 red[32][2 * MAXN];         // per-warp partial overlaps
     float redmax[32];
     const float *kp[7];           // physical slope buffers in logical order
-    int2 rows[MAX_TILE_PLANES][WY];   // row-table entries of the current tile's window rows
+    int2 rows[8][WY];             // row-table entries of the window rows, by plane mod 8
+    int4 seg[MAX_BLOCK_SEGMENTS]; // this block's segments (x0, y0, z0, z1)
+    int nseg;
 };
+
+// Position of a cursor in a block's stream of planes: segment t, whose first plane is stream
+// position `off`; the segment has np = z1 - z0 + 2 planes (z0-1 .. z1).
+struct Cursor {
+    int t, off, np, x0, y0, z0;
+};
+
+template <class SM>
+__device__ __forceinline__ void cursor_seek(const SM &sm, Cursor &cu, int g)
+{
+    while (g >= cu.off + cu.np && cu.t + 1 < sm.nseg) {
+        cu.off += cu.np;
+        cu.t++;
+        const int4 T = sm.seg[cu.t];
+        cu.x0 = T.x;
+        cu.y0 = T.y;
+        cu.z0 = T.z;
+        cu.np = T.w - T.z + 2;
+    }
+}
+
+template <class SM>
+__device__ __forceinline__ Cursor cursor_start(const SM &sm)
+{
+    const int4 T = sm.seg[0];
+    return Cursor{0, 0, T.w - T.z + 2, T.x, T.y, T.z};
+}
 
 // Per-thread accumulators of one stage.
 struct Acc {
@@ -170,66 +206,69 @@ __device__ __forceinline__ int2 row_entry(const Ctx &c, int y, int z)
     return __ldg(&c.rows[z * c.ny + y]);
 }
 
-// Issue the asynchronous copies of this thread's window position in plane q (and, for an
-// interior cell, its mode profiles), then commit one copy group (possibly empty).
+// Issue the asynchronous copies of this thread's window position in stream plane g, then
+// commit one copy group (possibly empty).
 template <int NS, int WX, int WY, bool HU, int S>
 __device__ __forceinline__ void issue_plane(const Ctx &c, StageSmem<NS, WX, WY, HU> &sm,
-                                            const float *mn, int q, int np, int x, int r,
-                                            bool corner, bool inner_cell)
+                                            const float *mn, int g, int gend, const Cursor &cu,
+                                            int r, int col, bool corner, bool inner_pos)
 {
-    constexpr int NQ = NS * 3, NA = n_arrays(S), D = StageSmem<NS, WX, WY, HU>::D;
+    using SM = StageSmem<NS, WX, WY, HU>;
+    constexpr int NQ = NS * 3, NA = n_arrays(S), D = SM::template depth<S>();
+    constexpr int W = SM::W;
     const int i = threadIdx.x;
-    if (q < np) {
-        const int slot = q % D;
-        const int idx = corner ? -1 : row_index(c, sm.rows[q][r], x);
+    if (g < gend) {
+        const int slot = g % D;
+        float *rp = sm.raw + (size_t)slot * NA * NQ * W;
+        const int q = g - cu.off;
+        const int idx = corner ? -1 : row_index(c, sm.rows[g & 7][r], cu.x0 - 1 + col);
         sm.ridx[slot][i] = idx;
         if (idx >= 0) {
 #pragma unroll
             for (int k = 0; k < NQ; k++) {
                 const size_t o = (size_t)k * c.ncell + idx;
-                cp_async4(&sm.raw[slot][0][k][i], mn + o);
+                cp_async4(rp + (0 * NQ + k) * W + i, mn + o);
 #pragma unroll
                 for (int a = 1; a < NA; a++)
-                    cp_async4(&sm.raw[slot][a][k][i], sm.kp[array_slope(S, a)] + o);
+                    cp_async4(rp + (a * NQ + k) * W + i, sm.kp[array_slope(S, a)] + o);
             }
-            if (HU && inner_cell)
-                for (int n = 0; n < c.nmodes; n++)
-                    cp_async4(&sm.uc[q % 4][n][i], c.u + (size_t)n * c.ncell + idx);
         }
     }
     cp_async_commit();
 }
 
-// Combine the raw operands of plane q (copied by this thread) into the stage value
+// Combine the raw operands of stream plane g (copied by this thread) into the stage value
 // m_S = m_n + sum_j (h a_Sj) k_j, and at stage 7 the partial error sum of interior cells.
 template <int NS, int WX, int WY, bool HU, int S>
 __device__ __forceinline__ void combine_plane(const Ctx &c, StageSmem<NS, WX, WY, HU> &sm,
-                                              const Coef &cf, int q, bool inner_cell)
+                                              const Coef &cf, int g, bool inner_cell)
 {
-    constexpr int NQ = NS * 3, NA = n_arrays(S), D = StageSmem<NS, WX, WY, HU>::D;
-    constexpr int R = StageSmem<NS, WX, WY, HU>::RING;
+    using SM = StageSmem<NS, WX, WY, HU>;
+    constexpr int NQ = NS * 3, NA = n_arrays(S), D = SM::template depth<S>();
+    constexpr int R = SM::RING, W = SM::W;
     const int i = threadIdx.x;
-    const int rs = q % D, vs = q % R;
+    const int rs = g % D, vs = g % R;
+    const float *rp = sm.raw + (size_t)rs * NA * NQ * W;
     const int idx = sm.ridx[rs][i];
     const bool here = idx >= 0;
 #pragma unroll
     for (int k = 0; k < NQ; k++) {
         float acc = 0.f, es = 0.f;
         if (here) {
-            acc = sm.raw[rs][0][k][i];
+            acc = rp[(0 * NQ + k) * W + i];
 #pragma unroll
             for (int a = 1; a < NA; a++) {
                 const int j = array_slope(S, a);
-                const float kj = sm.raw[rs][a][k][i];
+                const float kj = rp[(a * NQ + k) * W + i];
                 if (dp_a(S - 1, j) != 0.0) acc = fmaf(cf.cf[j], kj, acc);
                 if (S == 7 && dp_e(j) != 0.0) es = fmaf(cf.e[j], kj, es);
             }
         }
         sm.v[vs][k][i] = acc;
-        if (S == 7 && inner_cell) sm.es[q & 1][k][i] = es;
+        if (S == 7 && inner_cell) sm.es[g & 1][k][i] = es;
     }
     sm.v[vs][NQ][i] = here ? 1.f : 0.f;
-    sm.cidx[q & 1][i] = (inner_cell && here) ? idx : -1;
+    sm.cidx[g & 1][i] = (inner_cell && here) ? idx : -1;
 }
 
 // RHS of this thread's interior cell of plane p (ring slots: p-1, p, p+1).  Writes k_S (and at
@@ -237,7 +276,7 @@ __device__ __forceinline__ void combine_plane(const Ctx &c, StageSmem<NS, WX, WY
 template <int NS, int WX, int WY, bool HU, int S>
 __device__ __forceinline__ void compute_cell(const Ctx &c, StageSmem<NS, WX, WY, HU> &sm,
                                              float *kout, float *mnew, const Coef &cf, int p,
-                                             Acc &acc)
+                                             const float *ucell, Acc &acc)
 {
     using SM = StageSmem<NS, WX, WY, HU>;
     constexpr int NQ = SM::NQ, R = SM::RING;
@@ -275,7 +314,7 @@ __device__ __forceinline__ void compute_cell(const Ctx &c, StageSmem<NS, WX, WY,
 #pragma unroll
     for (int n = 0; n < MAXN; n++) {
         if (n < c.nmodes) {
-            const float un = HU ? sm.uc[p % 4][HU ? n : 0][i] : 1.f;
+            const float un = HU ? ucell[n] : 1.f;
             brf = fmaf(un, cf.hrf[n], brf);
             acc.re[n] = fmaf(un, hx, acc.re[n]);
             acc.im[n] = fmaf(-un, hy, acc.im[n]);
@@ -321,50 +360,110 @@ __device__ __forceinline__ void compute_cell(const Ctx &c, StageSmem<NS, WX, WY,
     }
 }
 
-// All segments of this block for stage S (a contiguous range of the segment list, balanced by
-// plane count).  Segment t covers interior x in [x0, x0+WX-2), y in [y0, y0+WY-2) and
-// z in [z0, z1); the block's threads cover the window with its rim.
-// Plane q of a tile is z0-1+q, q = 0..np-1 (np = z1-z0+2, halo planes included).
+// Copy-pipeline state of one stage: cursors for row loading (cr), copy issue (ci) and combine
+// (cc), the next plane to issue and the stream length.
+struct Pipe {
+    Cursor cr, ci, cc;
+    int nq, gend;
+};
+
+// Start stage S's stream: row entries of the first planes and the first D planes of copies.
+// Needs only m_n and the slopes of earlier stages, so it can run before the cavity update of
+// the previous stage is known.  Planes of the block's segments: segment t covers interior x in
+// [x0, x0+WX-2), y in [y0, y0+WY-2), z in [z0, z1) and contributes planes z0-1 .. z1.
 template <int NS, int WX, int WY, bool HU, int S>
-__device__ void stage_tiles(const Ctx &c, StageSmem<NS, WX, WY, HU> &sm, float *kout,
-                            const float *mn, float *mnew, const Coef &cf, Acc &acc)
+__device__ void tiles_begin(const Ctx &c, StageSmem<NS, WX, WY, HU> &sm, const float *mn,
+                            Pipe &pp)
 {
-    constexpr int D = StageSmem<NS, WX, WY, HU>::D;
+    constexpr int D = StageSmem<NS, WX, WY, HU>::template depth<S>();
+    constexpr int AHEAD = D + 3;   // row entries are loaded this many planes ahead (ring of 8)
+    pp.gend = 0;
+    for (int t = 0; t < sm.nseg; t++) pp.gend += sm.seg[t].w - sm.seg[t].z + 2;
+    pp.nq = 0;
+    if (sm.nseg == 0) return;
     const int r = threadIdx.x / WX, col = threadIdx.x - (threadIdx.x / WX) * WX;
     const bool corner = (r == 0 || r == WY - 1) && (col == 0 || col == WX - 1);
     const bool inner_pos = r >= 1 && r <= WY - 2 && col >= 1 && col <= WX - 2;
-    const int t_end = __ldg(&c.seg_begin[blockIdx.x + 1]);
-    for (int t = __ldg(&c.seg_begin[blockIdx.x]); t < t_end; t++) {
-        const int4 T = __ldg(&c.tiles[t]);
-        const int x = T.x - 1 + col, z0 = T.z, z1 = T.w;
-        const int np = z1 - z0 + 2;
-        auto inner = [&](int q) { return inner_pos && q >= 1 && q <= np - 2; };
-        __syncthreads();   // the previous tile may still read the shared buffers
-        // row-table entries of every window row of every plane of the tile, in one round
-        for (int k = threadIdx.x; k < np * WY; k += WX * WY)
-            sm.rows[k / WY][k % WY] = row_entry(c, T.y - 1 + k % WY, z0 - 1 + k / WY);
-        __syncthreads();
-        // prologue: D planes in flight, then planes 0 and 1 combined
-        int nq = 0;        // next plane to issue
-        for (; nq < D; nq++)
-            issue_plane<NS, WX, WY, HU, S>(c, sm, mn, nq, np, x, r, corner, inner(nq));
-        for (int q = 0; q < 2; q++) {
-            cp_async_wait<D - 1>();
-            combine_plane<NS, WX, WY, HU, S>(c, sm, cf, q, inner(q));
-            issue_plane<NS, WX, WY, HU, S>(c, sm, mn, nq, np, x, r, corner, inner(nq));
-            nq++;
+    pp.cr = cursor_start(sm);
+    pp.ci = pp.cr;
+    pp.cc = pp.cr;
+    __syncthreads();   // the previous stage may still read the shared buffers
+    for (int g = 0; g <= AHEAD; g++)
+        if (threadIdx.x < WY && g < pp.gend) {
+            cursor_seek(sm, pp.cr, g);
+            sm.rows[g & 7][threadIdx.x] =
+                row_entry(c, pp.cr.y0 - 1 + threadIdx.x, pp.cr.z0 - 1 + (g - pp.cr.off));
         }
-        for (int p = 1; p <= np - 2; p++) {
-            // plane p+1: its copies are the oldest in flight
-            cp_async_wait<D - 1>();
-            combine_plane<NS, WX, WY, HU, S>(c, sm, cf, p + 1, inner(p + 1));
-            issue_plane<NS, WX, WY, HU, S>(c, sm, mn, nq, np, x, r, corner, inner(nq));
-            nq++;
-            __syncthreads();
-            compute_cell<NS, WX, WY, HU, S>(c, sm, kout, mnew, cf, p, acc);
-        }
-        cp_async_wait<0>();
+    __syncthreads();
+    for (; pp.nq < D; pp.nq++) {
+        cursor_seek(sm, pp.ci, pp.nq);
+        issue_plane<NS, WX, WY, HU, S>(c, sm, mn, pp.nq, pp.gend, pp.ci, r, col, corner,
+                                       inner_pos);
     }
+}
+
+// Run stage S's stream to its end: combine the oldest plane in flight, issue the next, compute
+// the plane before it.  Only planes interior to their segment are computed; the profiles of
+// the next computed cell are loaded one plane ahead.
+template <int NS, int WX, int WY, bool HU, int S>
+__device__ void tiles_run(const Ctx &c, StageSmem<NS, WX, WY, HU> &sm, float *kout,
+                          const float *mn, float *mnew, const Coef &cf, Pipe &pp, Acc &acc)
+{
+    constexpr int D = StageSmem<NS, WX, WY, HU>::template depth<S>();
+    constexpr int AHEAD = D + 3;
+    const int gend = pp.gend;
+    if (sm.nseg == 0) return;
+    const int r = threadIdx.x / WX, col = threadIdx.x - (threadIdx.x / WX) * WX;
+    const bool corner = (r == 0 || r == WY - 1) && (col == 0 || col == WX - 1);
+    const bool inner_pos = r >= 1 && r <= WY - 2 && col >= 1 && col <= WX - 2;
+    auto load_rows = [&](int g) {   // rows of stream plane g into ring slot g mod 8
+        if (threadIdx.x < WY && g < gend) {
+            cursor_seek(sm, pp.cr, g);
+            sm.rows[g & 7][threadIdx.x] =
+                row_entry(c, pp.cr.y0 - 1 + threadIdx.x, pp.cr.z0 - 1 + (g - pp.cr.off));
+        }
+    };
+    auto inner_at = [&](const Cursor &cu, int g) {
+        const int q = g - cu.off;
+        return inner_pos && q >= 1 && q <= cu.np - 2;
+    };
+    float ucur[MAXN], unext[MAXN];
+#pragma unroll
+    for (int n = 0; n < MAXN; n++) ucur[n] = unext[n] = 1.f;
+    auto load_u = [&](int g, float *dst) {   // profiles of this thread's cell of plane g
+        if (!HU) return;
+        const int idx = sm.cidx[g & 1][threadIdx.x];
+#pragma unroll
+        for (int n = 0; n < MAXN; n++)
+            if (n < c.nmodes && idx >= 0) dst[n] = __ldg(c.u + (size_t)n * c.ncell + idx);
+    };
+    for (int g = 0; g < 2 && g < gend; g++) {
+        cp_async_wait<D - 1>();
+        cursor_seek(sm, pp.cc, g);
+        combine_plane<NS, WX, WY, HU, S>(c, sm, cf, g, inner_at(pp.cc, g));
+        cursor_seek(sm, pp.ci, pp.nq);
+        issue_plane<NS, WX, WY, HU, S>(c, sm, mn, pp.nq, gend, pp.ci, r, col, corner,
+                                       inner_pos);
+        pp.nq++;
+    }
+    load_u(1, unext);
+    for (int p = 1; p <= gend - 2; p++) {
+        load_rows(p + AHEAD);
+        // plane p+1: its copies are the oldest in flight
+        cp_async_wait<D - 1>();
+        cursor_seek(sm, pp.cc, p + 1);
+        combine_plane<NS, WX, WY, HU, S>(c, sm, cf, p + 1, inner_at(pp.cc, p + 1));
+        cursor_seek(sm, pp.ci, pp.nq);
+        issue_plane<NS, WX, WY, HU, S>(c, sm, mn, pp.nq, gend, pp.ci, r, col, corner,
+                                       inner_pos);
+        pp.nq++;
+#pragma unroll
+        for (int n = 0; n < MAXN; n++) ucur[n] = unext[n];
+        load_u(p + 1, unext);
+        __syncthreads();
+        compute_cell<NS, WX, WY, HU, S>(c, sm, kout, mnew, cf, p, ucur, acc);
+    }
+    cp_async_wait<0>();
 }
 
 }  // namespace cmx
