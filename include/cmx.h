@@ -191,6 +191,70 @@ int cmx_get_tiling(const cmx_problem *h, int *bx, int *by, int *bz, int *blocks,
 const char *cmx_last_error(const cmx_problem *h);
 const char *cmx_status_string(int status);
 
+/* ------------------------------------------------------------------------------------------
+ * Batched form: many independent problems (e.g. a field sweep across the anticrossing, Sec.
+ * IV A, or a cooperativity sweep, Sec. IV C) advanced by ONE persistent launch.  Each instance
+ * has its own grid, mask, material, modes, end time, adaptive step size, controller, log and
+ * trace.  The launch's blocks form teams of equal size; each team integrates the instances of
+ * its queue one after the other (longest first, queues balanced by cell count), with a barrier
+ * counter of its own instead of a grid-wide barrier.  All instances must share nsub and use
+ * uniform mode profiles (modes.u = NULL).
+ * ---------------------------------------------------------------------------------------- */
+typedef struct cmx_batch cmx_batch;
+
+/* One instance: grid, host mask, material, modes (u must be NULL), optional host initial state
+ * (m0: dense box [nsub][3][nbox] float32, NULL = +z / -z; a0: 2N doubles, NULL = 0) and the
+ * end time T of its integration. */
+typedef struct {
+    cmx_grid grid;
+    const uint8_t *mask;
+    cmx_material mat;
+    cmx_modes modes;
+    const float *m0;
+    const double *a0;
+    double T;
+} cmx_instance;
+
+/* bx, by: block window (as cmx_tiling; 0 = 32x8).  team: blocks per team (0 = smallest power of
+ * two for which the largest instance fits the average team load).  blocks_per_sm: cap (0 = as
+ * many as fit).  use_graph: capture each launch in a CUDA graph and replay it (1) or launch
+ * directly (0). */
+typedef struct {
+    int bx, by;
+    int team;
+    int blocks_per_sm;
+    int use_graph;
+} cmx_batch_config;
+
+/* Create a batch of n instances sharing the solver settings (log_cap / trace_cap apply per
+ * instance).  Copies everything; owns all device memory.  CMX_EINVAL on an empty mask, mixed
+ * nsub, non-NULL profiles, n <= 0. */
+int cmx_batch_create(const cmx_instance *inst, int n, const cmx_solver *solver,
+                     const cmx_batch_config *cfg, void *stream, cmx_batch **out);
+int cmx_batch_destroy(cmx_batch *b);
+
+/* Enqueue ONE launch in which every unfinished instance makes up to n_attempts attempts. */
+int cmx_batch_launch(cmx_batch *b, int n_attempts);
+
+/* Launch until every instance has reached its T (or failed), at most max_attempts attempts per
+ * instance (<= 0: no limit); *total sums the counters over instances (t = smallest t).  Returns
+ * the first instance error, if any. */
+int cmx_batch_run(cmx_batch *b, long long max_attempts, cmx_stats *total);
+
+/* Per-instance results (host pointers), same layouts as the single-problem calls. */
+int cmx_batch_stats(cmx_batch *b, int i, cmx_stats *st);
+int cmx_batch_get_a(cmx_batch *b, int i, double *a);
+int cmx_batch_get_m(cmx_batch *b, int i, float *m);
+int cmx_batch_get_log(cmx_batch *b, int i, cmx_step *dst, double *a, double *mm, int cap,
+                      long long *n);
+int cmx_batch_get_trace(cmx_batch *b, int i, double *t, double *a, double *mm, int cap,
+                        long long *n);
+
+/* Launch shape: teams, blocks per team, total blocks, total magnetic cells, graph in use. */
+int cmx_batch_info(const cmx_batch *b, int *teams, int *team_size, int *blocks,
+                   long long *cells, int *graph);
+const char *cmx_batch_last_error(const cmx_batch *b);
+
 #ifdef __cplusplus
 }
 #endif

@@ -62,6 +62,16 @@ class Stats(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class Instance(C.Structure):
+    _fields_ = [("grid", Grid), ("mask", C.c_void_p), ("mat", Material), ("modes", Modes),
+                ("m0", C.c_void_p), ("a0", C.c_void_p), ("T", C.c_double)]
+
+
+class BatchConfig(C.Structure):
+    _fields_ = [("bx", C.c_int), ("by", C.c_int), ("team", C.c_int), ("blocks_per_sm", C.c_int),
+                ("use_graph", C.c_int)]
+
+
 class Step(C.Structure):
     _fields_ = [("t", C.c_double), ("dt", C.c_double), ("err", C.c_double),
                 ("accepted", C.c_int32), ("pad", C.c_int32)]
@@ -95,6 +105,21 @@ SIGNATURES = {
                                  C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "cmx_last_error": (C.c_char_p, [_P]),
     "cmx_status_string": (C.c_char_p, [C.c_int]),
+    "cmx_batch_create": (C.c_int, [C.POINTER(Instance), C.c_int, C.POINTER(Solver),
+                                   C.POINTER(BatchConfig), C.c_void_p, C.POINTER(C.c_void_p)]),
+    "cmx_batch_destroy": (C.c_int, [_P]),
+    "cmx_batch_launch": (C.c_int, [_P, C.c_int]),
+    "cmx_batch_run": (C.c_int, [_P, C.c_longlong, C.POINTER(Stats)]),
+    "cmx_batch_stats": (C.c_int, [_P, C.c_int, C.POINTER(Stats)]),
+    "cmx_batch_get_a": (C.c_int, [_P, C.c_int, C.c_void_p]),
+    "cmx_batch_get_m": (C.c_int, [_P, C.c_int, C.c_void_p]),
+    "cmx_batch_get_log": (C.c_int, [_P, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int,
+                                    C.POINTER(C.c_longlong)]),
+    "cmx_batch_get_trace": (C.c_int, [_P, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int,
+                                      C.POINTER(C.c_longlong)]),
+    "cmx_batch_info": (C.c_int, [_P, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                 C.POINTER(C.c_longlong), C.POINTER(C.c_int)]),
+    "cmx_batch_last_error": (C.c_char_p, [_P]),
 }
 
 
@@ -375,3 +400,136 @@ class Simulation:
 
     def last_error(self) -> str:
         return load().cmx_last_error(self.h).decode()
+
+
+def _unpack_complex(v, N):
+    return v[0:2 * N:2] + 1j * v[1:2 * N:2]
+
+
+class BatchSimulation:
+    """One cmx_batch handle (cmx_batch_* calls): independent problems in one persistent launch."""
+
+    def __init__(self, problems, *, log_cap=0, trace_cap=0, sample_dt=0.0, solver=None,
+                 bx=0, by=0, team=0, blocks_per_sm=0, use_graph=True, stream=None):
+        lib = load()
+        keep = []
+        n = len(problems)
+        arr = (Instance * n)()
+        self.N, self.shapes, self.nsub = [], [], problems[0].nsub
+        for i, p in enumerate(problems):
+            if p.u is not None:
+                raise ValueError("batched problems use uniform mode profiles (u = None)")
+            mask = np.ascontiguousarray(np.asarray(p.mask, np.uint8).reshape(-1))
+            om, ka, gr, gi = _f64(p.omega), _f64(p.kappa), _f64(p.g_re), _f64(p.g_im)
+            m0 = _f32(p.m0)
+            a0 = np.zeros(max(2 * p.nmodes, 1))
+            if p.nmodes:
+                ac = np.asarray(p.a0, complex).reshape(-1)
+                a0[0:2 * p.nmodes:2], a0[1:2 * p.nmodes:2] = ac.real, ac.imag
+            keep += [mask, om, ka, gr, gi, m0, a0]
+            ins = arr[i]
+            ins.grid = Grid(p.nx, p.ny, p.nz, p.cx, p.cy, p.cz, p.nsub)
+            ins.mask = mask.ctypes.data
+            ins.mat = Material(p.Ms, p.Aex, p.alpha, p.gamma, p.Ku, (C.c_double * 3)(*p.ku_axis),
+                               (C.c_double * 3)(*p.B0), (C.c_double * 3)(*p.Ndemag), p.BE)
+            md = Modes()
+            md.n_modes = p.nmodes
+            md.omega, md.kappa, md.g_re, md.g_im = _dptr(om), _dptr(ka), _dptr(gr), _dptr(gi)
+            md.u, md.u_on_device = None, 0
+            ins.modes = md
+            ins.m0 = m0.ctypes.data
+            ins.a0 = a0.ctypes.data
+            ins.T = p.T
+            self.N.append(p.nmodes)
+            self.shapes.append((p.nz, p.ny, p.nx))
+        p0 = problems[0]
+        self.solver = solver or Solver(p0.rtol, p0.a_ref, p0.dt0, p0.dt_min, p0.dt_max, sample_dt,
+                                       log_cap, trace_cap)
+        cfg = BatchConfig(bx, by, team, blocks_per_sm, 1 if use_graph else 0)
+        h = C.c_void_p()
+        rc = lib.cmx_batch_create(arr, n, C.byref(self.solver), C.byref(cfg),
+                                  _stream_handle(stream), C.byref(h))
+        if rc != OK:
+            raise CmxError(rc, f"cmx_batch_create: {lib.cmx_status_string(rc).decode()}")
+        self.h = h
+        self.n = n
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().cmx_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc, what):
+        if rc != OK:
+            raise CmxError(rc, f"{what}: {load().cmx_batch_last_error(self.h).decode()}")
+
+    def launch(self, n_attempts: int):
+        self._check(load().cmx_batch_launch(self.h, int(n_attempts)), "batch_launch")
+
+    def run(self, max_attempts: int = 0) -> dict:
+        st = Stats()
+        self._check(load().cmx_batch_run(self.h, int(max_attempts), C.byref(st)), "batch_run")
+        return st.as_dict()
+
+    def stats(self, i: int) -> dict:
+        st = Stats()
+        self._check(load().cmx_batch_stats(self.h, int(i), C.byref(st)), "batch_stats")
+        return st.as_dict()
+
+    def get_a(self, i: int) -> np.ndarray:
+        buf = np.zeros(max(2 * self.N[i], 1))
+        self._check(load().cmx_batch_get_a(self.h, int(i), buf.ctypes.data), "batch_get_a")
+        return _unpack_complex(buf, self.N[i])
+
+    def get_m(self, i: int) -> np.ndarray:
+        buf = np.empty((self.nsub, 3) + self.shapes[i], np.float32)
+        self._check(load().cmx_batch_get_m(self.h, int(i), buf.ctypes.data), "batch_get_m")
+        return buf
+
+    def get_log(self, i: int, cap=None) -> dict:
+        cap = self.solver.log_cap if cap is None else cap
+        N = self.N[i]
+        steps = (Step * max(cap, 1))()
+        Q = max(2 * N, 1)
+        a = np.zeros(max(cap, 1) * Q)
+        mm = np.zeros(max(cap, 1) * Q)
+        n = C.c_longlong()
+        self._check(load().cmx_batch_get_log(self.h, int(i), steps, a.ctypes.data, mm.ctypes.data,
+                                             cap, C.byref(n)), "batch_get_log")
+        k = min(cap, n.value)
+        out = dict(n=n.value, t=np.array([s.t for s in steps[:k]]),
+                   dt=np.array([s.dt for s in steps[:k]]),
+                   err=np.array([s.err for s in steps[:k]]),
+                   accepted=np.array([bool(s.accepted) for s in steps[:k]], bool))
+        if N:
+            out["a"] = (a[:k * 2 * N][0::2] + 1j * a[:k * 2 * N][1::2]).reshape(k, N)
+            out["mm"] = (mm[:k * 2 * N][0::2] + 1j * mm[:k * 2 * N][1::2]).reshape(k, N)
+        return out
+
+    def get_trace(self, i: int, cap=None) -> dict:
+        cap = self.solver.trace_cap if cap is None else cap
+        N = self.N[i]
+        Q = max(2 * N, 1)
+        t = np.zeros(max(cap, 1))
+        a = np.zeros(max(cap, 1) * Q)
+        mm = np.zeros(max(cap, 1) * Q)
+        n = C.c_longlong()
+        self._check(load().cmx_batch_get_trace(self.h, int(i), t.ctypes.data, a.ctypes.data,
+                                               mm.ctypes.data, cap, C.byref(n)), "batch_get_trace")
+        k = min(cap, n.value)
+        out = dict(n=n.value, t=t[:k])
+        if N:
+            out["a"] = (a[:k * 2 * N][0::2] + 1j * a[:k * 2 * N][1::2]).reshape(k, N)
+            out["mm"] = (mm[:k * 2 * N][0::2] + 1j * mm[:k * 2 * N][1::2]).reshape(k, N)
+        return out
+
+    def info(self) -> dict:
+        v = [C.c_int(), C.c_int(), C.c_int(), C.c_longlong(), C.c_int()]
+        self._check(load().cmx_batch_info(self.h, *[C.byref(x) for x in v]), "batch_info")
+        return dict(zip(("teams", "team_size", "blocks", "cells", "graph"), [x.value for x in v]))

@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "cmx_kernels.h"
+#include "cmx_layout.h"
 
 using namespace cmx;
 
@@ -24,9 +25,7 @@ struct cmx_problem {
     long long nbox = 0;
     int ncell = 0, ncell_mag = 0;
     bool holes = false;
-    std::vector<int2> rows_h;
-    std::vector<int> box_of_cell_h;   // box index of each stored cell
-    std::vector<uint8_t> active_h;    // 1 = magnetic (stored cells)
+    Layout lay;
     // device buffers
     int2 *rows = nullptr;
     uint32_t *active = nullptr;
@@ -155,143 +154,6 @@ __global__ void prep_kernel(Ctl *ctl, PrepArgs a)
 
 int grid_blocks(long long n) { return (int)std::min<long long>(4096, (n + 255) / 256); }
 
-void build_layout(cmx_problem *h, const uint8_t *mask)
-{
-    const int nx = h->grid.nx, ny = h->grid.ny, nz = h->grid.nz;
-    h->rows_h.assign((size_t)ny * nz, make_int2(0, 0));
-    h->box_of_cell_h.clear();
-    h->active_h.clear();
-    int off = 0, nmag = 0;
-    for (int z = 0; z < nz; z++)
-        for (int y = 0; y < ny; y++) {
-            const size_t rb = ((size_t)z * ny + y) * nx;
-            int xs = -1, xe = -1;
-            for (int x = 0; x < nx; x++)
-                if (mask[rb + x]) {
-                    if (xs < 0) xs = x;
-                    xe = x + 1;
-                }
-            if (xs < 0) {
-                h->rows_h[(size_t)z * ny + y] = make_int2(off, 0);
-                continue;
-            }
-            h->rows_h[(size_t)z * ny + y] = make_int2(off, xs | (xe << 16));
-            for (int x = xs; x < xe; x++) {
-                h->box_of_cell_h.push_back((int)(rb + x));
-                h->active_h.push_back(mask[rb + x] ? 1 : 0);
-                nmag += mask[rb + x] ? 1 : 0;
-            }
-            off += xe - xs;
-        }
-    h->ncell = off;
-    h->ncell_mag = nmag;
-    h->holes = nmag != off;
-}
-
-// Columns of (wx-2) x (wy-2) interior cells (a wx x wy thread window with its one-cell rim):
-// the range of planes [zlo, zhi) that hold magnetic cells of the column, and per plane a work
-// weight (1: a plane iteration is latency-bound and costs about the same whatever its cells).
-struct Column {
-    int x0, y0, zlo, zhi;
-    std::vector<float> w;   // weight of plane zlo + i
-};
-
-std::vector<Column> build_columns(const cmx_problem *h, int wx, int wy)
-{
-    const int nx = h->grid.nx, ny = h->grid.ny, nz = h->grid.nz;
-    const int bx = wx - 2, by = wy - 2;
-    auto count = [&](int x0, int x1, int y0, int y1, int z) {
-        int n = 0;
-        if (z < 0 || z >= nz) return 0;
-        for (int y = std::max(0, y0); y < std::min(ny, y1); y++) {
-            const int2 r = h->rows_h[(size_t)z * ny + y];
-            const int xs = r.y & 0xffff, xe = (int)((unsigned)r.y >> 16);
-            for (int x = std::max(xs, x0); x < std::min(xe, x1); x++) n += h->active_h[r.x + x - xs];
-        }
-        return n;
-    };
-    std::vector<Column> out;
-    for (int y0 = 0; y0 < ny; y0 += by)
-        for (int x0 = 0; x0 < nx; x0 += bx) {
-            Column c{x0, y0, -1, -1, {}};
-            std::vector<float> w(nz);
-            for (int z = 0; z < nz; z++) {
-                const int inner = count(x0, x0 + bx, y0, y0 + by, z);
-                if (inner > 0) {
-                    if (c.zlo < 0) c.zlo = z;
-                    c.zhi = z + 1;
-                }
-                w[z] = 1.0f;   // a plane iteration costs about the same whatever its cells
-            }
-            if (c.zlo >= 0) {
-                c.w.assign(w.begin() + c.zlo, w.begin() + c.zhi);
-                out.push_back(std::move(c));
-            }
-        }
-    return out;
-}
-
-// Greedy fill of blocks with capacity `cap` (plane weights plus two halo planes per segment):
-// each block takes planes of consecutive columns until the next plane would exceed its
-// capacity; columns are cut into segments at block boundaries and every MAX_TILE_PLANES - 2
-// planes.  Returns the number of blocks used (segments and block starts in segs / begin).
-int fill_blocks(const std::vector<Column> &cols, double cap, int max_blocks,
-                std::vector<int4> &segs, std::vector<int> &begin)
-{
-    segs.clear();
-    begin.assign(1, 0);
-    double load = 0.0;
-    int nseg_block = 0;
-    for (const Column &c : cols) {
-        int z = c.zlo;
-        while (z < c.zhi) {
-            // a new segment costs its two halo planes plus at least one plane
-            if (nseg_block > 0 && (load + 2.0 + c.w[z - c.zlo] > cap ||
-                                   nseg_block >= MAX_BLOCK_SEGMENTS)) {
-                begin.push_back((int)segs.size());
-                if ((int)begin.size() - 1 >= max_blocks) return max_blocks + 1;
-                load = 0.0;
-                nseg_block = 0;
-            }
-            load += 2.0;
-            int len = 0;
-            while (z + len < c.zhi && len < MAX_TILE_PLANES - 2 &&
-                   (len == 0 || load + c.w[z + len - c.zlo] <= cap)) {
-                load += c.w[z + len - c.zlo];
-                len++;
-            }
-            segs.push_back(make_int4(c.x0, c.y0, z, z + len));
-            nseg_block++;
-            z += len;
-        }
-    }
-    begin.push_back((int)segs.size());
-    return (int)begin.size() - 1;
-}
-
-// Smallest per-block capacity (binary search) whose greedy fill needs at most `blocks`
-// blocks; the partition then has no block above that capacity.
-void build_segments(const std::vector<Column> &cols, int blocks, std::vector<int4> &segs,
-                    std::vector<int> &begin)
-{
-    double total = 0.0, wmax = 0.0;
-    for (const Column &c : cols)
-        for (float v : c.w) {
-            total += v;
-            wmax = std::max(wmax, (double)v);
-        }
-    double lo = std::max(total / blocks, 2.0 + wmax), hi = total + 2.0 * (total + cols.size());
-    for (int it = 0; it < 60 && hi - lo > 0.5; it++) {
-        const double mid = 0.5 * (lo + hi);
-        if (fill_blocks(cols, mid, blocks, segs, begin) <= blocks)
-            hi = mid;
-        else
-            lo = mid;
-    }
-    fill_blocks(cols, hi, blocks, segs, begin);
-    while ((int)begin.size() < blocks + 1) begin.push_back((int)segs.size());
-}
-
 int setup_tiling(cmx_problem *h, const cmx_tiling *t)
 {
     int bx = 32, by = 8, bz = 0, bps = 0;
@@ -310,7 +172,7 @@ int setup_tiling(cmx_problem *h, const cmx_tiling *t)
     int occ = single_blocks_per_sm(h->grid.nsub, bx, by, h->N > 0 && h->u != nullptr);
     if (occ <= 0) return fail(h, CMX_ECUDA, "occupancy query failed for %dx%d", bx, by);
     if (bps > 0) occ = std::min(occ, bps);
-    const std::vector<Column> cols = build_columns(h, bx, by);
+    const std::vector<Column> cols = build_columns(h->lay, bx, by);
     long long P = 0;
     for (const Column &c : cols) P += c.zhi - c.zlo;
     // bz: the fewest planes a block should get (default 4); all resident blocks otherwise
@@ -539,23 +401,25 @@ int cmx_create(const cmx_grid *grid, const uint8_t *mask, const cmx_material *ma
     cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, h->dev);
     if (!coop) return bail(CMX_ECUDA);
 
-    build_layout(h, mask);
+    build_layout(h->lay, grid->nx, grid->ny, grid->nz, mask);
+    h->ncell = h->lay.ncell;
+    h->ncell_mag = h->lay.ncell_mag;
+    h->holes = h->lay.holes;
     if (h->ncell_mag == 0) return bail(CMX_EINVAL);
     const int nq = 3 * grid->nsub;
     const size_t nc = (size_t)h->ncell;
     // device buffers
-    if (dalloc(&h->rows, h->rows_h.size()) || dalloc(&h->box_of_cell, nc) ||
+    if (dalloc(&h->rows, h->lay.rows.size()) || dalloc(&h->box_of_cell, nc) ||
         dalloc(&h->mbuf[0], nq * nc) || dalloc(&h->mbuf[1], nq * nc) || dalloc(&h->ctl, 1) ||
         dalloc(&h->dense, (size_t)nq * nbox))
         return bail(CMX_ENOMEM);
     for (int j = 0; j < 7; j++)
         if (dalloc(&h->kbuf[j], nq * nc)) return bail(CMX_ENOMEM);
-    cudaMemcpy(h->rows, h->rows_h.data(), h->rows_h.size() * sizeof(int2), cudaMemcpyHostToDevice);
-    cudaMemcpy(h->box_of_cell, h->box_of_cell_h.data(), nc * sizeof(int), cudaMemcpyHostToDevice);
+    cudaMemcpy(h->rows, h->lay.rows.data(), h->lay.rows.size() * sizeof(int2),
+               cudaMemcpyHostToDevice);
+    cudaMemcpy(h->box_of_cell, h->lay.box_of_cell.data(), nc * sizeof(int), cudaMemcpyHostToDevice);
     if (h->holes) {
-        std::vector<uint32_t> bits((nc + 31) / 32, 0u);
-        for (size_t i = 0; i < nc; i++)
-            if (h->active_h[i]) bits[i >> 5] |= 1u << (i & 31);
+        const std::vector<uint32_t> bits = active_bits(h->lay);
         if (dalloc(&h->active, bits.size())) return bail(CMX_ENOMEM);
         cudaMemcpy(h->active, bits.data(), bits.size() * sizeof(uint32_t), cudaMemcpyHostToDevice);
     }
@@ -571,7 +435,8 @@ int cmx_create(const cmx_grid *grid, const uint8_t *mask, const cmx_material *ma
             std::vector<float> uc((size_t)N * nc);
             for (int n = 0; n < N; n++)
                 for (size_t i = 0; i < nc; i++)
-                    uc[n * nc + i] = h->active_h[i] ? modes->u[n * nbox + h->box_of_cell_h[i]] : 0.f;
+                    uc[n * nc + i] =
+                        h->lay.active[i] ? modes->u[n * nbox + h->lay.box_of_cell[i]] : 0.f;
             cudaMemcpy(h->u, uc.data(), uc.size() * sizeof(float), cudaMemcpyHostToDevice);
         }
     }
@@ -643,7 +508,7 @@ int cmx_create(const cmx_grid *grid, const uint8_t *mask, const cmx_material *ma
     // initial state: +z (sublattice 2: -z), a = 0
     std::vector<float> m0((size_t)nq * nc, 0.f);
     for (size_t i = 0; i < nc; i++)
-        if (h->active_h[i]) {
+        if (h->lay.active[i]) {
             m0[2 * nc + i] = 1.f;
             if (grid->nsub == 2) m0[5 * nc + i] = -1.f;
         }

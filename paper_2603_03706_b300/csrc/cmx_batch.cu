@@ -1,0 +1,123 @@
+// Batched integrator: one persistent cooperative launch advances many independent problems.
+// The blocks form teams of equal size; a team integrates the instances of its queue one after
+// the other with the same engine as the single-problem kernel, synchronising only its own
+// blocks through the instance's arrival counter.
+#include "cmx_engine.cuh"
+#include "cmx_kernels.h"
+
+namespace cmx {
+
+template <int NS, int WX, int WY>
+__global__ void __launch_bounds__(WX *WY, (WX * WY <= 256 ? 2 : 1)) batch_kernel(BatchArgs B)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    auto &sm = *reinterpret_cast<StageSmem<NS, WX, WY, false> *>(smem_raw);
+    __shared__ Local L;
+    __shared__ Coef cf;
+    __shared__ double s_sum[2 * MAXN];
+    __shared__ float s_emax;
+    __shared__ int s_stop;
+    __shared__ __align__(16) Ctx sc;
+    const int team = blockIdx.x / B.team_size, rank = blockIdx.x % B.team_size;
+    const int qb = __ldg(&B.q_begin[team]), qe = __ldg(&B.q_begin[team + 1]);
+    for (int q = qb; q < qe; q++) {
+        const int inst = __ldg(&B.queue[q]);
+        // the instance's context into shared memory (word copy)
+        const int *src = reinterpret_cast<const int *>(B.ctx + inst);
+        int *dst = reinterpret_cast<int *>(&sc);
+        for (int w = threadIdx.x; w < (int)(sizeof(Ctx) / sizeof(int)); w += WX * WY)
+            dst[w] = __ldg(src + w);
+        __syncthreads();
+        const Team tm{rank, B.team_size, &sc.ctl->bar_count};
+        integrate<NS, WX, WY, false>(sc, tm, sm, L, cf, s_sum, s_emax, s_stop);
+    }
+}
+
+// Stream-ordered start of a batch launch: reset every instance's per-launch counters.
+__global__ void batch_prep_kernel(Ctl *const *ctls, int n, long long max_attempts)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        Ctl *c = ctls[i];
+        c->done = 0;
+        c->launch_attempts = 0;
+        c->max_launch_attempts = max_attempts;
+        c->bar_count = 0;
+        c->skip_block = -1;
+    }
+}
+
+// Number of instances that still have to run (t < T and no error) into *pending.
+__global__ void batch_pending_kernel(Ctl *const *ctls, int n, int *pending)
+{
+    __shared__ int s;
+    if (threadIdx.x == 0) s = 0;
+    __syncthreads();
+    int mine = 0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const Ctl *c = ctls[i];
+        mine += (c->status == 0 && c->t < c->T) ? 1 : 0;
+    }
+    atomicAdd(&s, mine);
+    __syncthreads();
+    if (threadIdx.x == 0) *pending = s;
+}
+
+template <int NS, int WX, int WY>
+static cudaError_t batch_launch_variant(const BatchArgs &b, int blocks, cudaStream_t s)
+{
+    auto *fn = batch_kernel<NS, WX, WY>;
+    const size_t smem = sizeof(StageSmem<NS, WX, WY, false>);
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    BatchArgs bb = b;
+    void *args[] = {&bb};
+    return cudaLaunchCooperativeKernel((const void *)fn, dim3(blocks), dim3(WX * WY), args, smem,
+                                       s);
+}
+
+template <int NS, int WX, int WY>
+static int batch_occupancy_variant()
+{
+    auto *fn = batch_kernel<NS, WX, WY>;
+    const size_t smem = sizeof(StageSmem<NS, WX, WY, false>);
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess)
+        return 0;
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, WX * WY, smem) != cudaSuccess)
+        return 0;
+    return nb;
+}
+
+#define CMX_BATCH_VARIANTS(X) X(1, 32, 8) X(1, 32, 16) X(1, 64, 4) X(2, 32, 8) X(2, 64, 4)
+
+cudaError_t launch_batch(const BatchArgs &b, int nsub, int bx, int by, int blocks, cudaStream_t s)
+{
+#define X(n, a, c) if (nsub == n && bx == a && by == c) return batch_launch_variant<n, a, c>(b, blocks, s);
+    CMX_BATCH_VARIANTS(X)
+#undef X
+    return cudaErrorInvalidValue;
+}
+
+int batch_blocks_per_sm(int nsub, int bx, int by)
+{
+#define X(n, a, c) if (nsub == n && bx == a && by == c) return batch_occupancy_variant<n, a, c>();
+    CMX_BATCH_VARIANTS(X)
+#undef X
+    return 0;
+}
+
+cudaError_t launch_batch_prep(Ctl *const *ctls, int n, long long max_attempts, cudaStream_t s)
+{
+    batch_prep_kernel<<<(n + 255) / 256, 256, 0, s>>>(ctls, n, max_attempts);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_pending(Ctl *const *ctls, int n, int *pending, cudaStream_t s)
+{
+    batch_pending_kernel<<<1, 256, 0, s>>>(ctls, n, pending);
+    return cudaGetLastError();
+}
+
+}  // namespace cmx

@@ -1,458 +1,8 @@
-// Persistent integrator for one problem.  Every Dormand-Prince attempt runs inside one
-// cooperative launch with a grid barrier after each stage: the cavity slope of a stage needs
-// the overlap reduction over all cells (Eq. (18)).  The barrier is a monotonic arrival counter
-// (one release-atomic per block, acquire polling).  After it every block reads all per-block
-// partials and reduces them in the same fixed order, then runs the same FP64 cavity update and
-// step-size controller on its own shared-memory copy of the integrator state: identical inputs
-// and identical code give every block the same decision, deterministic from run to run.
-// Block 0 records the step log and the trace and writes the state back when the launch ends.
-// No step returns to the host (Sec. III A).
+// Persistent single-problem integrator: one team of all blocks of a cooperative launch.
+#include "cmx_engine.cuh"
 #include "cmx_kernels.h"
-#include "cmx_stage.cuh"
 
 namespace cmx {
-
-// Block-local copy of the integrator state.
-struct Local {
-    double t, dt, T, h;
-    double a[2 * MAXN];
-    double ka[7][2 * MAXN];
-    double mm_n[2 * MAXN];
-    double trace_next;
-    long long attempts, accepted, launch_attempts, max_launch_attempts, rhs_evals;
-    long long replay_pos, replay_n, log_n, trace_n;
-    const double *replay_dts;
-    double mm[2 * MAXN], as[2 * MAXN];   // overlaps and cavity stage value of this stage
-    double err_n[MAXN], amax_n[MAXN];    // per-mode error and amplitude (stage 7)
-    double mc[4 * MAXN];                 // mode constants: w, kappa, Re g~, Im g~
-    unsigned bar_target;                 // arrival count that completes the next barrier
-    int skip_block;
-    int kphys[7];
-    int mcur, k1_valid, last_rejected, last, replay, done, status;
-};
-
-__device__ void load_local(const Ctx &c, Local &L)
-{
-    const volatile Ctl *g = c.ctl;
-    L.t = g->t;
-    L.dt = g->dt;
-    L.T = g->T;
-    for (int q = 0; q < 2 * c.nmodes; q++) {
-        L.a[q] = g->a[q];
-        L.mm_n[q] = g->mm_n[q];
-        for (int j = 0; j < 7; j++) L.ka[j][q] = g->ka[j][q];
-    }
-    L.trace_next = g->trace_next;
-    L.attempts = g->attempts;
-    L.accepted = g->accepted;
-    L.launch_attempts = g->launch_attempts;
-    L.max_launch_attempts = g->max_launch_attempts;
-    L.rhs_evals = g->rhs_evals;
-    L.replay_pos = g->replay_pos;
-    L.replay_n = g->replay_n;
-    L.log_n = g->log_n;
-    L.trace_n = g->trace_n;
-    L.replay_dts = g->replay_dts;
-    for (int j = 0; j < 7; j++) L.kphys[j] = g->kphys[j];
-    L.mcur = g->mcur;
-    L.k1_valid = g->k1_valid;
-    L.last_rejected = g->last_rejected;
-    L.replay = g->replay;
-    L.done = g->done;
-    L.status = g->status;
-    L.last = 0;
-    L.h = 0.0;
-    L.bar_target = 0;
-    L.skip_block = g->skip_block;
-}
-
-__device__ void store_local(const Ctx &c, const Local &L)
-{
-    volatile Ctl *g = c.ctl;
-    g->t = L.t;
-    g->dt = L.dt;
-    for (int q = 0; q < 2 * c.nmodes; q++) {
-        g->a[q] = L.a[q];
-        g->mm_n[q] = L.mm_n[q];
-        for (int j = 0; j < 7; j++) g->ka[j][q] = L.ka[j][q];
-    }
-    g->trace_next = L.trace_next;
-    g->attempts = L.attempts;
-    g->accepted = L.accepted;
-    g->launch_attempts = L.launch_attempts;
-    g->rhs_evals = L.rhs_evals;
-    g->replay_pos = L.replay_pos;
-    g->log_n = L.log_n;
-    g->trace_n = L.trace_n;
-    for (int j = 0; j < 7; j++) g->kphys[j] = L.kphys[j];
-    g->mcur = L.mcur;
-    g->k1_valid = L.k1_valid;
-    g->last_rejected = L.last_rejected;
-    g->done = L.done;
-    if (L.status) atomicCAS(&c.ctl->status, 0, L.status);
-    __threadfence();
-}
-
-// Size of the next attempt: the replay list, or min(dt, dt_max) shortened to land on T.
-__device__ void attempt_size(const Ctx &c, Local &L)
-{
-    L.last = 0;
-    if (L.replay) {
-        L.h = L.replay_dts[L.replay_pos];
-        return;
-    }
-    L.h = L.dt < c.dt_max ? L.dt : c.dt_max;
-    if (L.t + L.h >= L.T) {
-        L.h = L.T - L.t;
-        L.last = 1;
-    }
-}
-
-// Cavity right-hand side (-i w - kappa) a + i g~ mm for one mode (Eq. (12), (19)); the mode
-// constants come from the block's shared copy (w, kappa, Re g~, Im g~).
-__device__ __forceinline__ void cavity_rhs(const double *mc, int n, double ar, double ai,
-                                           double mr, double mi, double &dr, double &di)
-{
-    const double w = mc[4 * n], k = mc[4 * n + 1], gr = mc[4 * n + 2], gi = mc[4 * n + 3];
-    const double pr = gr * mr - gi * mi, pi = gr * mi + gi * mr;   // g~ <m^->
-    dr = -k * ar + w * ai - pi;
-    di = -k * ai - w * ar + pr;
-}
-
-// Stage-S cavity update and, after stage 7, error norm, accept/reject and step-size control,
-// on the block's copy L.  L.as holds the cavity stage value a_S (set before the stage), `sum`
-// the grid sums of the overlaps and `emax` the grid maximum of |e_m|.  The per-mode FP64 work
-// runs on 2N threads; the decision itself on thread 0.  Only block 0 writes log and trace.
-template <int S>
-__device__ void controller(const Ctx &c, Local &L, const double *sum, float emax)
-{
-    const int N = c.nmodes;
-    const int tid = threadIdx.x;
-    if (tid < 2 * N) L.mm[tid] = sum[tid] * c.inv_nmag;
-    __syncthreads();
-    if (tid < N) {
-        double dr, di;
-        cavity_rhs(L.mc, tid, L.as[2 * tid], L.as[2 * tid + 1], L.mm[2 * tid],
-                   L.mm[2 * tid + 1], dr, di);
-        L.ka[S - 1][2 * tid] = dr;
-        L.ka[S - 1][2 * tid + 1] = di;
-        if (S == 7) {
-            double er = 0.0, ei = 0.0;
-#pragma unroll
-            for (int j = 0; j < 7; j++) {
-                const double kr = j == 6 ? dr : L.ka[j][2 * tid];
-                const double ki = j == 6 ? di : L.ka[j][2 * tid + 1];
-                er += dp_e(j) * kr;
-                ei += dp_e(j) * ki;
-            }
-            // magnitudes in FP32: they only scale the error norm
-            L.err_n[tid] = (double)(fabsf((float)L.h) * hypotf((float)er, (float)ei));
-            L.amax_n[tid] = (double)fmaxf(hypotf((float)L.a[2 * tid], (float)L.a[2 * tid + 1]),
-                                          hypotf((float)L.as[2 * tid], (float)L.as[2 * tid + 1]));
-        }
-    }
-    __syncthreads();
-    if (tid != 0) return;
-    L.rhs_evals += 1;
-    if (S == 1) {
-        L.k1_valid = 1;
-        for (int q = 0; q < 2 * N; q++) L.mm_n[q] = L.mm[q];
-        if (c.stage_only) L.done = 1;
-        return;
-    }
-    if (S != 7) return;
-
-    // scaled error norm
-    const double h = L.h;
-    double ea = 0.0, amax = 0.0;
-    for (int n = 0; n < N; n++) {
-        if (L.err_n[n] > ea || L.err_n[n] != L.err_n[n]) ea = L.err_n[n];
-        amax = fmax(amax, L.amax_n[n]);
-    }
-    const double e1 = (double)emax / c.rtol;
-    const double e2 = ea / (c.rtol * fmax(c.a_ref, amax));
-    const double err = (e1 > e2 || e1 != e1) ? e1 : e2;
-    if (!isfinite(err)) {
-        L.status = CMX_ENAN;
-        L.done = 1;
-    }
-    const int accepted = L.status == 0 && (L.replay || err <= 1.0);
-    const bool rec = blockIdx.x == 0;
-    const long long li = L.log_n;
-    L.attempts += 1;
-    L.launch_attempts += 1;
-    const double t0 = L.t;
-    double t1 = t0;
-    const double *as = L.as, *mm = L.mm;
-    if (accepted) {
-        t1 = L.last ? L.T : t0 + h;
-        // uniform trace: cubic Hermite for a_n (end slopes k1, k7), linear for <m^->_n
-        if (c.tr_cap > 0 && c.sample_dt > 0.0) {
-            long long tn = L.trace_n;
-            double ts = L.trace_next;
-            while (tn < c.tr_cap && ts <= t1) {
-                const double th = (ts - t0) / h;
-                const double h00 = (2 * th - 3) * th * th + 1, h10 = ((th - 2) * th + 1) * th;
-                const double h01 = (3 - 2 * th) * th * th, h11 = (th - 1) * th * th;
-                if (rec) {
-                    c.tr_t[tn] = ts;
-                    for (int q = 0; q < 2 * N; q++) {
-                        c.tr_a[tn * 2 * N + q] = h00 * L.a[q] + h10 * h * L.ka[0][q] +
-                                                 h01 * as[q] + h11 * h * L.ka[6][q];
-                        c.tr_mm[tn * 2 * N + q] = (1 - th) * L.mm_n[q] + th * mm[q];
-                    }
-                }
-                tn++;
-                ts += c.sample_dt;
-            }
-            L.trace_n = tn;
-            L.trace_next = ts;
-        }
-        for (int q = 0; q < 2 * N; q++) {
-            L.a[q] = as[q];
-            L.ka[0][q] = L.ka[6][q];
-            L.mm_n[q] = mm[q];
-        }
-        const int k0 = L.kphys[0];
-        L.kphys[0] = L.kphys[6];
-        L.kphys[6] = k0;
-        L.mcur ^= 1;
-        L.t = t1;
-        L.accepted += 1;
-    }
-    if (rec && li < c.log_cap) {
-        cmx_step st;
-        st.t = accepted ? t1 : t0;
-        st.dt = h;
-        st.err = err;
-        st.accepted = accepted;
-        st.pad = 0;
-        c.log[li] = st;
-        if (accepted)
-            for (int q = 0; q < 2 * N; q++) {
-                c.log_a[li * 2 * N + q] = as[q];
-                c.log_mm[li * 2 * N + q] = mm[q];
-            }
-    }
-    L.log_n = li + 1;
-
-    if (L.replay) {
-        L.replay_pos += 1;
-        if (L.replay_pos >= L.replay_n) L.done = 1;
-    } else if (L.status == 0) {
-        // step factor in FP32 (FP64 pow has a very long latency here)
-        const float ef = (float)err;
-        double fac = ef > 0.f ? (double)(0.9f * powf(ef, -0.2f)) : 5.0;
-        fac = fmin(5.0, fmax(0.2, fac));
-        if (accepted) {
-            if (L.last_rejected && fac > 1.0) fac = 1.0;
-            L.last_rejected = 0;
-            L.dt = fmin(h * fac, c.dt_max);
-        } else {
-            L.last_rejected = 1;
-            L.dt = h * fac;
-            if (L.dt < c.dt_min) {
-                L.status = CMX_ESTEPFAIL;
-                L.done = 1;
-            }
-        }
-    }
-    if (L.t >= L.T || L.launch_attempts >= L.max_launch_attempts) L.done = 1;
-}
-
-// Block sum of the per-thread overlap accumulators (compensated pairs, fixed shuffle order)
-// and block max of |e_m|, written to the block's slot of c.part / c.errpart.
-template <int NS, int WX, int WY, bool HU>
-__device__ void block_reduce(const Ctx &c, StageSmem<NS, WX, WY, HU> &sm, const Acc &acc)
-{
-    constexpr int NT = WX * WY, NW = NT / 32;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-    for (int n = 0; n < MAXN; n++) {
-        if (n >= c.nmodes) break;
-        F2 r = {acc.re[n], 0.f}, i = {acc.im[n], 0.f};
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            r = f2_add(r, f2_shfl_xor(r, o));
-            i = f2_add(i, f2_shfl_xor(i, o));
-        }
-        if (lane == 0) {
-            sm.red[warp][2 * n] = r;
-            sm.red[warp][2 * n + 1] = i;
-        }
-    }
-    float e = acc.emax;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) e = nanmax(e, __shfl_xor_sync(0xffffffffu, e, o));
-    if (lane == 0) sm.redmax[warp] = e;
-    __syncthreads();
-    const int Q = 2 * c.nmodes;
-    if (threadIdx.x < Q) {
-        F2 s = {0.f, 0.f};
-        for (int w = 0; w < NW; w++) s = f2_add(s, sm.red[w][threadIdx.x]);
-        c.part[(size_t)blockIdx.x * Q + threadIdx.x] = make_float2(s.hi, s.lo);
-    }
-    if (threadIdx.x == NT - 1) {
-        float m = 0.f;
-        for (int w = 0; w < NW; w++) m = nanmax(m, sm.redmax[w]);
-        c.errpart[blockIdx.x] = m;
-    }
-}
-
-__device__ __forceinline__ void red_add_release(unsigned *p, unsigned v)
-{
-    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
-// Fixed-order sum over all blocks of the overlap partials (compensated pairs) and max of the
-// error partials, done identically by every block after the barrier, so every block holds the
-// same values.  Thread t sums component q = t mod QP of blocks b = t/QP, t/QP + NT/QP, ...
-// (QP = 2N rounded up to a power of two); lanes of equal q are then combined by shuffles and
-// the warps in order.
-template <int NS, int WX, int WY, bool HU>
-__device__ void grid_reduce(const Ctx &c, StageSmem<NS, WX, WY, HU> &sm, double *out, float *emax)
-{
-    constexpr int NT = WX * WY, NW = NT / 32;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int Q = 2 * c.nmodes, G = gridDim.x;
-    int QP = 1;
-    while (QP < Q) QP <<= 1;
-    const int q = threadIdx.x & (QP - 1), grp = threadIdx.x / QP, ngrp = NT / QP;
-    F2 s = {0.f, 0.f};
-    if (q < Q) {
-        int b = grp;
-        for (; b + 3 * ngrp < G; b += 4 * ngrp) {
-            const float2 v0 = __ldcg(c.part + (size_t)b * Q + q);
-            const float2 v1 = __ldcg(c.part + (size_t)(b + ngrp) * Q + q);
-            const float2 v2 = __ldcg(c.part + (size_t)(b + 2 * ngrp) * Q + q);
-            const float2 v3 = __ldcg(c.part + (size_t)(b + 3 * ngrp) * Q + q);
-            s = f2_add(s, {v0.x, v0.y});
-            s = f2_add(s, {v1.x, v1.y});
-            s = f2_add(s, {v2.x, v2.y});
-            s = f2_add(s, {v3.x, v3.y});
-        }
-        for (; b < G; b += ngrp) {
-            const float2 v = __ldcg(c.part + (size_t)b * Q + q);
-            s = f2_add(s, {v.x, v.y});
-        }
-    }
-    for (int o = 16; o >= QP; o >>= 1) s = f2_add(s, f2_shfl_xor(s, o));
-    if (lane < QP && lane < Q) sm.red[warp][lane] = s;
-    float e = 0.f;
-    for (int b = threadIdx.x; b < G; b += NT) e = nanmax(e, __ldcg(c.errpart + b));
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) e = nanmax(e, __shfl_xor_sync(0xffffffffu, e, o));
-    if (lane == 0) sm.redmax[warp] = e;
-    __syncthreads();
-    if (threadIdx.x < Q) {
-        F2 v = {0.f, 0.f};
-        for (int w = 0; w < NW; w++) v = f2_add(v, sm.red[w][threadIdx.x]);
-        out[threadIdx.x] = (double)v.hi + (double)v.lo;
-    }
-    if (threadIdx.x == NT - 1) {
-        float m = 0.f;
-        for (int w = 0; w < NW; w++) m = nanmax(m, sm.redmax[w]);
-        *emax = m;
-    }
-    __syncthreads();
-}
-
-// Grid barrier: every block adds 1 to a monotonic arrival counter with release semantics and
-// polls it with acquire loads until all blocks of this barrier have arrived.  Waits are bounded
-// by c.timeout_ns: on time-out the block sets CMX_ETIMEOUT and the run stops.  The block's
-// partials were written before the __syncthreads that precedes the release-add.  Returns false
-// if the run must stop.
-template <int NS, int WX, int WY, bool HU>
-__device__ bool grid_barrier(const Ctx &c, Local &L, int where)
-{
-    __shared__ int s_ok;
-    Ctl *ctl = c.ctl;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        s_ok = 1;
-        if (L.skip_block == (int)blockIdx.x) {
-            s_ok = -1;   // test hook: leave without arriving
-        } else {
-            L.bar_target += gridDim.x;
-            red_add_release(&ctl->bar_count, 1u);
-            const unsigned long long t0 = global_timer_ns();
-            unsigned spins = 0;
-            while ((int)(ld_acquire(&ctl->bar_count) - L.bar_target) < 0) {
-                if ((++spins & 31u) == 0) {
-                    if (ld_volatile_int(&ctl->status) != 0) {
-                        s_ok = 0;
-                        break;
-                    }
-                    if (global_timer_ns() - t0 > (unsigned long long)c.timeout_ns) {
-                        atomicCAS(&ctl->status, 0, (int)CMX_ETIMEOUT);
-                        ctl->timeout_where = where;
-                        s_ok = 0;
-                        break;
-                    }
-                }
-            }
-        }
-    }
-    __syncthreads();
-    return s_ok > 0;
-}
-
-// Physical buffer of logical slope j (select rather than index the kernel-parameter array,
-// which keeps it out of local memory).
-__device__ __forceinline__ const float *slope_buffer(const Ctx &c, int kj)
-{
-    const float *p = c.k[0];
-#pragma unroll
-    for (int u = 1; u < 7; u++)
-        if (kj == u) p = c.k[u];
-    return p;
-}
-
-// One stage.  If `begun`, the copy pipeline of this stage was started by the previous stage
-// (right after its barrier).  After the barrier this stage starts the next one (S < 7) before
-// it reduces the partials and updates the cavity, so those latencies overlap the first copies.
-template <int NS, int WX, int WY, bool HU, int S>
-__device__ bool run_stage(const Ctx &c, StageSmem<NS, WX, WY, HU> &sm, Local &L, Coef &cf,
-                          double *s_sum, float *s_emax, Pipe &pp, bool begun)
-{
-    const int tid = threadIdx.x, N = c.nmodes;
-    const double h = L.h;
-    const float *mn = L.mcur ? c.m[1] : c.m[0];
-    float *mnew = L.mcur ? c.m[0] : c.m[1];
-    if (!begun) {
-        if (tid < 7) sm.kp[tid] = slope_buffer(c, L.kphys[tid]);
-        __syncthreads();
-        tiles_begin<NS, WX, WY, HU, S>(c, sm, mn, pp);
-    }
-    // cavity stage value a_S = a_n + h sum_j a_Sj k^a_j (FP64, one thread per real component)
-    if (tid < 2 * N) {
-        double v = L.a[tid];
-#pragma unroll
-        for (int j = 0; j < S - 1; j++)
-            if (dp_a(S - 1, j) != 0.0) v += h * dp_a(S - 1, j) * L.ka[j][tid];
-        L.as[tid] = v;
-    }
-    if (tid >= 32 && tid < 38) cf.cf[tid - 32] = (float)(h * (tid - 32 < S - 1 ? dp_a(S - 1, tid - 32) : 0.0));
-    if (tid >= 64 && tid < 71) cf.e[tid - 64] = (float)dp_e(tid - 64);
-    if (tid == 96) cf.h = (float)h;
-    __syncthreads();
-    if (tid < N)
-        cf.hrf[tid] = (float)(c.two_over_gamma * (L.mc[4 * tid + 2] * L.as[2 * tid] -
-                                                  L.mc[4 * tid + 3] * L.as[2 * tid + 1]));
-    __syncthreads();
-    Acc acc;
-#pragma unroll
-    for (int n = 0; n < MAXN; n++) acc.re[n] = acc.im[n] = 0.f;
-    acc.emax = 0.f;
-    tiles_run<NS, WX, WY, HU, S>(c, sm, (float *)sm.kp[S - 1], mn, mnew, cf, pp, acc);
-    block_reduce<NS, WX, WY, HU>(c, sm, acc);
-    if (!grid_barrier<NS, WX, WY, HU>(c, L, S)) return false;
-    if (S >= 2 && S < 7 && !c.stage_only) tiles_begin<NS, WX, WY, HU, (S < 7 ? S + 1 : 7)>(c, sm, mn, pp);
-    grid_reduce<NS, WX, WY, HU>(c, sm, s_sum, s_emax);
-    controller<S>(c, L, s_sum, *s_emax);
-    __syncthreads();
-    return true;
-}
 
 // One block covers a WX x WY window; 256-thread blocks are held to 128 registers so that two
 // of them are resident per SM.
@@ -471,52 +21,8 @@ __global__ void __launch_bounds__(WX *WY, (MinBlocks<NS, WX * WY>::value)) run_k
     __shared__ double s_sum[2 * MAXN];
     __shared__ float s_emax;
     __shared__ int s_stop;
-    if (threadIdx.x == 0) load_local(c, L);
-    if (threadIdx.x < c.nmodes) {
-        const int n = threadIdx.x;
-        double w = c.omega[0], ka = c.kappa[0], gr = c.gre[0], gi = c.gim[0];
-#pragma unroll
-        for (int u = 1; u < MAXN; u++)
-            if (n == u) {
-                w = c.omega[u];
-                ka = c.kappa[u];
-                gr = c.gre[u];
-                gi = c.gim[u];
-            }
-        L.mc[4 * n] = w;
-        L.mc[4 * n + 1] = ka;
-        L.mc[4 * n + 2] = gr;
-        L.mc[4 * n + 3] = gi;
-    }
-    {
-        const int sb = __ldg(&c.seg_begin[blockIdx.x]), se = __ldg(&c.seg_begin[blockIdx.x + 1]);
-        if (threadIdx.x == 0) sm.nseg = se - sb;
-        for (int t = threadIdx.x; t < se - sb; t += WX * WY) sm.seg[t] = __ldg(&c.tiles[sb + t]);
-    }
-    __syncthreads();
-    bool ok = true;
-    Pipe pp;
-    for (;;) {
-        if (threadIdx.x == 0) {
-            s_stop = L.status != 0 || L.done || ld_volatile_int(&c.ctl->status) != 0 ||
-                     (c.stage_only && L.k1_valid);
-            if (!s_stop) attempt_size(c, L);
-        }
-        __syncthreads();
-        if (s_stop) break;
-        if (!L.k1_valid) {
-            if (!(ok = run_stage<NS, WX, WY, HU, 1>(c, sm, L, cf, s_sum, &s_emax, pp, false)))
-                break;
-            if (c.stage_only) break;
-        }
-        if (!(ok = run_stage<NS, WX, WY, HU, 2>(c, sm, L, cf, s_sum, &s_emax, pp, false))) break;
-        if (!(ok = run_stage<NS, WX, WY, HU, 3>(c, sm, L, cf, s_sum, &s_emax, pp, true))) break;
-        if (!(ok = run_stage<NS, WX, WY, HU, 4>(c, sm, L, cf, s_sum, &s_emax, pp, true))) break;
-        if (!(ok = run_stage<NS, WX, WY, HU, 5>(c, sm, L, cf, s_sum, &s_emax, pp, true))) break;
-        if (!(ok = run_stage<NS, WX, WY, HU, 6>(c, sm, L, cf, s_sum, &s_emax, pp, true))) break;
-        if (!(ok = run_stage<NS, WX, WY, HU, 7>(c, sm, L, cf, s_sum, &s_emax, pp, true))) break;
-    }
-    if (ok && blockIdx.x == 0 && threadIdx.x == 0) store_local(c, L);
+    const Team tm{(int)blockIdx.x, (int)gridDim.x, &c.ctl->bar_count};
+    integrate<NS, WX, WY, HU>(c, tm, sm, L, cf, s_sum, s_emax, s_stop);
 }
 
 // ---------------------------------------------------------------------------------------------
