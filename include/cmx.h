@@ -45,7 +45,8 @@ typedef enum {
     CMX_ECUDA = 3,       /* a CUDA runtime call failed */
     CMX_ENAN = 4,        /* the error norm became NaN or Inf on the device */
     CMX_ESTEPFAIL = 5,   /* the step size fell below dt_min */
-    CMX_ETIMEOUT = 6     /* a device-side wait (grid barrier) exceeded its time limit */
+    CMX_ETIMEOUT = 6,    /* a device-side wait (grid barrier) exceeded its time limit */
+    CMX_ESCRATCH = 7     /* cmx_eval_rhs_noalloc: the problem does not fit the fixed scratch */
 } cmx_status;
 
 #define CMX_MAX_MODES 8
@@ -190,6 +191,34 @@ int cmx_get_tiling(const cmx_problem *h, int *bx, int *by, int *bz, int *blocks,
 
 const char *cmx_last_error(const cmx_problem *h);
 const char *cmx_status_string(int status);
+
+/* ------------------------------------------------------------------------------------------
+ * Right-hand-side evaluation without device allocation (no counterpart in the paper).
+ *
+ * For callers that cannot call cudaMalloc: code that runs while a stream is captured into a
+ * CUDA graph, plug-ins living inside a host program that owns the device allocator, processes
+ * under a fixed device-memory budget.  It computes the same f(m, a) as cmx_eval_rhs, with the
+ * same stage kernel, but allocates nothing: no cudaMalloc, no cudaFree, no allocating library
+ * routine.  Every scratch buffer (compact layout tables, compact m and slope, control block,
+ * block partials) is carved from one file-scope device array of CMX_NOALLOC_SCRATCH_BYTES
+ * (16 MiB), which every GPU that loads the library holds until the process exits.
+ *
+ * grid, mask (host), mat, modes (u host or device, or NULL): as for cmx_create.
+ * m: DEVICE pointer, dense box [nsub][3][nbox] float32 (read on `stream`).
+ * a: host, 2N doubles (NULL = zeros).  dm: DEVICE pointer, dense box like m, written with the
+ * slopes (0 outside the mask).  da, mm: host, 2N doubles each (may be NULL).
+ * stream: cudaStream_t (NULL = legacy default stream); the call waits for it before returning.
+ *
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress) with
+ * that device current; make that first call before any stream capture starts.  All calls share
+ * the one array and it keeps the last call's contents: calls that overlap on the GPU (other
+ * host threads, other streams) race and must be serialised by the caller.
+ * Returns CMX_ESCRATCH when the problem's buffers need more than CMX_NOALLOC_SCRATCH_BYTES
+ * (about 150k stored cells for one sublattice with no profiles), CMX_EINVAL on bad arguments. */
+#define CMX_NOALLOC_SCRATCH_BYTES (16u << 20)
+int cmx_eval_rhs_noalloc(const cmx_grid *grid, const uint8_t *mask, const cmx_material *mat,
+                         const cmx_modes *modes, const float *m, const double *a, float *dm,
+                         double *da, double *mm, void *stream);
 
 /* ------------------------------------------------------------------------------------------
  * Batched form: many independent problems (e.g. a field sweep across the anticrossing, Sec.

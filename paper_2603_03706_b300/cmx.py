@@ -16,7 +16,7 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libcmx.so")
 
-OK, EINVAL, ENOMEM, ECUDA, ENAN, ESTEPFAIL, ETIMEOUT = range(7)
+OK, EINVAL, ENOMEM, ECUDA, ENAN, ESTEPFAIL, ETIMEOUT, ESCRATCH = range(8)
 MAX_MODES = 8
 
 
@@ -120,6 +120,9 @@ SIGNATURES = {
     "cmx_batch_info": (C.c_int, [_P, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int),
                                  C.POINTER(C.c_longlong), C.POINTER(C.c_int)]),
     "cmx_batch_last_error": (C.c_char_p, [_P]),
+    "cmx_eval_rhs_noalloc": (C.c_int, [C.POINTER(Grid), C.c_void_p, C.POINTER(Material),
+                                       C.POINTER(Modes), C.c_void_p, C.c_void_p, C.c_void_p,
+                                       C.c_void_p, C.c_void_p, C.c_void_p]),
 }
 
 
@@ -533,3 +536,36 @@ class BatchSimulation:
         v = [C.c_int(), C.c_int(), C.c_int(), C.c_longlong(), C.c_int()]
         self._check(load().cmx_batch_info(self.h, *[C.byref(x) for x in v]), "batch_info")
         return dict(zip(("teams", "team_size", "blocks", "cells", "graph"), [x.value for x in v]))
+
+
+def eval_rhs_noalloc(p, m_dev, dm_dev, a=None, stream=None):
+    """cmx_eval_rhs_noalloc for a workloads.Problem: m_dev, dm_dev are device pointers (or CUDA
+    tensors) of dense-box float32 arrays.  Returns (da, mm) complex; raises CmxError."""
+    lib = load()
+    g = Grid(p.nx, p.ny, p.nz, p.cx, p.cy, p.cz, p.nsub)
+    mt = Material(p.Ms, p.Aex, p.alpha, p.gamma, p.Ku, (C.c_double * 3)(*p.ku_axis),
+                  (C.c_double * 3)(*p.B0), (C.c_double * 3)(*p.Ndemag), p.BE)
+    mask = np.ascontiguousarray(np.asarray(p.mask, np.uint8).reshape(-1))
+    om, ka, gr, gi = _f64(p.omega), _f64(p.kappa), _f64(p.g_re), _f64(p.g_im)
+    md = Modes()
+    md.n_modes = p.nmodes
+    md.omega, md.kappa, md.g_re, md.g_im = _dptr(om), _dptr(ka), _dptr(gr), _dptr(gi)
+    uu = None
+    if p.u is not None:
+        uu = _f32(p.u)
+        md.u, md.u_on_device = uu.ctypes.data, 0
+    else:
+        md.u, md.u_on_device = None, 0
+    N = p.nmodes
+    aa = np.zeros(max(2 * N, 1))
+    if a is not None and N:
+        ac = np.asarray(a).reshape(-1)
+        aa[0:2 * N:2], aa[1:2 * N:2] = ac.real, ac.imag
+    da = np.zeros(max(2 * N, 1))
+    mm = np.zeros(max(2 * N, 1))
+    rc = lib.cmx_eval_rhs_noalloc(C.byref(g), mask.ctypes.data, C.byref(mt), C.byref(md),
+                                  _dev_ptr(m_dev), aa.ctypes.data, _dev_ptr(dm_dev),
+                                  da.ctypes.data, mm.ctypes.data, _stream_handle(stream))
+    if rc != OK:
+        raise CmxError(rc, "cmx_eval_rhs_noalloc: " + lib.cmx_status_string(rc).decode())
+    return _unpack_complex(da, N), _unpack_complex(mm, N)

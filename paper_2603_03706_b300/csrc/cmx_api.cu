@@ -348,6 +348,7 @@ const char *cmx_status_string(int s)
     case CMX_ENAN: return "NaN in error norm";
     case CMX_ESTEPFAIL: return "step size underflow";
     case CMX_ETIMEOUT: return "device wait timed out";
+    case CMX_ESCRATCH: return "problem exceeds the fixed scratch of cmx_eval_rhs_noalloc";
     default: return "unknown status";
     }
 }
