@@ -17,6 +17,8 @@
  *                    + diagonal demag + B_rf (+ inter-sublattice exchange -B_E m_other, AFM,
  *                    Sec. II G); for two sublattices the cavity couples to (m1 + m2)/2.
  *   time stepping    Dormand-Prince 5(4), FSAL; the paper only says "adaptive RK45" (Sec. III A).
+ *   adjoint          orc_rhs_vjp / orc_adjoint: reverse-mode derivative of the replayed steps
+ *                    (not in the paper; the gradient form added beside the integrator).
  *
  * Readings where the paper is silent (each also listed in the design notes):
  *   - coupling sign +i g~ (Eq. (1)); complex g~ = g - i g_d feeds back through Re[g~ a]
@@ -481,4 +483,359 @@ int orc_replay(const orc_problem *P, orc_state *S, const orc_solver *sv, const d
         log_attempt(L, S, S->t, dts[i], err, 1);
     }
     return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------------------------- */
+/* Discrete adjoint (reverse mode) of a replayed Dormand-Prince step sequence.                  */
+/* Not in the paper: it differentiates exactly the computation above (stages, FSAL slope taken  */
+/* at the un-normalised 5th-order point, renormalisation of m on accept) with the step sizes     */
+/* held fixed.                                                                                  */
+/* ------------------------------------------------------------------------------------------- */
+
+/* Parameter gradients; every pointer may be NULL.  The routines below ADD into them. */
+typedef struct {
+    double *g_re, *g_im, *kappa, *omega; /* nmodes each: dL/d Re g~_n, dL/d Im g~_n, ... */
+    double *alpha;                       /* 1 */
+    double *u;                           /* nmodes * nbox (only with profiles) */
+} orc_grads;
+
+/*
+ * Vector-Jacobian product of orc_rhs at (m, a).  Given adjoint weights wm (layout of m) on the
+ * slopes dm and wa (2N) on da, ADDS (df/dm)^T w to gm, (df/da)^T w to ga and (df/dtheta)^T w to
+ * the parameter gradients.  Each term of the forward evaluation is transposed on its own, in
+ * scatter form: the forward adds w_d (m_j - m_i) to B_i for every in-mask neighbour j, so its
+ * transpose adds w_d Bbar_i to gm_j and subtracts it from gm_i.
+ */
+int orc_rhs_vjp(const orc_problem *P, const double *m, const double *a, const double *wm,
+                const double *wa, double *gm, double *ga, orc_grads *G)
+{
+    const int nx = P->nx, ny = P->ny, nz = P->nz, ns = P->nsub, N = P->nmodes;
+    const long nbox = (long)nx * ny * nz;
+    const double opa = 1.0 + P->alpha * P->alpha;
+    const double pre = -P->gamma / opa;
+    const double exch = 2.0 * P->Aex / P->Ms;
+    const double wx = exch / (P->cx * P->cx), wy = exch / (P->cy * P->cy),
+                 wz = exch / (P->cz * P->cz);
+    const double anis = 2.0 * P->Ku / P->Ms;
+    const double dmg = ORC_MU0 * P->Ms;
+    if (N > 64 || ns < 1 || ns > 2) return ORC_EINVAL;
+    const int want_u = P->u && G && G->u;
+    double hrf[64], hbar[64], mm[128];
+    for (int n = 0; n < N; n++) {
+        hrf[n] = 2.0 / P->gamma * (P->g_re[n] * a[2 * n] - P->g_im[n] * a[2 * n + 1]);
+        hbar[n] = 0.0;
+    }
+    orc_overlap(P, m, mm);
+    double *Bb = calloc((size_t)ns * 3 * nbox, sizeof(double));
+    if (!Bb) return ORC_ENOMEM;
+    const int dx[6] = {-1, 1, 0, 0, 0, 0}, dy[6] = {0, 0, -1, 1, 0, 0}, dz[6] = {0, 0, 0, 0, -1, 1};
+
+    /* pass 1: the field B of every cell (as in orc_rhs), the torque's local transpose and the
+       adjoint of the field, Bbar = (dT/dB)^T w */
+    double galpha = 0.0;
+    for (int z = 0; z < nz; z++)
+        for (int y = 0; y < ny; y++)
+            for (int x = 0; x < nx; x++) {
+                long c = x + (long)nx * (y + (long)ny * z);
+                if (!P->mask[c]) continue;
+                double brf = 0.0;
+                for (int n = 0; n < N; n++) brf += profile(P, n, c) * hrf[n];
+                double mtot[3] = {0, 0, 0};
+                for (int s = 0; s < ns; s++)
+                    for (int k = 0; k < 3; k++) mtot[k] += m[(s * 3 + k) * nbox + c];
+                for (int s = 0; s < ns; s++) {
+                    const double *ms = m + (long)s * 3 * nbox;
+                    double mi[3] = {ms[c], ms[nbox + c], ms[2 * nbox + c]};
+                    double B[3] = {0, 0, 0};
+                    for (int q = 0; q < 6; q++) {
+                        int xx = x + dx[q], yy = y + dy[q], zz = z + dz[q];
+                        if (!in_mask(P, xx, yy, zz)) continue;
+                        long j = xx + (long)nx * (yy + (long)ny * zz);
+                        double w = dx[q] ? wx : (dy[q] ? wy : wz);
+                        for (int k = 0; k < 3; k++) B[k] += w * (ms[k * nbox + j] - mi[k]);
+                    }
+                    double mk = mi[0] * P->ku[0] + mi[1] * P->ku[1] + mi[2] * P->ku[2];
+                    for (int k = 0; k < 3; k++) B[k] += anis * mk * P->ku[k];
+                    for (int k = 0; k < 3; k++) B[k] += P->B0[k] - dmg * P->Nd[k] * mtot[k];
+                    if (ns == 2) {
+                        const double *mo = m + (long)(1 - s) * 3 * nbox;
+                        for (int k = 0; k < 3; k++) B[k] -= P->BE * mo[k * nbox + c];
+                    }
+                    B[0] += brf;
+                    double w[3];
+                    for (int k = 0; k < 3; k++) w[k] = wm[(s * 3 + k) * nbox + c];
+                    /* T = pre (T1 + alpha T2), T1 = m x B, T2 = m x T1 = m (m.B) - B (m.m) */
+                    double T1[3] = {mi[1] * B[2] - mi[2] * B[1], mi[2] * B[0] - mi[0] * B[2],
+                                    mi[0] * B[1] - mi[1] * B[0]};
+                    double T2[3] = {mi[1] * T1[2] - mi[2] * T1[1], mi[2] * T1[0] - mi[0] * T1[2],
+                                    mi[0] * T1[1] - mi[1] * T1[0]};
+                    double mB = mi[0] * B[0] + mi[1] * B[1] + mi[2] * B[2];
+                    double wmi = w[0] * mi[0] + w[1] * mi[1] + w[2] * mi[2];
+                    double wB = w[0] * B[0] + w[1] * B[1] + w[2] * B[2];
+                    double mmi = mi[0] * mi[0] + mi[1] * mi[1] + mi[2] * mi[2];
+                    /* w . T1 = m . (B x w)  ->  d/dm = B x w,  d/dB = w x m */
+                    double Bxw[3] = {B[1] * w[2] - B[2] * w[1], B[2] * w[0] - B[0] * w[2],
+                                     B[0] * w[1] - B[1] * w[0]};
+                    /* w . T2 = (w.m)(m.B) - (w.B)(m.m) */
+                    for (int k = 0; k < 3; k++) {
+                        double dT2dm = w[k] * mB + wmi * B[k] - 2.0 * wB * mi[k];
+                        double dT2dB = wmi * mi[k] - mmi * w[k];
+                        gm[(s * 3 + k) * nbox + c] += pre * (Bxw[k] + P->alpha * dT2dm);
+                        Bb[(s * 3 + k) * nbox + c] = pre * P->alpha * dT2dB;
+                    }
+                    double wxm[3] = {w[1] * mi[2] - w[2] * mi[1], w[2] * mi[0] - w[0] * mi[2],
+                                     w[0] * mi[1] - w[1] * mi[0]};
+                    for (int k = 0; k < 3; k++) Bb[(s * 3 + k) * nbox + c] += pre * wxm[k];
+                    /* d pre / d alpha = -pre 2 alpha / (1 + alpha^2) */
+                    for (int k = 0; k < 3; k++) {
+                        double Tk = pre * (T1[k] + P->alpha * T2[k]);
+                        galpha += w[k] * (-2.0 * P->alpha / opa * Tk + pre * T2[k]);
+                    }
+                }
+            }
+
+    /* pass 2: transpose of the field B(m, a) */
+    for (int z = 0; z < nz; z++)
+        for (int y = 0; y < ny; y++)
+            for (int x = 0; x < nx; x++) {
+                long c = x + (long)nx * (y + (long)ny * z);
+                if (!P->mask[c]) continue;
+                for (int s = 0; s < ns; s++) {
+                    double bb[3];
+                    for (int k = 0; k < 3; k++) bb[k] = Bb[(s * 3 + k) * nbox + c];
+                    double *g = gm + (long)s * 3 * nbox;
+                    /* exchange */
+                    for (int q = 0; q < 6; q++) {
+                        int xx = x + dx[q], yy = y + dy[q], zz = z + dz[q];
+                        if (!in_mask(P, xx, yy, zz)) continue;
+                        long j = xx + (long)nx * (yy + (long)ny * zz);
+                        double w = dx[q] ? wx : (dy[q] ? wy : wz);
+                        for (int k = 0; k < 3; k++) {
+                            g[k * nbox + j] += w * bb[k];
+                            g[k * nbox + c] -= w * bb[k];
+                        }
+                    }
+                    /* anisotropy */
+                    double bk = bb[0] * P->ku[0] + bb[1] * P->ku[1] + bb[2] * P->ku[2];
+                    for (int k = 0; k < 3; k++) g[k * nbox + c] += anis * bk * P->ku[k];
+                    /* demag of the total moment: every sublattice */
+                    for (int s2 = 0; s2 < ns; s2++)
+                        for (int k = 0; k < 3; k++)
+                            gm[(s2 * 3 + k) * nbox + c] -= dmg * P->Nd[k] * bb[k];
+                    /* inter-sublattice exchange */
+                    if (ns == 2)
+                        for (int k = 0; k < 3; k++)
+                            gm[((1 - s) * 3 + k) * nbox + c] -= P->BE * bb[k];
+                    /* feedback B_x += sum_n u_n hrf_n */
+                    for (int n = 0; n < N; n++) {
+                        hbar[n] += profile(P, n, c) * bb[0];
+                        if (want_u) G->u[(long)n * nbox + c] += hrf[n] * bb[0];
+                    }
+                }
+            }
+    free(Bb);
+    if (G && G->alpha) *G->alpha += galpha;
+
+    /* hrf_n = (2/gamma) (Re g~ Re a - Im g~ Im a) */
+    for (int n = 0; n < N; n++) {
+        const double c2 = 2.0 / P->gamma * hbar[n];
+        ga[2 * n] += c2 * P->g_re[n];
+        ga[2 * n + 1] -= c2 * P->g_im[n];
+        if (G && G->g_re) G->g_re[n] += c2 * a[2 * n];
+        if (G && G->g_im) G->g_im[n] -= c2 * a[2 * n + 1];
+    }
+
+    /* cavity slopes: da_re = -k ar + w ai - (gr mi + gi mr), da_im = -k ai - w ar + (gr mr - gi mi) */
+    const double inv = 1.0 / ((double)count_cells(P) * ns);
+    for (int n = 0; n < N; n++) {
+        const double wr = wa[2 * n], wi = wa[2 * n + 1];
+        const double ar = a[2 * n], ai = a[2 * n + 1];
+        const double gr = P->g_re[n], gi = P->g_im[n], mr = mm[2 * n], mi = mm[2 * n + 1];
+        ga[2 * n] += -P->kappa[n] * wr - P->omega[n] * wi;
+        ga[2 * n + 1] += P->omega[n] * wr - P->kappa[n] * wi;
+        if (G && G->g_re) G->g_re[n] += -mi * wr + mr * wi;
+        if (G && G->g_im) G->g_im[n] += -mr * wr - mi * wi;
+        if (G && G->kappa) G->kappa[n] += -ar * wr - ai * wi;
+        if (G && G->omega) G->omega[n] += ai * wr - ar * wi;
+        const double mbr = -gi * wr + gr * wi, mbi = -gr * wr - gi * wi;
+        /* overlap: mm_re = inv sum u sum_s m_x, mm_im = -inv sum u sum_s m_y */
+        for (long c = 0; c < nbox; c++) {
+            if (!P->mask[c]) continue;
+            const double un = profile(P, n, c);
+            double sx = 0.0, sy = 0.0;
+            for (int s = 0; s < ns; s++) {
+                gm[(s * 3 + 0) * nbox + c] += inv * un * mbr;
+                gm[(s * 3 + 1) * nbox + c] -= inv * un * mbi;
+                sx += m[(s * 3 + 0) * nbox + c];
+                sy += m[(s * 3 + 1) * nbox + c];
+            }
+            if (want_u) G->u[(long)n * nbox + c] += inv * (mbr * sx - mbi * sy);
+        }
+    }
+    return ORC_OK;
+}
+
+/*
+ * Gradient of a loss L(a_0, ..., a_n, m_n) through n replayed steps of sizes dts from (m0, a0)
+ * (the states a_i after i steps; y_0 = (m0, a0) as given, not renormalised).
+ * dL_da: (n+1) x 2N, row i = dL/d a_i (NULL: zero); dL_dm: dL/d m_n (NULL: zero).
+ * Writes dL/d m0 (gm0, nvar) and dL/d a0 (ga0, 2N) and ADDS the parameter gradients to G.
+ * The state (m_i, a_i) and the FSAL slope k1_i of every step are kept; the reverse sweep
+ * recomputes the stages of step i from them and runs through the stages last to first:
+ *   stage point Y_s = y_i + h sum_{j<s} A_sj k_j,  k_s = f(Y_s) (s = 2..7; k_1 given),
+ *   y_{i+1} = (normalise(Y_7,m), Y_7,a),  k1_{i+1} = k_7.
+ * With F_s the adjoint of Y_s: F_7 = J_norm(Y_7)^T ybar_{i+1} + J_f(Y_7)^T k1bar_{i+1},
+ * F_s = J_f(Y_s)^T (h sum_{s'>s} A_s's F_s') for s = 6..2, and then
+ * ybar_i = sum_s F_s, k1bar_i = h sum_s A_s1 F_s.  Step 0's slope k1 = f(y_0) adds
+ * J_f(y_0)^T k1bar_0 at the end.
+ */
+int orc_adjoint(const orc_problem *P, const orc_solver *sv, const double *m0, const double *a0,
+                const double *dts, long n, const double *dL_da, const double *dL_dm,
+                double *gm0, double *ga0, orc_grads *G)
+{
+    orc_state *S = orc_state_new(P);
+    if (!S) return ORC_ENOMEM;
+    const long nv = S->nvar, nbox = S->nbox;
+    const int N = P->nmodes, na = 2 * (N > 0 ? N : 1), ns = P->nsub;
+    int rc = ORC_OK;
+    double *Mst = malloc((size_t)(n > 0 ? n : 1) * nv * sizeof(double));
+    double *Kst = malloc((size_t)(n > 0 ? n : 1) * nv * sizeof(double));
+    double *Ast = malloc((size_t)(n > 0 ? n : 1) * na * sizeof(double));
+    double *KAst = malloc((size_t)(n > 0 ? n : 1) * na * sizeof(double));
+    double *Ym[7], *Ya[7], *Fm[7], *Fa[7];
+    double *lm = calloc(nv, sizeof(double)), *la = calloc(na, sizeof(double));
+    double *lkm = calloc(nv, sizeof(double)), *lka = calloc(na, sizeof(double));
+    double *wkm = calloc(nv, sizeof(double)), *wka = calloc(na, sizeof(double));
+    int ok = Mst && Kst && Ast && KAst && lm && la && lkm && lka && wkm && wka;
+    for (int s = 0; s < 7; s++) {
+        Ym[s] = calloc(nv, sizeof(double));
+        Fm[s] = calloc(nv, sizeof(double));
+        Ya[s] = calloc(na, sizeof(double));
+        Fa[s] = calloc(na, sizeof(double));
+        ok = ok && Ym[s] && Fm[s] && Ya[s] && Fa[s];
+    }
+    if (!ok) {
+        rc = ORC_ENOMEM;
+        goto done;
+    }
+
+    /* forward: keep (m_i, a_i, k1_i) of every step */
+    orc_state_set(S, m0, a0, 0.0, n > 0 ? dts[0] : 1.0);
+    for (long i = 0; i < n; i++) {
+        double err;
+        memcpy(Mst + i * nv, S->m, nv * sizeof(double));
+        memcpy(Ast + i * na, S->a, 2 * N * sizeof(double));
+        rc = dp_attempt(P, S, sv, dts[i], &err);
+        if (rc) goto done;
+        memcpy(Kst + i * nv, S->km[0], nv * sizeof(double));
+        memcpy(KAst + i * na, S->ka[0], 2 * N * sizeof(double));
+        dp_accept(P, S, dts[i]);
+    }
+
+    /* reverse */
+    if (dL_dm) memcpy(lm, dL_dm, nv * sizeof(double));
+    if (dL_da) memcpy(la, dL_da + n * 2 * N, 2 * N * sizeof(double));
+    for (long i = n - 1; i >= 0; i--) {
+        const double h = dts[i];
+        double err;
+        memcpy(S->m, Mst + i * nv, nv * sizeof(double));
+        memcpy(S->a, Ast + i * na, 2 * N * sizeof(double));
+        memcpy(S->km[0], Kst + i * nv, nv * sizeof(double));
+        memcpy(S->ka[0], KAst + i * na, 2 * N * sizeof(double));
+        S->k1_valid = 1;
+        rc = dp_attempt(P, S, sv, h, &err);
+        if (rc) goto done;
+        /* stage points of stages 2..7 (0-based 1..6) */
+        for (int s = 1; s < 7; s++) {
+            for (long v = 0; v < nv; v++) {
+                double acc = S->m[v];
+                for (int j = 0; j < s; j++) acc += h * DP_A[s][j] * S->km[j][v];
+                Ym[s][v] = acc;
+            }
+            for (int q = 0; q < 2 * N; q++) {
+                double acc = S->a[q];
+                for (int j = 0; j < s; j++) acc += h * DP_A[s][j] * S->ka[j][q];
+                Ya[s][q] = acc;
+            }
+            memset(Fm[s], 0, nv * sizeof(double));
+            memset(Fa[s], 0, na * sizeof(double));
+        }
+        /* stage 7: renormalisation of m, direct a, and the FSAL slope k1_{i+1} = k_7 */
+        for (int s = 0; s < ns; s++)
+            for (long c = 0; c < nbox; c++) {
+                if (!P->mask[c]) continue;
+                double y[3], l[3];
+                for (int k = 0; k < 3; k++) {
+                    y[k] = Ym[6][(s * 3 + k) * nbox + c];
+                    l[k] = lm[(s * 3 + k) * nbox + c];
+                }
+                const double r = sqrt(y[0] * y[0] + y[1] * y[1] + y[2] * y[2]);
+                const double nl = (y[0] * l[0] + y[1] * l[1] + y[2] * l[2]) / r;
+                for (int k = 0; k < 3; k++) Fm[6][(s * 3 + k) * nbox + c] = (l[k] - y[k] / r * nl) / r;
+            }
+        for (int q = 0; q < 2 * N; q++) Fa[6][q] = la[q];
+        rc = orc_rhs_vjp(P, Ym[6], Ya[6], lkm, lka, Fm[6], Fa[6], G);
+        if (rc) goto done;
+        for (int s = 5; s >= 1; s--) {
+            for (long v = 0; v < nv; v++) {
+                double acc = 0.0;
+                for (int t = s + 1; t < 7; t++) acc += h * DP_A[t][s] * Fm[t][v];
+                wkm[v] = acc;
+            }
+            for (int q = 0; q < 2 * N; q++) {
+                double acc = 0.0;
+                for (int t = s + 1; t < 7; t++) acc += h * DP_A[t][s] * Fa[t][q];
+                wka[q] = acc;
+            }
+            rc = orc_rhs_vjp(P, Ym[s], Ya[s], wkm, wka, Fm[s], Fa[s], G);
+            if (rc) goto done;
+        }
+        for (long v = 0; v < nv; v++) {
+            double sy = 0.0, sk = 0.0;
+            for (int s = 1; s < 7; s++) {
+                sy += Fm[s][v];
+                sk += h * DP_A[s][0] * Fm[s][v];
+            }
+            lm[v] = sy;
+            lkm[v] = sk;
+        }
+        for (int q = 0; q < 2 * N; q++) {
+            double sy = 0.0, sk = 0.0;
+            for (int s = 1; s < 7; s++) {
+                sy += Fa[s][q];
+                sk += h * DP_A[s][0] * Fa[s][q];
+            }
+            la[q] = sy + (dL_da ? dL_da[i * 2 * N + q] : 0.0);
+            lka[q] = sk;
+        }
+    }
+    if (n == 0 && dL_da)
+        for (int q = 0; q < 2 * N; q++) la[q] = dL_da[q];
+    /* step 0 evaluated its first slope at y_0 */
+    if (n > 0) {
+        rc = orc_rhs_vjp(P, m0, a0, lkm, lka, lm, la, G);
+        if (rc) goto done;
+    }
+    if (gm0) memcpy(gm0, lm, nv * sizeof(double));
+    if (ga0) memcpy(ga0, la, 2 * N * sizeof(double));
+
+done:
+    free(Mst);
+    free(Kst);
+    free(Ast);
+    free(KAst);
+    free(lm);
+    free(la);
+    free(lkm);
+    free(lka);
+    free(wkm);
+    free(wka);
+    for (int s = 0; s < 7; s++) {
+        free(Ym[s]);
+        free(Ya[s]);
+        free(Fm[s]);
+        free(Fa[s]);
+    }
+    orc_state_free(S);
+    return rc;
 }

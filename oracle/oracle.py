@@ -12,6 +12,10 @@ Functions
 ``jacobian(op, m, a)``       central-difference Jacobian of the right-hand side (for the
                              linearised-eigenvalue pins, Sec. II B, F, G).
 ``tableau()``                the oracle's own Butcher tableau (for the order-condition pin).
+``rhs_vjp(op, m, a, wm, wa)`` transposed derivative of f applied to adjoint weights, with the
+                             parameter gradients (g~_n, kappa_n, omega_n, alpha, u_n(r)).
+``adjoint(op, m0, a0, dts, dL_da, dL_dm)``  gradient of a loss on the states a_0..a_n and m_n
+                             through n replayed steps (discrete adjoint, step sizes fixed).
 """
 from __future__ import annotations
 
@@ -62,6 +66,12 @@ class _Log(C.Structure):
                 ("mm", C.POINTER(C.c_double))]
 
 
+class _Grads(C.Structure):
+    _fields_ = [("g_re", C.POINTER(C.c_double)), ("g_im", C.POINTER(C.c_double)),
+                ("kappa", C.POINTER(C.c_double)), ("omega", C.POINTER(C.c_double)),
+                ("alpha", C.POINTER(C.c_double)), ("u", C.POINTER(C.c_double))]
+
+
 _lib = None
 
 
@@ -86,6 +96,12 @@ def lib():
         _lib.orc_replay.argtypes = [P, vp, C.POINTER(_Solver), dp, C.c_long, C.POINTER(_Log)]
         _lib.orc_replay.restype = C.c_int
         _lib.orc_tableau.argtypes = [dp, dp, dp]
+        G = C.POINTER(_Grads)
+        _lib.orc_rhs_vjp.argtypes = [P, dp, dp, dp, dp, dp, dp, G]
+        _lib.orc_rhs_vjp.restype = C.c_int
+        _lib.orc_adjoint.argtypes = [P, C.POINTER(_Solver), dp, dp, dp, C.c_long, dp, dp, dp,
+                                     dp, G]
+        _lib.orc_adjoint.restype = C.c_int
     return _lib
 
 
@@ -287,3 +303,81 @@ def jacobian(op: OracleProblem, m: np.ndarray, a: np.ndarray, h: float = 1e-5,
             an[q] -= h
             J[:, col] = (f(m, ap) - f(m, an)) / (2 * h)
     return J, idx
+
+
+class Grads:
+    """Parameter gradients filled by the adjoint routines (FP64): dL/d Re g~_n, dL/d Im g~_n,
+    dL/d kappa_n, dL/d omega_n (each N), dL/d alpha and, with profiles, dL/d u_n(r) (N x nbox)."""
+
+    def __init__(self, op: OracleProblem):
+        N = max(op.N, 1)
+        self.g_re, self.g_im = np.zeros(N), np.zeros(N)
+        self.kappa, self.omega = np.zeros(N), np.zeros(N)
+        self.alpha = np.zeros(1)
+        self.u = np.zeros((N, op.nbox)) if op.u is not None else None
+        s = _Grads()
+        s.g_re, s.g_im = _dptr(self.g_re), _dptr(self.g_im)
+        s.kappa, s.omega = _dptr(self.kappa), _dptr(self.omega)
+        s.alpha = _dptr(self.alpha)
+        s.u = _dptr(self.u) if self.u is not None else C.POINTER(C.c_double)()
+        self.s = s
+        self.N = op.N
+
+    def as_dict(self):
+        N = self.N
+        d = dict(g_re=self.g_re[:N].copy(), g_im=self.g_im[:N].copy(),
+                 kappa=self.kappa[:N].copy(), omega=self.omega[:N].copy(),
+                 alpha=float(self.alpha[0]))
+        d["u"] = None if self.u is None else self.u[:N].copy()
+        return d
+
+
+def rhs_vjp(op: OracleProblem, m, a, wm, wa):
+    """(df/dm)^T w, (df/da)^T w and the parameter parts at (m, a) for weights (wm, wa)."""
+    m = np.ascontiguousarray(m, np.float64).reshape(-1)
+    a = np.ascontiguousarray(a, np.float64).reshape(-1)
+    wm = np.ascontiguousarray(wm, np.float64).reshape(-1)
+    wa = np.ascontiguousarray(wa, np.float64).reshape(-1)
+    if a.size == 0:
+        a, wa = np.zeros(2), np.zeros(2)
+    gm = np.zeros_like(m)
+    ga = np.zeros(max(2 * op.N, 2))
+    g = Grads(op)
+    rc = lib().orc_rhs_vjp(op.ref, _dptr(m), _dptr(a), _dptr(wm), _dptr(wa), _dptr(gm),
+                           _dptr(ga), C.byref(g.s))
+    if rc:
+        raise RuntimeError(f"orc_rhs_vjp failed: {rc}")
+    d = g.as_dict()
+    d["m"], d["a"] = gm, ga[:2 * op.N]
+    return d
+
+
+def adjoint(op: OracleProblem, m0, a0, dts, dL_da=None, dL_dm=None):
+    """Gradient of L(a_0..a_n, m_n) through the replayed steps dts (n = len(dts)).
+
+    dL_da: (n+1, 2N) packed reals (row i = dL/d a_i) or None; dL_dm: flat like m or None.
+    Returns dict with m0, a0 (packed) and the parameter gradients of Grads.as_dict().
+    """
+    m0 = np.ascontiguousarray(m0, np.float64).reshape(-1)
+    a0 = np.ascontiguousarray(a0, np.float64).reshape(-1)
+    if a0.size == 0:
+        a0 = np.zeros(2)
+    dts = np.ascontiguousarray(dts, np.float64).reshape(-1)
+    n = len(dts)
+    null = C.POINTER(C.c_double)()
+    la = None if dL_da is None else np.ascontiguousarray(dL_da, np.float64).reshape(-1)
+    if la is not None and la.size != (n + 1) * 2 * op.N:
+        raise ValueError("dL_da must hold (n+1) x 2N values")
+    lm = None if dL_dm is None else np.ascontiguousarray(dL_dm, np.float64).reshape(-1)
+    gm0 = np.zeros_like(m0)
+    ga0 = np.zeros(max(2 * op.N, 2))
+    g = Grads(op)
+    rc = lib().orc_adjoint(op.ref, C.byref(op.solver), _dptr(m0), _dptr(a0), _dptr(dts), n,
+                           _dptr(la) if la is not None else null,
+                           _dptr(lm) if lm is not None else null, _dptr(gm0), _dptr(ga0),
+                           C.byref(g.s))
+    if rc:
+        raise RuntimeError(f"orc_adjoint failed: {rc}")
+    d = g.as_dict()
+    d["m0"], d["a0"] = gm0, ga0[:2 * op.N]
+    return d
