@@ -45,6 +45,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--adjoint-T", type=float, default=20e-9,
+                    help="end time of the adjoint measurement (64^3 sphere, 3 modes)")
+    ap.add_argument("--adjoint-every", type=int, default=200)
     return ap.parse_args()
 
 
@@ -203,6 +207,59 @@ def cpu_baseline(p, seconds):
                       f"({rhs} RHS evaluations x {p.ncells} cells) in {dt:.1f} s"}
 
 
+def adjoint_ratio(T, every, stream):
+    """Adjoint form on the 64^3 sphere with three profiled modes: wall time of the forward run
+    (adaptive, to T) and of the gradient of the cavity 1 -> 3 energy transfer with respect to
+    g~_n, kappa_n, omega_n, alpha, u_n(r), a_0 and m_0 (recompute + reverse sweep), each
+    bracketed by device synchronisation."""
+    import numpy as np
+    import torch
+    from paper_2603_03706_b300 import cmx
+    from paper_2603_03706_b300 import workloads as W
+    p = W.adjoint_sphere(T=T)
+    sim = cmx.Simulation.from_problem(p, stream=stream, log_cap=400000)
+    # warm-up: a short recorded run and its gradient (allocations, module load)
+    sim.adjoint_record(every, 400000)
+    sim.run(20 * p.dt_max)
+    sim.adjoint(None, None, want_u=False, want_m0=False)
+    # plain forward
+    sim.set_state(p.m0, p.a0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    st_plain = sim.run(p.T)
+    torch.cuda.synchronize()
+    t_plain = time.perf_counter() - t0
+    # recorded forward + backward
+    sim.set_state(p.m0, p.a0)
+    sim.adjoint_record(every, 400000)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    st = sim.run(p.T)
+    torch.cuda.synchronize()
+    t_fwd = time.perf_counter() - t0
+    log = sim.get_log(cap=st["attempts"])
+    acc = log["accepted"]
+    n = int(acc.sum())
+    aT = log["a"][acc][-1]
+    e0 = abs(p.a0[0]) ** 2
+    la = np.zeros((n + 1, 2 * p.nmodes))
+    la[-1, 4:6] = 2 * np.array([aT[2].real, aT[2].imag]) / e0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    g = sim.adjoint(la, None)
+    torch.cuda.synchronize()
+    t_bwd = time.perf_counter() - t0
+    sim.close()
+    return {"ratio": t_bwd / t_plain, "unit": "backward s / forward s",
+            "forward_s": t_plain, "forward_recorded_s": t_fwd, "backward_s": t_bwd,
+            "total_over_forward": (t_fwd + t_bwd) / t_plain,
+            "workload": p.name, "T": p.T, "accepted_steps": n, "attempts": st_plain["attempts"],
+            "checkpoint_every": every, "cells": p.ncells, "modes": p.nmodes,
+            "loss": "energy transfer |a_3(T)|^2/|a_1(0)|^2",
+            "energy_transfer": float(abs(aT[2]) ** 2 / e0),
+            "dL_dg_re": [float(v) for v in g["g_re"]], "timing": "wall clock, synchronised"}
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -347,8 +404,11 @@ def main():
         }
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(p, args.cpu_seconds)
-        print(json.dumps(line))
     sim.close()
+    if rank == 0:
+        if not args.no_adjoint:
+            line["adjoint"] = adjoint_ratio(args.adjoint_T, args.adjoint_every, stream)
+        print(json.dumps(line))
     if world > 1:
         torch.distributed.destroy_process_group()
 

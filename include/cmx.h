@@ -284,6 +284,61 @@ int cmx_batch_info(const cmx_batch *b, int *teams, int *team_size, int *blocks,
                    long long *cells, int *graph);
 const char *cmx_batch_last_error(const cmx_batch *b);
 
+/* ---------------------------------------------------------------------------------------------
+ * Adjoint form: gradients through the accepted steps of a run
+ *
+ * The paper integrates forward only; this is the differentiation form built beside it.  For a
+ * loss L(a_0, a_1, ..., a_n, m_n) of the cavity amplitudes after every accepted step (a_0: the
+ * initial amplitudes) and the final magnetisation, cmx_adjoint returns dL/d(Re g~_n),
+ * dL/d(Im g~_n), dL/d kappa_n, dL/d omega_n, dL/d alpha, dL/d u_n(r) and dL/d(a_0, m_0): the
+ * discrete adjoint of exactly the computation the run performed (its stages, the FSAL slope of
+ * the un-normalised 5th-order point, the renormalisation of m on accept), with the accepted
+ * step sizes held fixed (a step-size change is not differentiated).
+ *
+ *   cmx_set_state(h, m0, ..., a0, t0);
+ *   cmx_adjoint_record(h, every, max_steps);  // arm the checkpoint store (allocates)
+ *   cmx_run(h, T, 0, &st);                    // forward; checkpoints every `every` accepted steps
+ *   cmx_adjoint(h, dL_da, dL_dm, 0, &grads);  // reverse sweep
+ *
+ * Memory: checkpoints hold 2 x nsub*3 FP32 per stored cell plus 6N doubles per slot
+ * (max_steps/every + 1 slots); the reverse sweep recomputes one checkpoint interval at a time and
+ * keeps its stage points (every x 6 x nsub*3 FP32 per stored cell) plus twelve per-cell arrays.
+ * ------------------------------------------------------------------------------------------- */
+
+/* Gradients written by cmx_adjoint.  Every pointer may be NULL (that gradient is skipped). */
+typedef struct {
+    double *g_re, *g_im;   /* host, n_modes each: dL/d Re g~_n, dL/d Im g~_n (rad/s)^-1 */
+    double *kappa, *omega; /* host, n_modes each */
+    double *alpha;         /* host, 1 */
+    double *a0;            /* host, 2N packed (Re, Im): dL/d a_0 */
+    float *m0;             /* dense nsub*3*nbox: dL/d m_0 of the normalised initial state; 0
+                              outside the mask */
+    int m0_on_device;      /* m0 is a device pointer */
+    double *u;             /* dense N*nbox: dL/d u_n(r); needs mode profiles; 0 outside */
+    int u_on_device;       /* u is a device pointer */
+} cmx_grads;
+
+/* Arm the checkpoint store for the next run: call after cmx_set_state and before any launch.
+ * every >= 1 accepted steps between checkpoints; max_steps bounds the accepted steps the run
+ * may take (a run that takes more makes cmx_adjoint fail with CMX_EINVAL).  cmx_set_state
+ * disarms it.  The run's step log must hold all of its attempts (solver.log_cap). */
+int cmx_adjoint_record(cmx_problem *h, int every, long long max_steps);
+
+/* Reverse sweep over the accepted steps of the run since cmx_adjoint_record.
+ * dL_da: host, (n+1) x 2N doubles, row i = dL/d a_i packed (Re, Im), n = accepted steps (the
+ *        a_i are the step log's amplitudes of the accepted attempts, a_0 the initial ones);
+ *        NULL = zero.
+ * dL_dm: dense nsub*3*nbox FP32, dL/d m_n (host, or device if dL_dm_on_device); NULL = zero.
+ * Writes the gradients requested in g.  The handle's own state (m, a, t) is not changed; the run
+ * may be differentiated again with another loss.  Errors: CMX_EINVAL if nothing was recorded,
+ * if the run took more than max_steps accepted steps or the step log overflowed; device errors
+ * as cmx_run (CMX_ETIMEOUT, CMX_ENAN). */
+int cmx_adjoint(cmx_problem *h, const double *dL_da, const float *dL_dm, int dL_dm_on_device,
+                cmx_grads *g);
+
+/* Accepted steps recorded since cmx_adjoint_record (n of the loss above). */
+int cmx_adjoint_steps(cmx_problem *h, long long *n);
+
 #ifdef __cplusplus
 }
 #endif

@@ -72,6 +72,13 @@ class BatchConfig(C.Structure):
                 ("use_graph", C.c_int)]
 
 
+class Grads(C.Structure):
+    _fields_ = [("g_re", C.c_void_p), ("g_im", C.c_void_p), ("kappa", C.c_void_p),
+                ("omega", C.c_void_p), ("alpha", C.c_void_p), ("a0", C.c_void_p),
+                ("m0", C.c_void_p), ("m0_on_device", C.c_int), ("u", C.c_void_p),
+                ("u_on_device", C.c_int)]
+
+
 class Step(C.Structure):
     _fields_ = [("t", C.c_double), ("dt", C.c_double), ("err", C.c_double),
                 ("accepted", C.c_int32), ("pad", C.c_int32)]
@@ -120,6 +127,9 @@ SIGNATURES = {
     "cmx_batch_info": (C.c_int, [_P, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int),
                                  C.POINTER(C.c_longlong), C.POINTER(C.c_int)]),
     "cmx_batch_last_error": (C.c_char_p, [_P]),
+    "cmx_adjoint_record": (C.c_int, [_P, C.c_int, C.c_longlong]),
+    "cmx_adjoint": (C.c_int, [_P, C.c_void_p, C.c_void_p, C.c_int, C.POINTER(Grads)]),
+    "cmx_adjoint_steps": (C.c_int, [_P, C.POINTER(C.c_longlong)]),
     "cmx_eval_rhs_noalloc": (C.c_int, [C.POINTER(Grid), C.c_void_p, C.POINTER(Material),
                                        C.POINTER(Modes), C.c_void_p, C.c_void_p, C.c_void_p,
                                        C.c_void_p, C.c_void_p, C.c_void_p]),
@@ -196,6 +206,7 @@ class Simulation:
             raise ValueError("mask size")
         om, ka, gr, gi = _f64(omega), _f64(kappa), _f64(g_re), _f64(g_im)
         self.N = len(om)
+        self.has_u = u is not None
         md = Modes()
         md.n_modes = self.N
         md.omega, md.kappa, md.g_re, md.g_im = _dptr(om), _dptr(ka), _dptr(gr), _dptr(gi)
@@ -380,6 +391,61 @@ class Simulation:
             out["a"] = (a[0::2] + 1j * a[1::2]).reshape(k, self.N)
             out["mm"] = (mm[0::2] + 1j * mm[1::2]).reshape(k, self.N)
         return out
+
+    # -- adjoint -----------------------------------------------------------------------------
+    def adjoint_record(self, every: int, max_steps: int):
+        """Arm the checkpoint store for the next run (right after set_state)."""
+        self._check(load().cmx_adjoint_record(self.h, int(every), int(max_steps)),
+                    "adjoint_record")
+
+    def adjoint_steps(self) -> int:
+        n = C.c_longlong()
+        self._check(load().cmx_adjoint_steps(self.h, C.byref(n)), "adjoint_steps")
+        return n.value
+
+    def adjoint(self, dL_da=None, dL_dm=None, want_u: bool = True, want_m0: bool = True) -> dict:
+        """Gradients of a loss through the recorded run (cmx_adjoint).
+
+        dL_da: (n+1, N) complex or (n+1, 2N) packed reals, dL/d a_i for the states after i
+        accepted steps; dL_dm: dense (nsub, 3, nz, ny, nx) FP32 or None.  Returns numpy arrays:
+        g_re, g_im, kappa, omega (N), alpha (float), a0 (N complex: dL/dRe + i dL/dIm), m0 (dense)
+        and u ((N, nz, ny, nx) float64, with mode profiles).
+        """
+        N = self.N
+        n = self.adjoint_steps()
+        la = None
+        if dL_da is not None:
+            d = np.asarray(dL_da)
+            if np.iscomplexobj(d):
+                d = np.stack([d.real, d.imag], -1)
+            la = _f64(d)
+            if la.size != (n + 1) * 2 * N:
+                raise ValueError(f"dL_da must hold {n + 1} x {2 * N} values")
+        lm = None if dL_dm is None else _f32(dL_dm)
+        if lm is not None and lm.size != 3 * self.nsub * self.nbox:
+            raise ValueError("dL_dm size")
+        out = {k: np.zeros(max(N, 1)) for k in ("g_re", "g_im", "kappa", "omega")}
+        alpha = np.zeros(1)
+        a0 = np.zeros(max(2 * N, 1))
+        m0 = np.zeros(3 * self.nsub * self.nbox, np.float32) if want_m0 else None
+        u = np.zeros(max(N, 1) * self.nbox) if (want_u and self.has_u) else None
+        g = Grads(out["g_re"].ctypes.data, out["g_im"].ctypes.data, out["kappa"].ctypes.data,
+                  out["omega"].ctypes.data, alpha.ctypes.data, a0.ctypes.data,
+                  m0.ctypes.data if m0 is not None else None, 0,
+                  u.ctypes.data if u is not None else None, 0)
+        self._check(load().cmx_adjoint(self.h, la.ctypes.data if la is not None else None,
+                                       lm.ctypes.data if lm is not None else None, 0,
+                                       C.byref(g)), "adjoint")
+        res = {k: v[:N].copy() for k, v in out.items()}
+        res["alpha"] = float(alpha[0])
+        res["a0"] = a0[0:2 * N:2] + 1j * a0[1:2 * N:2]
+        res["a0_packed"] = a0[:2 * N].copy()
+        res["n"] = n
+        if m0 is not None:
+            res["m0"] = m0.reshape((self.nsub, 3) + self.shape)
+        if u is not None:
+            res["u"] = u[:N * self.nbox].reshape((N,) + self.shape)
+        return res
 
     # -- configuration -----------------------------------------------------------------------
     def ncells(self):

@@ -9,56 +9,12 @@
 #include <string>
 #include <vector>
 
-#include "cmx_kernels.h"
-#include "cmx_layout.h"
+#include "cmx_problem.h"
 
 using namespace cmx;
+using namespace cmx_host;
 
-struct cmx_problem {
-    int dev = 0;
-    cudaStream_t stream = nullptr;
-    cmx_grid grid{};
-    cmx_material mat{};
-    cmx_solver sv{};
-    int N = 0;
-    double omega[MAXN]{}, kappa[MAXN]{}, gre[MAXN]{}, gim[MAXN]{};
-    long long nbox = 0;
-    int ncell = 0, ncell_mag = 0;
-    bool holes = false;
-    Layout lay;
-    // device buffers
-    int2 *rows = nullptr;
-    uint32_t *active = nullptr;
-    int *box_of_cell = nullptr;
-    int4 *tiles = nullptr;
-    int *seg_begin = nullptr;
-    int ntiles = 0;
-    float *u = nullptr;
-    float *mbuf[2] = {nullptr, nullptr};
-    float *kbuf[7] = {};
-    Ctl *ctl = nullptr;
-    float2 *part = nullptr;
-    float *errpart = nullptr;
-    cmx_step *log = nullptr;
-    double *log_a = nullptr, *log_mm = nullptr;
-    double *tr_t = nullptr, *tr_a = nullptr, *tr_mm = nullptr;
-    double *replay_dts = nullptr;
-    long long replay_cap = 0;
-    float *dense = nullptr;           // nsub*3*nbox scratch for dense <-> compact
-    // eval_rhs scratch
-    float *ev_m = nullptr, *ev_k = nullptr;
-    Ctl *ev_ctl = nullptr;
-    // launch shape
-    int bx = 32, by = 8, bz = 16, blocks = 0, bps = 0, nsm = 0;
-    long long launch_attempts = 4096;
-    long long timeout_ns = 2000000000LL;
-    int skip_block = -1;
-    int launches = 0;
-    std::string err;
-    Ctx base{};
-};
-
-namespace {
+namespace cmx_host {
 
 int fail(cmx_problem *h, int code, const char *fmt, ...)
 {
@@ -71,22 +27,6 @@ int fail(cmx_problem *h, int code, const char *fmt, ...)
         h->err = buf;
     }
     return code;
-}
-
-#define CU(call)                                                                           \
-    do {                                                                                   \
-        cudaError_t e_ = (call);                                                           \
-        if (e_ != cudaSuccess)                                                             \
-            return fail(h, e_ == cudaErrorMemoryAllocation ? CMX_ENOMEM : CMX_ECUDA,       \
-                        "%s failed: %s", #call, cudaGetErrorString(e_));                   \
-    } while (0)
-
-template <class T>
-cudaError_t dalloc(T **p, size_t n)
-{
-    *p = nullptr;
-    if (n == 0) n = 1;
-    return cudaMalloc((void **)p, n * sizeof(T));
 }
 
 __global__ void gather_kernel(const float *dense, float *compact, const int *box_of_cell,
@@ -112,6 +52,10 @@ __global__ void scatter_kernel(const float *compact, float *dense, const int *bo
         if (on) dense[q * nbox + box_of_cell[c]] = compact[i];
     }
 }
+
+}  // namespace cmx_host
+
+namespace {
 
 // Normalise the magnetic cells of a freshly set state (inputs need not be exact unit vectors).
 __global__ void normalise_kernel(float *m, const uint32_t *active, int ncell, int nsub)
@@ -152,7 +96,11 @@ __global__ void prep_kernel(Ctl *ctl, PrepArgs a)
     }
 }
 
-int grid_blocks(long long n) { return (int)std::min<long long>(4096, (n + 255) / 256); }
+}  // namespace
+
+int cmx_host::grid_blocks(long long n) { return (int)std::min<long long>(4096, (n + 255) / 256); }
+
+namespace {
 
 int setup_tiling(cmx_problem *h, const cmx_tiling *t)
 {
@@ -208,7 +156,9 @@ int setup_tiling(cmx_problem *h, const cmx_tiling *t)
     return CMX_OK;
 }
 
-Ctx make_ctx(const cmx_problem *h)
+}  // namespace
+
+Ctx cmx_host::make_ctx(const cmx_problem *h)
 {
     Ctx c = h->base;
     c.tiles = h->tiles;
@@ -221,6 +171,8 @@ Ctx make_ctx(const cmx_problem *h)
     return c;
 }
 
+namespace {
+
 int launch(cmx_problem *h, const PrepArgs &pa, const Ctx &c)
 {
     prep_kernel<<<1, 1, 0, h->stream>>>(c.ctl, pa);
@@ -232,12 +184,16 @@ int launch(cmx_problem *h, const PrepArgs &pa, const Ctx &c)
     return CMX_OK;
 }
 
-int read_ctl(cmx_problem *h, Ctl *out)
+}  // namespace
+
+int cmx_host::read_ctl(cmx_problem *h, Ctl *out)
 {
     CU(cudaMemcpyAsync(out, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, h->stream));
     CU(cudaStreamSynchronize(h->stream));
     return CMX_OK;
 }
+
+namespace {
 
 void fill_stats(const cmx_problem *h, const Ctl &c, cmx_stats *st)
 {
@@ -251,7 +207,9 @@ void fill_stats(const cmx_problem *h, const Ctl &c, cmx_stats *st)
     st->launches = h->launches;
 }
 
-int device_status(cmx_problem *h, const Ctl &c)
+}  // namespace
+
+int cmx_host::device_status(cmx_problem *h, const Ctl &c)
 {
     if (c.status == CMX_OK) return CMX_OK;
     if (c.status == CMX_ETIMEOUT)
@@ -262,6 +220,8 @@ int device_status(cmx_problem *h, const Ctl &c)
         return fail(h, CMX_ESTEPFAIL, "step size below dt_min at t=%g", c.t);
     return fail(h, c.status, "device status %d", c.status);
 }
+
+namespace {
 
 // Run launches until the integrator reports done because of T / replay end, an error, or the
 // attempt budget.
@@ -314,6 +274,7 @@ void free_all(cmx_problem *h)
         if (p) cudaFree(p);
     for (float *p : h->kbuf)
         if (p) cudaFree(p);
+    adj_free(h);
 }
 
 int reset_ctl(cmx_problem *h, const double *a, double t)
@@ -546,6 +507,9 @@ int cmx_set_state(cmx_problem *h, const float *m, int m_on_device, const double 
     normalise_kernel<<<grid_blocks((long long)nc), 256, 0, h->stream>>>(h->mbuf[0], h->active,
                                                                          h->ncell, h->grid.nsub);
     CU(cudaGetLastError());
+    // a new state ends any checkpoint recording for the adjoint
+    h->base.traj_m = h->base.traj_k = nullptr;
+    h->base.traj_a = nullptr;
     return reset_ctl(h, a, t);
 }
 
@@ -690,6 +654,10 @@ int cmx_eval_rhs(cmx_problem *h, const float *m, const double *a, float *dm, dou
     c.stage_only = 1;
     c.log_cap = 0;
     c.tr_cap = 0;
+    c.traj_m = c.traj_k = nullptr;
+    c.traj_a = nullptr;
+    c.rec_m = nullptr;
+    c.rec_a = nullptr;
     cudaError_t e = launch_single(c, h->bx, h->by, h->blocks, h->stream);
     if (e != cudaSuccess) return fail(h, CMX_ECUDA, "eval launch: %s", cudaGetErrorString(e));
     CU(cudaMemsetAsync(h->dense, 0, (size_t)nq * h->nbox * sizeof(float), h->stream));

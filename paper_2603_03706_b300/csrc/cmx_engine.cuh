@@ -119,6 +119,20 @@ __device__ __forceinline__ void attempt_size(const Ctx &c, Local &L)
     }
 }
 
+// Checkpoint slot that stage S of the current attempt writes, or -1: stage 1 of the first
+// attempt writes slot 0 (the initial state and its slope), stage 7 writes slot k when the
+// attempt would complete k * traj_every accepted steps.
+template <int S>
+__device__ __forceinline__ int checkpoint_slot(const Ctx &c, const Local &L)
+{
+    if (!c.traj_m || (S != 1 && S != 7)) return -1;
+    const long long k = L.accepted - c.traj_base;
+    long long slot = -1;
+    if (S == 1 && k == 0) slot = 0;
+    if (S == 7 && (k + 1) % c.traj_every == 0) slot = (k + 1) / c.traj_every;
+    return slot < c.traj_slots ? (int)slot : -1;
+}
+
 // Cavity right-hand side (-i w - kappa) a + i g~ mm for one mode (Eq. (12), (19)); the mode
 // constants come from the block's shared copy (w, kappa, Re g~, Im g~).
 __device__ __forceinline__ void cavity_rhs(const double *mc, int n, double ar, double ai,
@@ -165,6 +179,25 @@ __device__ void controller(const Ctx &c, const Team &tm, Local &L, const double 
     __syncthreads();
     if (tid != 0) return;
     L.rhs_evals += 1;
+    if (tm.rank == 0) {
+        // adjoint stores: a rejected attempt's checkpoint is overwritten by the accepted retry
+        const int slot = checkpoint_slot<S>(c, L);
+        if (slot >= 0 && c.traj_a) {
+            double *d = c.traj_a + (size_t)slot * 6 * N;
+            for (int q = 0; q < 2 * N; q++) {
+                d[q] = S == 7 ? L.as[q] : L.a[q];
+                d[2 * N + q] = L.ka[S - 1][q];
+                d[4 * N + q] = L.mm[q];
+            }
+        }
+        if (c.rec_a && L.replay && L.replay_pos < c.rec_steps) {
+            double *d = c.rec_a + ((size_t)L.replay_pos * 7 + (S - 1)) * 4 * N;
+            for (int q = 0; q < 2 * N; q++) {
+                d[q] = L.as[q];
+                d[2 * N + q] = L.mm[q];
+            }
+        }
+    }
     if (S == 1) {
         L.k1_valid = 1;
         for (int q = 0; q < 2 * N; q++) L.mm_n[q] = L.mm[q];
@@ -457,7 +490,12 @@ __device__ bool run_stage(const Ctx &c, const Team &tm, StageSmem<NS, WX, WY, HU
 #pragma unroll
     for (int n = 0; n < MAXN; n++) acc.re[n] = acc.im[n] = 0.f;
     acc.emax = 0.f;
-    tiles_run<NS, WX, WY, HU, S>(c, sm, (float *)sm.kp[S - 1], mn, mnew, cf, pp, acc);
+    // checkpoint slot and stage-record step written by this stage (adjoint stores only)
+    const int tslot = checkpoint_slot<S>(c, L);
+    const int rslot = (S >= 2 && c.rec_m && L.replay && L.replay_pos < c.rec_steps)
+                          ? (int)L.replay_pos : -1;
+    tiles_run<NS, WX, WY, HU, S>(c, sm, (float *)sm.kp[S - 1], mn, mnew, cf, pp, tslot, rslot,
+                                 acc);
     block_reduce<NS, WX, WY, HU>(c, tm, sm, acc);
     if (!grid_barrier<NS, WX, WY, HU>(c, tm, L, S)) return false;
     if (S >= 2 && S < 7 && !c.stage_only) tiles_begin<NS, WX, WY, HU, (S < 7 ? S + 1 : 7)>(c, sm, mn, pp);

@@ -100,6 +100,18 @@ struct Ctx {
     int tr_cap;
     long long timeout_ns;
     int stage_only;                  // 1: evaluate stage 1 once (cmx_eval_rhs) and stop
+    // Checkpoint store of the adjoint (NULL = off): slot k holds the state after
+    // k * traj_every accepted steps counted from traj_base (slot 0: the initial state):
+    // m (renormalised) and the FSAL slope k1, and a, k1^a and <m^-> at the slope's point.
+    float *traj_m, *traj_k;          // [slot][nsub*3][ncell]
+    double *traj_a;                  // [slot][3][2N]
+    long long traj_base;
+    int traj_every, traj_slots;
+    // Stage record of a replay (NULL = off): replay step j stores its stage points
+    // m_S (S = 2..7) and, for every stage it evaluates, a_S and <m^->_S.
+    float *rec_m;                    // [j][S-2][nsub*3][ncell]
+    double *rec_a;                   // [j][S-1][2][2N]
+    int rec_steps;
 };
 
 }  // namespace cmx

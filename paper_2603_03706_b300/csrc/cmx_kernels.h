@@ -22,6 +22,38 @@ int batch_blocks_per_sm(int nsub, int bx, int by);
 cudaError_t launch_batch_prep(Ctl *const *ctls, int n, long long max_attempts, cudaStream_t s);
 cudaError_t launch_batch_pending(Ctl *const *ctls, int n, int *pending, cudaStream_t s);
 
+// reverse sweep of the adjoint (cmx_adjoint.cu)
+// Scalar adjoint state in device memory, carried from one checkpoint interval to the previous.
+struct AdjCtl {
+    double abar[2 * MAXN];           // dL/d a at the current step boundary
+    double k1a[2 * MAXN];            // dL/d (cavity part of the FSAL slope)
+    double gacc[4 * MAXN];           // per mode: dL/d Re g~, dL/d Im g~, dL/d kappa, dL/d omega
+    double galpha;                   // dL/d alpha
+    unsigned int bar_count;          // arrival counter of the launch's barrier
+    int status;
+    int timeout_where;
+};
+
+struct AdjArgs {
+    Ctx f;                           // problem (tiles / seg_begin: the reverse partition)
+    const float *rec_m;              // stage points m_S, [j][S-2][nsub*3][ncell]
+    const double *rec_a;             // a_S, <m^->_S, [j][S-1][2][2N]
+    const double *dts;               // step sizes of the interval
+    const double *dL_da;             // [n+1][2N] by global state index, or NULL
+    const float *m_first;            // initial state (stage-1 point of global step 0)
+    const double *a_first;           // a_0, k1^a_0, <m^->(y_0): [3][2N]
+    float *F[5];                     // adjoints of the stage points of stages 3..7
+    float *mbar, *k1bar;             // dL/d m at the step boundary, dL/d (FSAL slope)
+    float *ubar;                     // [N][ncell] interval accumulator of dL/d u, or NULL
+    AdjCtl *ctl;
+    float2 *part;                    // [blocks][N+1] block partials
+    long long step0;                 // global index of the interval's first step
+    int nsteps;
+};
+cudaError_t launch_reverse(const AdjArgs &a, int blocks, cudaStream_t s);
+int reverse_blocks_per_sm(int nsub, bool has_u);
+constexpr int REV_WX = 32, REV_WY = 8;   // window of the reverse kernel
+
 // small helpers (cmx_api.cu)
 struct PrepArgs {
     double T;

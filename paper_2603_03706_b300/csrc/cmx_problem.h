@@ -1,0 +1,98 @@
+// Host-side state of one problem handle and the helpers shared by the C-ABI source files.
+#pragma once
+
+#include <string>
+
+#include "cmx_kernels.h"
+#include "cmx_layout.h"
+
+namespace cmx_host {
+struct AdjState;
+}
+
+using cmx::Ctl;
+using cmx::Ctx;
+using cmx::Layout;
+using cmx::MAXN;
+
+struct cmx_problem {
+    int dev = 0;
+    cudaStream_t stream = nullptr;
+    cmx_grid grid{};
+    cmx_material mat{};
+    cmx_solver sv{};
+    int N = 0;
+    double omega[MAXN]{}, kappa[MAXN]{}, gre[MAXN]{}, gim[MAXN]{};
+    long long nbox = 0;
+    int ncell = 0, ncell_mag = 0;
+    bool holes = false;
+    Layout lay;
+    // device buffers
+    int2 *rows = nullptr;
+    uint32_t *active = nullptr;
+    int *box_of_cell = nullptr;
+    int4 *tiles = nullptr;
+    int *seg_begin = nullptr;
+    int ntiles = 0;
+    float *u = nullptr;
+    float *mbuf[2] = {nullptr, nullptr};
+    float *kbuf[7] = {};
+    Ctl *ctl = nullptr;
+    float2 *part = nullptr;
+    float *errpart = nullptr;
+    cmx_step *log = nullptr;
+    double *log_a = nullptr, *log_mm = nullptr;
+    double *tr_t = nullptr, *tr_a = nullptr, *tr_mm = nullptr;
+    double *replay_dts = nullptr;
+    long long replay_cap = 0;
+    float *dense = nullptr;           // nsub*3*nbox scratch for dense <-> compact
+    // eval_rhs scratch
+    float *ev_m = nullptr, *ev_k = nullptr;
+    Ctl *ev_ctl = nullptr;
+    // launch shape
+    int bx = 32, by = 8, bz = 16, blocks = 0, bps = 0, nsm = 0;
+    long long launch_attempts = 4096;
+    long long timeout_ns = 2000000000LL;
+    int skip_block = -1;
+    int launches = 0;
+    std::string err;
+    Ctx base{};
+    cmx_host::AdjState *adj = nullptr;   // adjoint stores (cmx_adjoint_api.cu)
+};
+
+
+namespace cmx_host {
+
+using namespace cmx;
+
+// Record an error message on the handle and return the code.
+int fail(cmx_problem *h, int code, const char *fmt, ...);
+
+#define CU(call)                                                                           \
+    do {                                                                                   \
+        cudaError_t e_ = (call);                                                           \
+        if (e_ != cudaSuccess)                                                             \
+            return cmx_host::fail(h, e_ == cudaErrorMemoryAllocation ? CMX_ENOMEM : CMX_ECUDA, \
+                                  "%s failed: %s", #call, cudaGetErrorString(e_));         \
+    } while (0)
+
+template <class T>
+cudaError_t dalloc(T **p, size_t n)
+{
+    *p = nullptr;
+    if (n == 0) n = 1;
+    return cudaMalloc((void **)p, n * sizeof(T));
+}
+
+int grid_blocks(long long n);
+// dense box <-> compact cells, nq components
+__global__ void gather_kernel(const float *dense, float *compact, const int *box_of_cell,
+                              const uint32_t *active, int ncell, long long nbox, int nq);
+__global__ void scatter_kernel(const float *compact, float *dense, const int *box_of_cell,
+                               const uint32_t *active, int ncell, long long nbox, int nq);
+Ctx make_ctx(const cmx_problem *h);
+int read_ctl(cmx_problem *h, Ctl *out);
+int device_status(cmx_problem *h, const Ctl &c);
+void adj_free(cmx_problem *h);
+
+}  // namespace cmx_host

@@ -276,7 +276,8 @@ __device__ __forceinline__ void combine_plane(const Ctx &c, StageSmem<NS, WX, WY
 template <int NS, int WX, int WY, bool HU, int S>
 __device__ __forceinline__ void compute_cell(const Ctx &c, StageSmem<NS, WX, WY, HU> &sm,
                                              float *kout, float *mnew, const Coef &cf, int p,
-                                             const float *ucell, Acc &acc)
+                                             const float *ucell, int tslot, int rslot,
+                                             Acc &acc)
 {
     using SM = StageSmem<NS, WX, WY, HU>;
     constexpr int NQ = SM::NQ, R = SM::RING;
@@ -347,6 +348,20 @@ __device__ __forceinline__ void compute_cell(const Ctx &c, StageSmem<NS, WX, WY,
                              c.pre * fmaf(c.alpha, t2z, t1z)};
 #pragma unroll
         for (int k = 0; k < 3; k++) kout[(size_t)(s * 3 + k) * c.ncell + idx] = kv[k];
+        if (S >= 2 && rslot >= 0) {
+            const size_t o = ((size_t)rslot * 6 + (S >= 2 ? S - 2 : 0)) * NQ * c.ncell;
+#pragma unroll
+            for (int k = 0; k < 3; k++) c.rec_m[o + (size_t)(s * 3 + k) * c.ncell + idx] = mm[k];
+        }
+        if ((S == 1 || S == 7) && tslot >= 0) {
+            const size_t o = (size_t)tslot * NQ * c.ncell;
+            const float r = S == 7 ? rsqrtf(mm[0] * mm[0] + mm[1] * mm[1] + mm[2] * mm[2]) : 1.f;
+#pragma unroll
+            for (int k = 0; k < 3; k++) {
+                c.traj_m[o + (size_t)(s * 3 + k) * c.ncell + idx] = mm[k] * r;
+                c.traj_k[o + (size_t)(s * 3 + k) * c.ncell + idx] = kv[k];
+            }
+        }
         if (S == 7) {
             const float r = rsqrtf(mm[0] * mm[0] + mm[1] * mm[1] + mm[2] * mm[2]);
 #pragma unroll
@@ -407,7 +422,8 @@ __device__ void tiles_begin(const Ctx &c, StageSmem<NS, WX, WY, HU> &sm, const f
 // the next computed cell are loaded one plane ahead.
 template <int NS, int WX, int WY, bool HU, int S>
 __device__ void tiles_run(const Ctx &c, StageSmem<NS, WX, WY, HU> &sm, float *kout,
-                          const float *mn, float *mnew, const Coef &cf, Pipe &pp, Acc &acc)
+                          const float *mn, float *mnew, const Coef &cf, Pipe &pp, int tslot,
+                          int rslot, Acc &acc)
 {
     constexpr int D = StageSmem<NS, WX, WY, HU>::template depth<S>();
     constexpr int AHEAD = D + 3;
@@ -461,7 +477,7 @@ __device__ void tiles_run(const Ctx &c, StageSmem<NS, WX, WY, HU> &sm, float *ko
         for (int n = 0; n < MAXN; n++) ucur[n] = unext[n];
         load_u(p + 1, unext);
         __syncthreads();
-        compute_cell<NS, WX, WY, HU, S>(c, sm, kout, mnew, cf, p, ucur, acc);
+        compute_cell<NS, WX, WY, HU, S>(c, sm, kout, mnew, cf, p, ucur, tslot, rslot, acc);
     }
     cp_async_wait<0>();
 }
