@@ -97,16 +97,23 @@ typedef struct {
     int trace_cap;
 } cmx_solver;
 
-/* Launch shape.  bx, by: thread-block window in cells (one thread per window column; compiled
- * windows: 32x8, 32x16, 64x4, and 32x8, 64x4 for two sublattices).  A block computes the
- * (bx-2) x (by-2) interior columns, the one-cell rim is the exchange halo, and marches along z.
- * The columns' planes are split into contiguous per-block segments with equal plane counts.
+/* Launch shape.  Two window kinds march along z through columns of the grid:
+ *  - one cell per thread (quad = 0 or 1, the default): bx, by = thread window in cells
+ *    (compiled windows: 32x8, 32x16, 64x4, and 32x8, 32x16, 64x4 for two sublattices; bx = by =
+ *    0 selects 32x8); a block computes the (bx-2) x (by-2) interior columns, the one-cell rim is
+ *    the exchange halo;
+ *  - four x-cells per thread (quad = 4, one sublattice only): a window of bx/4 x by threads
+ *    (bx a multiple of 4, (bx/4) * by a multiple of 32 and at most 256, by <= 16; bx = by = 0
+ *    selects 64x16) computes (bx-8) x (by-2) interior cells with 16-byte operands; cells are
+ *    stored with rows aligned to 4 cells.  On B300 it runs one block per SM and is slower than
+ *    the default on the measured workloads.
+ * The columns' planes are split into contiguous per-block segments with balanced plane counts;
  * bz: the fewest planes per block (0 = 4); fewer blocks are used when the grid is small.
- * blocks_per_sm caps the resident blocks per SM (0 = as many as fit).  bx = by = 0 selects
- * the 32x8 window. */
+ * blocks_per_sm caps the resident blocks per SM (0 = as many as fit). */
 typedef struct {
     int bx, by, bz;
     int blocks_per_sm;   /* 0 = as many as fit */
+    int quad;            /* 0 or 1 = one cell per thread, 4 = four cells per thread */
 } cmx_tiling;
 
 typedef struct {
@@ -187,7 +194,8 @@ int cmx_set_timeout(cmx_problem *h, long long ns);
 int cmx_debug_skip_arrival(cmx_problem *h, int block);
 
 /* Launch shape actually used: bx, by, bz, grid blocks, tiles. */
-int cmx_get_tiling(const cmx_problem *h, int *bx, int *by, int *bz, int *blocks, int *tiles);
+int cmx_get_tiling(const cmx_problem *h, int *bx, int *by, int *bz, int *blocks, int *tiles,
+                   int *quad);
 
 const char *cmx_last_error(const cmx_problem *h);
 const char *cmx_status_string(int status);

@@ -50,7 +50,8 @@ class Solver(C.Structure):
 
 
 class Tiling(C.Structure):
-    _fields_ = [("bx", C.c_int), ("by", C.c_int), ("bz", C.c_int), ("blocks_per_sm", C.c_int)]
+    _fields_ = [("bx", C.c_int), ("by", C.c_int), ("bz", C.c_int), ("blocks_per_sm", C.c_int),
+                ("quad", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -109,7 +110,7 @@ SIGNATURES = {
     "cmx_set_timeout": (C.c_int, [_P, C.c_longlong]),
     "cmx_debug_skip_arrival": (C.c_int, [_P, C.c_int]),
     "cmx_get_tiling": (C.c_int, [_P, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int),
-                                 C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+                                   C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "cmx_last_error": (C.c_char_p, [_P]),
     "cmx_status_string": (C.c_char_p, [C.c_int]),
     "cmx_batch_create": (C.c_int, [C.POINTER(Instance), C.c_int, C.POINTER(Solver),
@@ -463,9 +464,9 @@ class Simulation:
         self._check(load().cmx_debug_skip_arrival(self.h, int(block)), "debug_skip_arrival")
 
     def get_tiling(self) -> dict:
-        v = [C.c_int() for _ in range(5)]
+        v = [C.c_int() for _ in range(6)]
         self._check(load().cmx_get_tiling(self.h, *[C.byref(x) for x in v]), "get_tiling")
-        return dict(zip(("bx", "by", "bz", "blocks", "tiles"), [x.value for x in v]))
+        return dict(zip(("bx", "by", "bz", "blocks", "tiles", "quad"), [x.value for x in v]))
 
     def last_error(self) -> str:
         return load().cmx_last_error(self.h).decode()

@@ -102,9 +102,39 @@ int cmx_host::grid_blocks(long long n) { return (int)std::min<long long>(4096, (
 
 namespace {
 
+int install_tiling(cmx_problem *h, const std::vector<Column> &cols, int blocks, int bx, int by,
+                   int bz, int occ);
+
 int setup_tiling(cmx_problem *h, const cmx_tiling *t)
 {
     int bx = 32, by = 8, bz = 0, bps = 0;
+    if (h->quad) {
+        int wq = 0, wy = 0;
+        if (t) {
+            bz = t->bz;
+            bps = t->blocks_per_sm;
+        }
+        if (bz <= 0) bz = 4;
+        wq = 16;   // default quad window: 64 x 16 cells
+        wy = 16;
+        if (t && (t->bx || t->by)) {
+            if (t->bx % 4 || !quad_shape_supported(t->bx / 4, t->by))
+                return fail(h, CMX_EINVAL,
+                            "quad window %dx%d: bx must be a multiple of 4 with (bx/4)*by a "
+                            "multiple of 32, at most 256 threads, by <= 16", t->bx, t->by);
+            wq = t->bx / 4;
+            wy = t->by;
+        }
+        int occ = quad_blocks_per_sm(wq, wy, h->u ? h->N : 0);
+        if (occ <= 0) return fail(h, CMX_ECUDA, "occupancy query failed for quad %dx%d", wq, wy);
+        if (bps > 0) occ = std::min(occ, bps);
+        const std::vector<Column> cols = build_columns(h->lay, 4 * (wq - 2) + 2, wy);
+        long long P = 0;
+        for (const Column &c : cols) P += c.zhi - c.zlo;
+        const long long cap = (long long)occ * h->nsm;
+        const int blocks = (int)std::max<long long>(1, std::min<long long>(cap, (P + bz - 1) / bz));
+        return install_tiling(h, cols, blocks, 4 * wq, wy, bz, occ);
+    }
     if (t && (t->bx || t->by)) {
         bx = t->bx;
         by = t->by;
@@ -127,6 +157,13 @@ int setup_tiling(cmx_problem *h, const cmx_tiling *t)
     if (bz <= 0) bz = 4;
     const long long cap = (long long)occ * h->nsm;
     const int blocks = (int)std::max<long long>(1, std::min<long long>(cap, (P + bz - 1) / bz));
+    return install_tiling(h, cols, blocks, bx, by, bz, occ);
+}
+
+// Partition the columns among `blocks` blocks and upload the segments; record the shape.
+int install_tiling(cmx_problem *h, const std::vector<Column> &cols, int blocks, int bx, int by,
+                   int bz, int occ)
+{
     std::vector<int4> segs;
     std::vector<int> begin;
     build_segments(cols, blocks, segs, begin);
@@ -323,7 +360,7 @@ int cmx_create(const cmx_grid *grid, const uint8_t *mask, const cmx_material *ma
     if (!out) return CMX_EINVAL;
     *out = nullptr;
     if (!grid || !mask || !mat || !solver) return CMX_EINVAL;
-    if (grid->nx <= 0 || grid->ny <= 0 || grid->nz <= 0 || grid->nx > 65535 ||
+    if (grid->nx <= 0 || grid->ny <= 0 || grid->nz <= 0 || grid->nx > 65532 ||
         (grid->nsub != 1 && grid->nsub != 2) || !(grid->cx > 0) || !(grid->cy > 0) ||
         !(grid->cz > 0))
         return CMX_EINVAL;
@@ -363,7 +400,12 @@ int cmx_create(const cmx_grid *grid, const uint8_t *mask, const cmx_material *ma
     cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, h->dev);
     if (!coop) return bail(CMX_ECUDA);
 
-    build_layout(h->lay, grid->nx, grid->ny, grid->nz, mask);
+    // window kind: one cell per thread unless quad windows are asked for
+    const int tq = tiling ? tiling->quad : 0;
+    if (tq != 0 && tq != 1 && tq != 4) return bail(CMX_EINVAL);
+    if (tq == 4 && grid->nsub != 1) return bail(CMX_EINVAL);
+    h->quad = tq == 4;
+    build_layout(h->lay, grid->nx, grid->ny, grid->nz, mask, h->quad ? 4 : 1);
     h->ncell = h->lay.ncell;
     h->ncell_mag = h->lay.ncell_mag;
     h->holes = h->lay.holes;
@@ -463,6 +505,7 @@ int cmx_create(const cmx_grid *grid, const uint8_t *mask, const cmx_material *ma
     c.tr_a = h->tr_a;
     c.tr_mm = h->tr_mm;
     c.tr_cap = solver->trace_cap;
+    c.quad = h->quad;
 
     int rc = setup_tiling(h, tiling);
     if (rc) return bail(rc);
@@ -705,9 +748,11 @@ int cmx_debug_skip_arrival(cmx_problem *h, int block)
     return CMX_OK;
 }
 
-int cmx_get_tiling(const cmx_problem *h, int *bx, int *by, int *bz, int *blocks, int *tiles)
+int cmx_get_tiling(const cmx_problem *h, int *bx, int *by, int *bz, int *blocks, int *tiles,
+                   int *quad)
 {
     if (!h) return CMX_EINVAL;
+    if (quad) *quad = h->quad ? 4 : 1;
     if (bx) *bx = h->bx;
     if (by) *by = h->by;
     if (bz) *bz = h->bz;

@@ -29,7 +29,7 @@ __global__ void __launch_bounds__(WX *WY, (WX * WY <= 256 ? 2 : 1)) batch_kernel
             dst[w] = __ldg(src + w);
         __syncthreads();
         const Team tm{rank, B.team_size, &sc.ctl->bar_count};
-        integrate<NS, WX, WY, false>(sc, tm, sm, L, cf, s_sum, s_emax, s_stop);
+        integrate(sc, tm, sm, L, cf, s_sum, s_emax, s_stop);
     }
 }
 

@@ -306,11 +306,10 @@ __device__ void controller(const Ctx &c, const Team &tm, Local &L, const double 
 
 // Block sum of the per-thread overlap accumulators (compensated pairs, fixed shuffle order)
 // and block max of |e_m|, written to the block's slot of c.part / c.errpart.
-template <int NS, int WX, int WY, bool HU>
-__device__ void block_reduce(const Ctx &c, const Team &tm, StageSmem<NS, WX, WY, HU> &sm,
-                             const Acc &acc)
+template <class SM>
+__device__ void block_reduce(const Ctx &c, const Team &tm, SM &sm, const Acc &acc)
 {
-    constexpr int NT = WX * WY, NW = NT / 32;
+    const int NT = blockDim.x, NW = NT / 32;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int n = 0; n < MAXN; n++) {
@@ -354,11 +353,10 @@ __device__ __forceinline__ void red_add_release(unsigned *p, unsigned v)
 // same values.  Thread t sums component q = t mod QP of blocks b = t/QP, t/QP + NT/QP, ...
 // (QP = 2N rounded up to a power of two); lanes of equal q are then combined by shuffles and
 // the warps in order.
-template <int NS, int WX, int WY, bool HU>
-__device__ void grid_reduce(const Ctx &c, const Team &tm, StageSmem<NS, WX, WY, HU> &sm,
-                            double *out, float *emax)
+template <class SM>
+__device__ void grid_reduce(const Ctx &c, const Team &tm, SM &sm, double *out, float *emax)
 {
-    constexpr int NT = WX * WY, NW = NT / 32;
+    const int NT = blockDim.x, NW = NT / 32;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int Q = 2 * c.nmodes, G = tm.nblk;
     int QP = 1;
@@ -408,7 +406,7 @@ __device__ void grid_reduce(const Ctx &c, const Team &tm, StageSmem<NS, WX, WY, 
 // by c.timeout_ns: on time-out the block sets CMX_ETIMEOUT and the run stops.  The block's
 // partials were written before the __syncthreads that precedes the release-add.  Returns false
 // if the run must stop.
-template <int NS, int WX, int WY, bool HU>
+template <class SM>
 __device__ bool grid_barrier(const Ctx &c, const Team &tm, Local &L, int where)
 {
     __shared__ int s_ok;
@@ -457,9 +455,9 @@ __device__ __forceinline__ const float *slope_buffer(const Ctx &c, int kj)
 // One stage.  If `begun`, the copy pipeline of this stage was started by the previous stage
 // (right after its barrier).  After the barrier this stage starts the next one (S < 7) before
 // it reduces the partials and updates the cavity, so those latencies overlap the first copies.
-template <int NS, int WX, int WY, bool HU, int S>
-__device__ bool run_stage(const Ctx &c, const Team &tm, StageSmem<NS, WX, WY, HU> &sm, Local &L,
-                          Coef &cf, double *s_sum, float *s_emax, Pipe &pp, bool begun)
+template <int S, class SM>
+__device__ bool run_stage(const Ctx &c, const Team &tm, SM &sm, Local &L, Coef &cf,
+                          double *s_sum, float *s_emax, Pipe &pp, bool begun)
 {
     const int tid = threadIdx.x, N = c.nmodes;
     const double h = L.h;
@@ -468,7 +466,7 @@ __device__ bool run_stage(const Ctx &c, const Team &tm, StageSmem<NS, WX, WY, HU
     if (!begun) {
         if (tid < 7) sm.kp[tid] = slope_buffer(c, L.kphys[tid]);
         __syncthreads();
-        tiles_begin<NS, WX, WY, HU, S>(c, sm, mn, pp);
+        stage_begin<S>(c, sm, mn, pp);
     }
     // cavity stage value a_S = a_n + h sum_j a_Sj k^a_j (FP64, one thread per real component)
     if (tid < 2 * N) {
@@ -494,12 +492,11 @@ __device__ bool run_stage(const Ctx &c, const Team &tm, StageSmem<NS, WX, WY, HU
     const int tslot = checkpoint_slot<S>(c, L);
     const int rslot = (S >= 2 && c.rec_m && L.replay && L.replay_pos < c.rec_steps)
                           ? (int)L.replay_pos : -1;
-    tiles_run<NS, WX, WY, HU, S>(c, sm, (float *)sm.kp[S - 1], mn, mnew, cf, pp, tslot, rslot,
-                                 acc);
-    block_reduce<NS, WX, WY, HU>(c, tm, sm, acc);
-    if (!grid_barrier<NS, WX, WY, HU>(c, tm, L, S)) return false;
-    if (S >= 2 && S < 7 && !c.stage_only) tiles_begin<NS, WX, WY, HU, (S < 7 ? S + 1 : 7)>(c, sm, mn, pp);
-    grid_reduce<NS, WX, WY, HU>(c, tm, sm, s_sum, s_emax);
+    stage_run<S>(c, sm, (float *)sm.kp[S - 1], mn, mnew, cf, pp, tslot, rslot, acc);
+    block_reduce(c, tm, sm, acc);
+    if (!grid_barrier<SM>(c, tm, L, S)) return false;
+    if (S >= 2 && S < 7 && !c.stage_only) stage_begin<(S < 7 ? S + 1 : 7)>(c, sm, mn, pp);
+    grid_reduce(c, tm, sm, s_sum, s_emax);
     controller<S>(c, tm, L, s_sum, *s_emax);
     __syncthreads();
     return true;
@@ -509,9 +506,9 @@ __device__ bool run_stage(const Ctx &c, const Team &tm, StageSmem<NS, WX, WY, HU
 // this block's segments and the mode constants, then run Dormand-Prince attempts until the
 // problem is done (t >= T, replay end, attempt budget of the launch, or an error).  The team's
 // rank-0 block writes the state back.  Returns false if the run stopped on a device error.
-template <int NS, int WX, int WY, bool HU>
-__device__ bool integrate(const Ctx &c, const Team &tm, StageSmem<NS, WX, WY, HU> &sm, Local &L,
-                          Coef &cf, double *s_sum, float &s_emax, int &s_stop)
+template <class SM>
+__device__ bool integrate(const Ctx &c, const Team &tm, SM &sm, Local &L, Coef &cf,
+                          double *s_sum, float &s_emax, int &s_stop)
 {
     if (threadIdx.x == 0) load_local(c, L);
     if (threadIdx.x < c.nmodes) {
@@ -533,7 +530,7 @@ __device__ bool integrate(const Ctx &c, const Team &tm, StageSmem<NS, WX, WY, HU
     {
         const int sb = __ldg(&c.seg_begin[tm.rank]), se = __ldg(&c.seg_begin[tm.rank + 1]);
         if (threadIdx.x == 0) sm.nseg = se - sb;
-        for (int t = threadIdx.x; t < se - sb; t += WX * WY) sm.seg[t] = __ldg(&c.tiles[sb + t]);
+        for (int t = threadIdx.x; t < se - sb; t += blockDim.x) sm.seg[t] = __ldg(&c.tiles[sb + t]);
     }
     __syncthreads();
     bool ok = true;
@@ -547,16 +544,16 @@ __device__ bool integrate(const Ctx &c, const Team &tm, StageSmem<NS, WX, WY, HU
         __syncthreads();
         if (s_stop) break;
         if (!L.k1_valid) {
-            if (!(ok = run_stage<NS, WX, WY, HU, 1>(c, tm, sm, L, cf, s_sum, &s_emax, pp, false)))
+            if (!(ok = run_stage<1>(c, tm, sm, L, cf, s_sum, &s_emax, pp, false)))
                 break;
             if (c.stage_only) break;
         }
-        if (!(ok = run_stage<NS, WX, WY, HU, 2>(c, tm, sm, L, cf, s_sum, &s_emax, pp, false))) break;
-        if (!(ok = run_stage<NS, WX, WY, HU, 3>(c, tm, sm, L, cf, s_sum, &s_emax, pp, true))) break;
-        if (!(ok = run_stage<NS, WX, WY, HU, 4>(c, tm, sm, L, cf, s_sum, &s_emax, pp, true))) break;
-        if (!(ok = run_stage<NS, WX, WY, HU, 5>(c, tm, sm, L, cf, s_sum, &s_emax, pp, true))) break;
-        if (!(ok = run_stage<NS, WX, WY, HU, 6>(c, tm, sm, L, cf, s_sum, &s_emax, pp, true))) break;
-        if (!(ok = run_stage<NS, WX, WY, HU, 7>(c, tm, sm, L, cf, s_sum, &s_emax, pp, true))) break;
+        if (!(ok = run_stage<2>(c, tm, sm, L, cf, s_sum, &s_emax, pp, false))) break;
+        if (!(ok = run_stage<3>(c, tm, sm, L, cf, s_sum, &s_emax, pp, true))) break;
+        if (!(ok = run_stage<4>(c, tm, sm, L, cf, s_sum, &s_emax, pp, true))) break;
+        if (!(ok = run_stage<5>(c, tm, sm, L, cf, s_sum, &s_emax, pp, true))) break;
+        if (!(ok = run_stage<6>(c, tm, sm, L, cf, s_sum, &s_emax, pp, true))) break;
+        if (!(ok = run_stage<7>(c, tm, sm, L, cf, s_sum, &s_emax, pp, true))) break;
     }
     if (ok && tm.rank == 0 && threadIdx.x == 0) store_local(c, L);
     __syncthreads();

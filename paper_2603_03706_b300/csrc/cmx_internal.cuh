@@ -100,6 +100,7 @@ struct Ctx {
     int tr_cap;
     long long timeout_ns;
     int stage_only;                  // 1: evaluate stage 1 once (cmx_eval_rhs) and stop
+    int quad;                        // 1: quad windows (four x-cells per thread, align-4 rows)
     // Checkpoint store of the adjoint (NULL = off): slot k holds the state after
     // k * traj_every accepted steps counted from traj_base (slot 0: the initial state):
     // m (renormalised) and the FSAL slope k1, and a, k1^a and <m^-> at the slope's point.

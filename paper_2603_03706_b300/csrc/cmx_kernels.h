@@ -7,6 +7,9 @@ namespace cmx {
 
 // persistent single-problem integrator (cmx_single.cu)
 bool tile_shape_supported(int nsub, int bx, int by);
+// quad windows (Ctx::quad): wq x wy threads of four x-cells, launched with bx = 4 wq, by = wy
+bool quad_shape_supported(int wq, int wy);
+int quad_blocks_per_sm(int wq, int wy, int nu);
 cudaError_t launch_single(const Ctx &c, int bx, int by, int blocks, cudaStream_t s);
 int single_blocks_per_sm(int nsub, int bx, int by, bool has_u);
 

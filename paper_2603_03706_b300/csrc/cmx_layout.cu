@@ -6,8 +6,9 @@
 
 namespace cmx {
 
-void build_layout(Layout &L, int nx, int ny, int nz, const uint8_t *mask)
+void build_layout(Layout &L, int nx, int ny, int nz, const uint8_t *mask, int align)
 {
+    if (align < 1) align = 1;
     L.nx = nx;
     L.ny = ny;
     L.nz = nz;
@@ -28,11 +29,16 @@ void build_layout(Layout &L, int nx, int ny, int nz, const uint8_t *mask)
                 L.rows[(size_t)z * ny + y] = make_int2(off, 0);
                 continue;
             }
+            // the stored span starts and ends on multiples of `align` (cells beyond the box are
+            // inactive padding), so that aligned groups of `align` cells are aligned in memory
+            xs -= xs % align;
+            xe = (xe + align - 1) / align * align;
             L.rows[(size_t)z * ny + y] = make_int2(off, xs | (xe << 16));
             for (int x = xs; x < xe; x++) {
-                L.box_of_cell.push_back((int)(rb + x));
-                L.active.push_back(mask[rb + x] ? 1 : 0);
-                nmag += mask[rb + x] ? 1 : 0;
+                const bool on = x < nx && mask[rb + x];
+                L.box_of_cell.push_back((int)(rb + std::min(x, nx - 1)));
+                L.active.push_back(on ? 1 : 0);
+                nmag += on ? 1 : 0;
             }
             off += xe - xs;
         }

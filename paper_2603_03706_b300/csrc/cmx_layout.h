@@ -9,8 +9,10 @@
 
 namespace cmx {
 
-// Cells are stored per (y, z) row between the first and the last magnetic x of the row; cells
-// in between that are not magnetic are holes (inactive).  rows[z*ny + y] = (offset, xs | xe<<16).
+// Cells are stored per (y, z) row between the first and the last magnetic x of the row, the
+// span widened to multiples of `align` cells; cells in it that are not magnetic are holes
+// (inactive).  rows[z*ny + y] = (offset, xs | xe<<16).  With align = 4 every row starts at a
+// multiple of 4 stored cells and ncell is a multiple of 4 (16-byte aligned groups of four).
 struct Layout {
     int nx = 0, ny = 0, nz = 0;
     int ncell = 0, ncell_mag = 0;
@@ -20,7 +22,7 @@ struct Layout {
     std::vector<uint8_t> active;    // 1 = magnetic (stored cells)
 };
 
-void build_layout(Layout &L, int nx, int ny, int nz, const uint8_t *mask);
+void build_layout(Layout &L, int nx, int ny, int nz, const uint8_t *mask, int align = 1);
 
 // 32-bit words of the active-cell bitmask (bit i of word i/32 = stored cell i is magnetic).
 std::vector<uint32_t> active_bits(const Layout &L);

@@ -51,6 +51,7 @@ struct cmx_problem {
     Ctl *ev_ctl = nullptr;
     // launch shape
     int bx = 32, by = 8, bz = 16, blocks = 0, bps = 0, nsm = 0;
+    int quad = 0;                     // quad windows (four x-cells per thread)
     long long launch_attempts = 4096;
     long long timeout_ns = 2000000000LL;
     int skip_block = -1;

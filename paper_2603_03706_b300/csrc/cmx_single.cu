@@ -1,6 +1,7 @@
 // Persistent single-problem integrator: one team of all blocks of a cooperative launch.
 #include "cmx_engine.cuh"
 #include "cmx_kernels.h"
+#include "cmx_quad.cuh"
 
 namespace cmx {
 
@@ -22,7 +23,22 @@ __global__ void __launch_bounds__(WX *WY, (MinBlocks<NS, WX * WY>::value)) run_k
     __shared__ float s_emax;
     __shared__ int s_stop;
     const Team tm{(int)blockIdx.x, (int)gridDim.x, &c.ctl->bar_count};
-    integrate<NS, WX, WY, HU>(c, tm, sm, L, cf, s_sum, s_emax, s_stop);
+    integrate(c, tm, sm, L, cf, s_sum, s_emax, s_stop);
+}
+
+// Quad windows (one sublattice): wq x wy threads, four x-cells each; one block per SM.
+template <bool HU>
+__global__ void __launch_bounds__(QMAX_NT, 1) run_kernel_quad(Ctx c, int wq, int wy)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    QuadSmem<HU> sm = quad_smem<HU>(smem_raw, wq, wy, c.nmodes);
+    __shared__ Local L;
+    __shared__ Coef cf;
+    __shared__ double s_sum[2 * MAXN];
+    __shared__ float s_emax;
+    __shared__ int s_stop;
+    const Team tm{(int)blockIdx.x, (int)gridDim.x, &c.ctl->bar_count};
+    integrate(c, tm, sm, L, cf, s_sum, s_emax, s_stop);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -61,6 +77,46 @@ static int occupancy_variant()
 #define CMX_VARIANTS(X) \
     X(1, 32, 8) X(1, 32, 16) X(1, 64, 4) X(2, 32, 8) X(2, 32, 16) X(2, 64, 4)
 
+template <bool HU>
+static cudaError_t launch_quad(const Ctx &c, int wq, int wy, int blocks, cudaStream_t s)
+{
+    auto *fn = run_kernel_quad<HU>;
+    const size_t smem = quad_smem_bytes(wq * wy, HU ? c.nmodes : 0);
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    Ctx cc = c;
+    void *args[] = {&cc, &wq, &wy};
+    return cudaLaunchCooperativeKernel((const void *)fn, dim3(blocks), dim3(wq * wy), args, smem,
+                                       s);
+}
+
+bool quad_shape_supported(int wq, int wy)
+{
+    return wq >= 3 && wy >= 3 && wy <= QMAX_WY && wq * wy <= QMAX_NT && (wq * wy) % 32 == 0;
+}
+
+int quad_blocks_per_sm(int wq, int wy, int nu)
+{
+    const int nt = wq * wy;
+    const size_t smem = quad_smem_bytes(nt, nu);
+    int nb = 0;
+    if (nu > 0) {
+        auto *fn = run_kernel_quad<true>;
+        if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+                cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, nt, smem) != cudaSuccess)
+            return 0;
+    } else {
+        auto *fn = run_kernel_quad<false>;
+        if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+                cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, nt, smem) != cudaSuccess)
+            return 0;
+    }
+    return nb;
+}
+
 bool tile_shape_supported(int nsub, int bx, int by)
 {
 #define X(n, a, b) if (nsub == n && bx == a && by == b) return true;
@@ -71,6 +127,11 @@ bool tile_shape_supported(int nsub, int bx, int by)
 
 cudaError_t launch_single(const Ctx &c, int bx, int by, int blocks, cudaStream_t s)
 {
+    if (c.quad) {
+        if (c.nsub != 1 || bx % 4 || !quad_shape_supported(bx / 4, by)) return cudaErrorInvalidValue;
+        return c.u ? launch_quad<true>(c, bx / 4, by, blocks, s)
+                   : launch_quad<false>(c, bx / 4, by, blocks, s);
+    }
 #define X(n, a, b)                                                                       \
     if (c.nsub == n && bx == a && by == b)                                               \
         return c.u ? launch_variant<n, a, b, true>(c, blocks, s)                         \

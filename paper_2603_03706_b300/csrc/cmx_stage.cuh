@@ -104,6 +104,13 @@ __device__ __forceinline__ void cp_async4(void *smem, const void *gmem)
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(s), "l"(gmem) : "memory");
 }
 
+// Asynchronous 16-byte global -> shared copy (both addresses 16-byte aligned).
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
+}
+
 __device__ __forceinline__ void cp_async_commit()
 {
     asm volatile("cp.async.commit_group;" ::: "memory");
@@ -380,6 +387,7 @@ __device__ __forceinline__ void compute_cell(const Ctx &c, StageSmem<NS, WX, WY,
 struct Pipe {
     Cursor cr, ci, cc;
     int nq, gend;
+    int fidx, fnib, finner;   // quad windows: the first plane, issued by stage_begin
 };
 
 // Start stage S's stream: row entries of the first planes and the first D planes of copies.
@@ -480,6 +488,23 @@ __device__ void tiles_run(const Ctx &c, StageSmem<NS, WX, WY, HU> &sm, float *ko
         compute_cell<NS, WX, WY, HU, S>(c, sm, kout, mnew, cf, p, ucur, tslot, rslot, acc);
     }
     cp_async_wait<0>();
+}
+
+// Engine-facing names of the stage code of this window type (overloaded by smem type).
+template <int S, int NS, int WX, int WY, bool HU>
+__device__ __forceinline__ void stage_begin(const Ctx &c, StageSmem<NS, WX, WY, HU> &sm,
+                                            const float *mn, Pipe &pp)
+{
+    tiles_begin<NS, WX, WY, HU, S>(c, sm, mn, pp);
+}
+
+template <int S, int NS, int WX, int WY, bool HU>
+__device__ __forceinline__ void stage_run(const Ctx &c, StageSmem<NS, WX, WY, HU> &sm,
+                                          float *kout, const float *mn, float *mnew,
+                                          const Coef &cf, Pipe &pp, int tslot, int rslot,
+                                          Acc &acc)
+{
+    tiles_run<NS, WX, WY, HU, S>(c, sm, kout, mn, mnew, cf, pp, tslot, rslot, acc);
 }
 
 }  // namespace cmx

@@ -57,8 +57,8 @@ def ferro_plain(T=0.2e-9):
     return f32_state(p.replace(dt_max=W.stable_dt_max(p)))
 
 
-def forward(p, every, max_steps=100000):
-    sim = cmx.Simulation.from_problem(p, log_cap=max_steps + 64)
+def forward(p, every, max_steps=100000, tiling=None):
+    sim = cmx.Simulation.from_problem(p, log_cap=max_steps + 64, tiling=tiling)
     sim.adjoint_record(every, max_steps)
     st = sim.run(p.T)
     log = sim.get_log()
@@ -104,10 +104,12 @@ def compare(p, g, go):
     return errs
 
 
-@pytest.mark.parametrize("case,every", [("sphere16", 40), ("afm", 16), ("plain", 25)])
-def test_adjoint_matches_oracle(case, every):
+@pytest.mark.parametrize("case,every,tiling", [("sphere16", 40, None), ("afm", 16, None),
+                                               ("plain", 25, None),
+                                               ("sphere16", 40, (64, 16, 0, 0, 4))])
+def test_adjoint_matches_oracle(case, every, tiling):
     p = {"sphere16": sphere16, "afm": afm_small, "plain": ferro_plain}[case]()
-    sim, dts, traj = forward(p, every)
+    sim, dts, traj = forward(p, every, tiling=tiling)
     assert len(dts) > 2 * every, len(dts)   # several intervals and a partial last one
     la, wm = loss_weights(p, traj)
     g = sim.adjoint(la, wm)

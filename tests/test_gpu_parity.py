@@ -67,7 +67,12 @@ def rhs_compare(p, tiling=None):
 # one stage
 # ---------------------------------------------------------------------------------------------
 
-@pytest.mark.parametrize("tiling", [None, (32, 8, 3), (64, 4, 5), (32, 16, 11), (32, 8, 1)])
+# one cell per thread (bx, by, bz) and quad windows (bx, by, bz, blocks_per_sm, 4)
+TILINGS = [None, (32, 8, 3), (64, 4, 5), (32, 16, 11), (32, 8, 1), (128, 8, 3, 0, 4),
+           (96, 8, 5, 0, 4), (64, 16, 2, 0, 4), (32, 16, 1, 0, 4), (64, 8, 7, 0, 4)]
+
+
+@pytest.mark.parametrize("tiling", TILINGS)
 def test_rhs_ferromagnet_ragged(tiling):
     r = rhs_compare(ragged_problem(), tiling)
     assert r["err_m"] < 2e-6, r
@@ -75,8 +80,9 @@ def test_rhs_ferromagnet_ragged(tiling):
     assert r["err_mm"] < 1e-7 and r["err_da"] < 1e-6, r
 
 
-def test_rhs_mask_with_holes_and_many_runs_per_row():
-    r = rhs_compare(ragged_problem(holes=True, nmodes=8, seed=3), (64, 4, 4))
+@pytest.mark.parametrize("tiling", [(64, 4, 4), (64, 8, 4, 0, 4)])
+def test_rhs_mask_with_holes_and_many_runs_per_row(tiling):
+    r = rhs_compare(ragged_problem(holes=True, nmodes=8, seed=3), tiling)
     assert r["err_m"] < 2e-6 and r["outside"] == 0.0, r
     assert r["err_mm"] < 1e-7 and r["err_da"] < 1e-6, r
 
@@ -104,10 +110,11 @@ def test_replay_single_sphere_1000_steps():
     assert dm <= TOL_M and da <= TOL_A, (dm, da)
 
 
-def test_replay_ragged_multimode_1000_steps():
+@pytest.mark.parametrize("tiling", [(64, 4, 4), (64, 16, 4, 0, 4)])
+def test_replay_ragged_multimode_1000_steps(tiling):
     p = ragged_problem(nmodes=3, seed=11)
     p = p.replace(m0=W.tilted_state(1, p.nx, p.ny, p.nz, 5.0, 0.3), a0=np.array([1e-3, 0, 0j]))
-    dm, da, info = replay_compare(p.replace(T=1e-6), 1000, tiling=(64, 4, 4))
+    dm, da, info = replay_compare(p.replace(T=1e-6), 1000, tiling=tiling)
     assert dm <= TOL_M and da <= TOL_A, (dm, da)
 
 
