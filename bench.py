@@ -360,6 +360,10 @@ def main():
     stream = torch.cuda.Stream()
     tiling = tuple(int(v) for v in args.tiling.split(",")) if args.tiling else None
     sim = cmx.Simulation.from_problem(p, stream=stream, tiling=tiling)
+    tuned = None
+    if tiling is None:
+        tuned = sim.autotune(20)        # measured window choice, state restored afterwards
+        torch.cuda.synchronize()
     ncell = sim.ncells()[0]
     bpa = bytes_per_cell_attempt(p) * ncell
     # attempts per launch: about 20 ms of work per step at the HBM roofline
@@ -441,7 +445,8 @@ def main():
                        "nsub": p.nsub, "modes": p.nmodes, "attempts_per_step": A,
                        "rhs_evals_per_step": updates / ncell / args.steps,
                        "dt_max": p.dt_max, "l2": "flushed between timed steps (256 MiB write)",
-                       "tiling": tl, "parallelism": "replicas" if world > 1 else "single"},
+                       "tiling": tl, "autotune_us_per_attempt": tuned and tuned["us_per_attempt"],
+                       "parallelism": "replicas" if world > 1 else "single"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak_gbs, "unit": "GB/s",
                          "frac": achieved / peak_gbs,
                          "traffic": recorded_traffic(p.name),

@@ -193,6 +193,14 @@ int cmx_set_timeout(cmx_problem *h, long long ns);
  * the other blocks reach their wait limit; -1 disables.  Used only to test CMX_ETIMEOUT. */
 int cmx_debug_skip_arrival(cmx_problem *h, int block);
 
+/* Autotuner: time `attempts` Dormand-Prince attempts (after a one-attempt warm-up) from the
+ * current state with each compiled one-cell window (32x8, 32x16, 64x4; blocks_per_sm and bz of
+ * the current tiling), restore the state after each trial (m, FSAL slope, control block; the
+ * step log and trace counters roll back too) and keep the fastest window.  *chosen (may be
+ * NULL) receives it; us_per_attempt (may be NULL, 3 entries) the measured times in that order.
+ * Quad windows are left as they are (nothing is tuned). */
+int cmx_autotune(cmx_problem *h, int attempts, cmx_tiling *chosen, double *us_per_attempt);
+
 /* Launch shape actually used: bx, by, bz, grid blocks, tiles. */
 int cmx_get_tiling(const cmx_problem *h, int *bx, int *by, int *bz, int *blocks, int *tiles,
                    int *quad);

@@ -128,6 +128,7 @@ SIGNATURES = {
     "cmx_batch_info": (C.c_int, [_P, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int),
                                  C.POINTER(C.c_longlong), C.POINTER(C.c_int)]),
     "cmx_batch_last_error": (C.c_char_p, [_P]),
+    "cmx_autotune": (C.c_int, [_P, C.c_int, C.c_void_p, C.c_void_p]),
     "cmx_adjoint_record": (C.c_int, [_P, C.c_int, C.c_longlong]),
     "cmx_adjoint": (C.c_int, [_P, C.c_void_p, C.c_void_p, C.c_int, C.POINTER(Grads)]),
     "cmx_adjoint_steps": (C.c_int, [_P, C.POINTER(C.c_longlong)]),
@@ -462,6 +463,15 @@ class Simulation:
 
     def debug_skip_arrival(self, block: int):
         self._check(load().cmx_debug_skip_arrival(self.h, int(block)), "debug_skip_arrival")
+
+    def autotune(self, attempts: int = 20) -> dict:
+        """cmx_autotune: time the compiled windows from the current state, keep the fastest."""
+        t = Tiling()
+        us = np.zeros(3)
+        self._check(load().cmx_autotune(self.h, int(attempts), C.byref(t), us.ctypes.data),
+                    "autotune")
+        return dict(bx=t.bx, by=t.by, bz=t.bz, us_per_attempt=dict(
+            zip(("32x8", "32x16", "64x4"), [float(v) for v in us])))
 
     def get_tiling(self) -> dict:
         v = [C.c_int() for _ in range(6)]

@@ -108,6 +108,7 @@ int install_tiling(cmx_problem *h, const std::vector<Column> &cols, int blocks, 
 int setup_tiling(cmx_problem *h, const cmx_tiling *t)
 {
     int bx = 32, by = 8, bz = 0, bps = 0;
+    h->bps_cap = t ? t->blocks_per_sm : 0;
     if (h->quad) {
         int wq = 0, wy = 0;
         if (t) {
@@ -745,6 +746,82 @@ int cmx_debug_skip_arrival(cmx_problem *h, int block)
 {
     if (!h || block >= h->blocks) return fail(h, CMX_EINVAL, "bad argument");
     h->skip_block = block;
+    return CMX_OK;
+}
+
+int cmx_autotune(cmx_problem *h, int attempts, cmx_tiling *chosen, double *us_per_attempt)
+{
+    if (!h || attempts <= 0) return fail(h, CMX_EINVAL, "bad argument");
+    if (h->quad) {
+        if (chosen) *chosen = cmx_tiling{h->bx, h->by, h->bz, 0, 4};
+        return CMX_OK;
+    }
+    Ctl saved;
+    int rc = read_ctl(h, &saved);
+    if (rc) return rc;
+    if (saved.status) return device_status(h, saved);
+    const int nq = 3 * h->grid.nsub;
+    const size_t bytes = (size_t)nq * h->ncell * sizeof(float);
+    float *m_save = nullptr, *k_save = nullptr;
+    CU(dalloc(&m_save, (size_t)nq * h->ncell));
+    if (dalloc(&k_save, (size_t)nq * h->ncell) != cudaSuccess) {
+        cudaFree(m_save);
+        return fail(h, CMX_ENOMEM, "autotune scratch");
+    }
+    cudaStream_t st = h->stream;
+    cudaMemcpyAsync(m_save, h->mbuf[saved.mcur], bytes, cudaMemcpyDeviceToDevice, st);
+    cudaMemcpyAsync(k_save, h->kbuf[saved.kphys[0]], bytes, cudaMemcpyDeviceToDevice, st);
+    auto restore = [&]() {
+        cudaMemcpyAsync(h->mbuf[saved.mcur], m_save, bytes, cudaMemcpyDeviceToDevice, st);
+        cudaMemcpyAsync(h->kbuf[saved.kphys[0]], k_save, bytes, cudaMemcpyDeviceToDevice, st);
+        cudaMemcpyAsync(h->ctl, &saved, sizeof saved, cudaMemcpyHostToDevice, st);
+        return cudaStreamSynchronize(st);
+    };
+    static const int cand[3][2] = {{32, 8}, {32, 16}, {64, 4}};
+    const int bz = h->bz, bps = h->bps_cap;
+    double best = 1e300;
+    int bi = 0;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    for (int ci = 0; ci < 3; ci++) {
+        double us = NAN;
+        cmx_tiling t{cand[ci][0], cand[ci][1], bz, bps, 1};
+        if (tile_shape_supported(h->grid.nsub, t.bx, t.by) && setup_tiling(h, &t) == CMX_OK) {
+            PrepArgs pa{};
+            pa.T = INFINITY;
+            pa.set_replay = -1;
+            pa.skip_block = -1;
+            pa.max_launch_attempts = 1;
+            int r1 = launch(h, pa, make_ctx(h));   // warm-up
+            pa.max_launch_attempts = attempts;
+            cudaEventRecord(e0, st);
+            int r2 = r1 ? r1 : launch(h, pa, make_ctx(h));
+            cudaEventRecord(e1, st);
+            Ctl after;
+            if (!r2 && read_ctl(h, &after) == CMX_OK && !after.status &&
+                after.attempts > saved.attempts + 1) {
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                us = 1e3 * ms / (double)(after.attempts - saved.attempts - 1);
+            }
+        }
+        if (us_per_attempt) us_per_attempt[ci] = us;
+        if (us == us && us < best) {
+            best = us;
+            bi = ci;
+        }
+        if (restore() != cudaSuccess) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(m_save);
+    cudaFree(k_save);
+    if (!(best < 1e300)) return fail(h, CMX_ECUDA, "autotune: no window could be timed");
+    cmx_tiling t{cand[bi][0], cand[bi][1], bz, bps, 1};
+    rc = setup_tiling(h, &t);
+    if (rc) return rc;
+    if (chosen) *chosen = t;
     return CMX_OK;
 }
 

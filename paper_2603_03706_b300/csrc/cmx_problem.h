@@ -52,6 +52,7 @@ struct cmx_problem {
     // launch shape
     int bx = 32, by = 8, bz = 16, blocks = 0, bps = 0, nsm = 0;
     int quad = 0;                     // quad windows (four x-cells per thread)
+    int bps_cap = 0;                  // blocks_per_sm requested (0 = as many as fit)
     long long launch_attempts = 4096;
     long long timeout_ns = 2000000000LL;
     int skip_block = -1;

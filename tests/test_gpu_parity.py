@@ -210,3 +210,20 @@ def test_nan_state_reports_enan():
         sim.run(p.T, max_attempts=5)
     assert ei.value.code == cmx.ENAN
     sim.close()
+
+
+def test_autotune_restores_the_state_and_keeps_a_compiled_window():
+    p = f32_state(f32_profiles(ragged_problem(nmodes=2, seed=21)))
+    sim = sim_for(p, log_cap=64)
+    sim.run(p.T, max_attempts=5)
+    m0, a0, st0 = sim.get_m(), sim.get_a(), sim.sync()
+    t = sim.autotune(3)
+    assert (t["bx"], t["by"]) in ((32, 8), (32, 16), (64, 4))
+    assert all(v > 0 for v in t["us_per_attempt"].values()), t
+    st1 = sim.sync()
+    assert np.array_equal(sim.get_m(), m0) and np.array_equal(sim.get_a(), a0)
+    assert (st1["t"], st1["attempts"], st1["accepted"]) == (st0["t"], st0["attempts"],
+                                                            st0["accepted"])
+    sim.run(p.T, max_attempts=5)
+    assert sim.sync()["attempts"] == st0["attempts"] + 5
+    sim.close()
