@@ -87,6 +87,11 @@ __global__ void adj_restore_kernel(Ctl *ctl, const double *slot, int N, const do
     ctl->trace_next = 0.0;
     ctl->bar_count = 0;
     ctl->skip_block = -1;
+    for (int k = 0; k < 3; k++) {
+        for (int q = 0; q < 2 * MAXN; q++) ctl->racc[k][q] = 0;
+        ctl->remax[k] = 0u;
+    }
+    ctl->range_error = 0;
 }
 
 // FP64 running sum of the interval accumulators of dL/du, which are cleared.

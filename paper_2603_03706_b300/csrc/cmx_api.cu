@@ -430,18 +430,22 @@ int cmx_create(const cmx_grid *grid, const uint8_t *mask, const cmx_material *ma
     }
     for (int j = 0; j < 7; j++) cudaMemset(h->kbuf[j], 0, nq * nc * sizeof(float));
     cudaMemset(h->mbuf[1], 0, nq * nc * sizeof(float));
-    // mode profiles, compacted
+    // mode profiles, compacted (umax bounds the overlap sums; device profiles: |u| <= 256)
+    double umax = 1.0;
     if (N > 0 && modes->u) {
         if (dalloc(&h->u, (size_t)N * nc)) return bail(CMX_ENOMEM);
         if (modes->u_on_device) {
+            umax = 256.0;
             gather_kernel<<<grid_blocks((long long)N * nc), 256>>>(
                 modes->u, h->u, h->box_of_cell, h->active, h->ncell, nbox, N);
         } else {
             std::vector<float> uc((size_t)N * nc);
             for (int n = 0; n < N; n++)
-                for (size_t i = 0; i < nc; i++)
+                for (size_t i = 0; i < nc; i++) {
                     uc[n * nc + i] =
                         h->lay.active[i] ? modes->u[n * nbox + h->lay.box_of_cell[i]] : 0.f;
+                    umax = std::max(umax, (double)std::fabs(uc[n * nc + i]));
+                }
             cudaMemcpy(h->u, uc.data(), uc.size() * sizeof(float), cudaMemcpyHostToDevice);
         }
     }
@@ -492,6 +496,7 @@ int cmx_create(const cmx_grid *grid, const uint8_t *mask, const cmx_material *ma
     }
     c.two_over_gamma = 2.0 / mat->gamma;
     c.inv_nmag = 1.0 / (double)h->ncell_mag;
+    c.red_scale = overlap_scale(umax * (double)h->ncell_mag);
     c.rtol = solver->rtol;
     c.a_ref = solver->a_ref;
     c.dt_min = solver->dt_min;

@@ -305,9 +305,11 @@ __device__ void controller(const Ctx &c, const Team &tm, Local &L, const double 
 }
 
 // Block sum of the per-thread overlap accumulators (compensated pairs, fixed shuffle order)
-// and block max of |e_m|, written to the block's slot of c.part / c.errpart.
+// and block max of |e_m|, added into accumulator set `set` of the control block: the sums as
+// fixed-point integers (exact, so their total does not depend on the order of the blocks), the
+// maximum through an integer max on the bit pattern of the non-negative float.
 template <class SM>
-__device__ void block_reduce(const Ctx &c, const Team &tm, SM &sm, const Acc &acc)
+__device__ void block_reduce(const Ctx &c, const Team &tm, SM &sm, const Acc &acc, int set)
 {
     const int NT = blockDim.x, NW = NT / 32;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -334,12 +336,18 @@ __device__ void block_reduce(const Ctx &c, const Team &tm, SM &sm, const Acc &ac
     if (threadIdx.x < Q) {
         F2 s = {0.f, 0.f};
         for (int w = 0; w < NW; w++) s = f2_add(s, sm.red[w][threadIdx.x]);
-        c.part[(size_t)tm.rank * Q + threadIdx.x] = make_float2(s.hi, s.lo);
+        const double v = ((double)s.hi + (double)s.lo) * c.red_scale;
+        if (fabs(v) < 4.0e18) {
+            atomicAdd(reinterpret_cast<unsigned long long *>(&c.ctl->racc[set][threadIdx.x]),
+                      (unsigned long long)__double2ll_rn(v));
+        } else {
+            atomicExch(&c.ctl->range_error, 1);
+        }
     }
     if (threadIdx.x == NT - 1) {
         float m = 0.f;
         for (int w = 0; w < NW; w++) m = nanmax(m, sm.redmax[w]);
-        c.errpart[tm.rank] = m;
+        atomicMax(&c.ctl->remax[set], __float_as_uint(m));
     }
 }
 
@@ -348,55 +356,23 @@ __device__ __forceinline__ void red_add_release(unsigned *p, unsigned v)
     asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-// Fixed-order sum over all blocks of the overlap partials (compensated pairs) and max of the
-// error partials, done identically by every block after the barrier, so every block holds the
-// same values.  Thread t sums component q = t mod QP of blocks b = t/QP, t/QP + NT/QP, ...
-// (QP = 2N rounded up to a power of two); lanes of equal q are then combined by shuffles and
-// the warps in order.
+// After the barrier: the grid sums of set `set`, identical for every block.  The team's rank 0
+// then clears the set that stage count + 2 will use (every block has finished reading it: it
+// was read before the arrival at this barrier).
 template <class SM>
-__device__ void grid_reduce(const Ctx &c, const Team &tm, SM &sm, double *out, float *emax)
+__device__ void grid_reduce(const Ctx &c, const Team &tm, SM &sm, double *out, float *emax, int set)
 {
-    const int NT = blockDim.x, NW = NT / 32;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int Q = 2 * c.nmodes, G = tm.nblk;
-    int QP = 1;
-    while (QP < Q) QP <<= 1;
-    const int q = threadIdx.x & (QP - 1), grp = threadIdx.x / QP, ngrp = NT / QP;
-    F2 s = {0.f, 0.f};
-    if (q < Q) {
-        int b = grp;
-        for (; b + 3 * ngrp < G; b += 4 * ngrp) {
-            const float2 v0 = __ldcg(c.part + (size_t)b * Q + q);
-            const float2 v1 = __ldcg(c.part + (size_t)(b + ngrp) * Q + q);
-            const float2 v2 = __ldcg(c.part + (size_t)(b + 2 * ngrp) * Q + q);
-            const float2 v3 = __ldcg(c.part + (size_t)(b + 3 * ngrp) * Q + q);
-            s = f2_add(s, {v0.x, v0.y});
-            s = f2_add(s, {v1.x, v1.y});
-            s = f2_add(s, {v2.x, v2.y});
-            s = f2_add(s, {v3.x, v3.y});
-        }
-        for (; b < G; b += ngrp) {
-            const float2 v = __ldcg(c.part + (size_t)b * Q + q);
-            s = f2_add(s, {v.x, v.y});
-        }
+    const int Q = 2 * c.nmodes;
+    volatile Ctl *g = c.ctl;
+    if ((int)threadIdx.x < Q) out[threadIdx.x] = (double)g->racc[set][threadIdx.x] / c.red_scale;
+    if ((int)threadIdx.x == Q) {
+        const unsigned bits = g->remax[set];
+        *emax = g->range_error ? __int_as_float(0x7fffffff) : __uint_as_float(bits);
     }
-    for (int o = 16; o >= QP; o >>= 1) s = f2_add(s, f2_shfl_xor(s, o));
-    if (lane < QP && lane < Q) sm.red[warp][lane] = s;
-    float e = 0.f;
-    for (int b = threadIdx.x; b < G; b += NT) e = nanmax(e, __ldcg(c.errpart + b));
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) e = nanmax(e, __shfl_xor_sync(0xffffffffu, e, o));
-    if (lane == 0) sm.redmax[warp] = e;
-    __syncthreads();
-    if (threadIdx.x < Q) {
-        F2 v = {0.f, 0.f};
-        for (int w = 0; w < NW; w++) v = f2_add(v, sm.red[w][threadIdx.x]);
-        out[threadIdx.x] = (double)v.hi + (double)v.lo;
-    }
-    if (threadIdx.x == NT - 1) {
-        float m = 0.f;
-        for (int w = 0; w < NW; w++) m = nanmax(m, sm.redmax[w]);
-        *emax = m;
+    if (tm.rank == 0) {
+        const int clr = (set + 2) % 3;
+        if ((int)threadIdx.x < Q) g->racc[clr][threadIdx.x] = 0;
+        if ((int)threadIdx.x == Q) g->remax[clr] = 0u;
     }
     __syncthreads();
 }
@@ -493,10 +469,11 @@ __device__ bool run_stage(const Ctx &c, const Team &tm, SM &sm, Local &L, Coef &
     const int rslot = (S >= 2 && c.rec_m && L.replay && L.replay_pos < c.rec_steps)
                           ? (int)L.replay_pos : -1;
     stage_run<S>(c, sm, (float *)sm.kp[S - 1], mn, mnew, cf, pp, tslot, rslot, acc);
-    block_reduce(c, tm, sm, acc);
+    const int set = (int)(L.rhs_evals % 3);
+    block_reduce(c, tm, sm, acc, set);
     if (!grid_barrier<SM>(c, tm, L, S)) return false;
     if (S >= 2 && S < 7 && !c.stage_only) stage_begin<(S < 7 ? S + 1 : 7)>(c, sm, mn, pp);
-    grid_reduce(c, tm, sm, s_sum, s_emax);
+    grid_reduce(c, tm, sm, s_sum, s_emax, set);
     controller<S>(c, tm, L, s_sum, *s_emax);
     __syncthreads();
     return true;

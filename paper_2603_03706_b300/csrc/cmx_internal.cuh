@@ -1,6 +1,7 @@
 // Internal definitions shared by the sm_103a kernels and the host code of libcmx.
 #pragma once
 
+#include <cmath>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -40,6 +41,15 @@ __host__ __device__ constexpr double dp_e(int j)
     return E[j];
 }
 
+// Fixed-point scale of the overlap sums: the largest power of two (at most 2^40) that keeps a
+// sum of magnitude up to `bound` (max |u| times the magnetic cells) below 2^61.
+inline double overlap_scale(double bound)
+{
+    int e = 61 - (int)std::ceil(std::log2(bound > 1.0 ? bound : 1.0));
+    if (e > 40) e = 40;
+    return std::ldexp(1.0, e);
+}
+
 // Integrator control block in device memory.  Written only by the block that completes a
 // grid barrier (the "controller"), read by every block after the barrier is released.
 struct Ctl {
@@ -61,8 +71,14 @@ struct Ctl {
     long long log_n, trace_n;
     double trace_next;
     unsigned int bar_count, bar_gen; // grid barrier
-    double bc[2 * MAXN];             // barrier broadcast: grid sums of the overlaps
-    float bc_emax;                   // barrier broadcast: grid max of |e_m|
+    // Grid sums of the stage's overlaps as fixed-point integers (value x red_scale), and the bit
+    // pattern of the grid max of |e_m|, in three sets used in turn by stage count mod 3: the
+    // blocks add into the current set before the barrier; the set for two stages ahead is
+    // cleared by the team's rank 0 after it.  Integer addition makes the sum independent of the
+    // order of arrival.
+    long long racc[3][2 * MAXN];
+    unsigned int remax[3];
+    int range_error;                 // a block partial left the fixed-point range
     int skip_block;                  // test hook (see cmx_debug_skip_arrival)
     int timeout_where;
 };
@@ -87,6 +103,7 @@ struct Ctx {
     // modes
     double omega[MAXN], kappa[MAXN], gre[MAXN], gim[MAXN];
     double two_over_gamma, inv_nmag;
+    double red_scale;                // fixed-point scale of the overlap sums (a power of two)
     // solver
     double rtol, a_ref, dt_min, dt_max, sample_dt;
     Ctl *ctl;

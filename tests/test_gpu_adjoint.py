@@ -235,7 +235,9 @@ def test_autograd_function_matches_the_direct_call():
     sim.close()
     assert abs(float(L) - eT / e0) <= 1e-12 * eT / e0
     for k in ("g_re", "g_im", "kappa", "omega"):
-        assert np.allclose(prm[k].grad.numpy(), g[k], rtol=1e-12, atol=0), k
+        # entries far below the largest one come from cancellations: compare on its scale
+        ref = np.abs(g[k]).max()
+        assert np.allclose(prm[k].grad.numpy(), g[k], rtol=1e-12, atol=1e-12 * ref), k
     assert abs(float(prm["alpha"].grad) - g["alpha"]) <= 1e-12 * abs(g["alpha"])
     # dL/da_0 sums the direct term of |a_1(0)|^2 and the adjoint's: compare on its scale
     ga = np.stack([g["a0"].real, g["a0"].imag], -1)
