@@ -82,12 +82,19 @@ def bytes_per_cell_attempt(p):
     return p.nsub * per_sub + prof
 
 
+# Sources that define the single-problem integrator launch (kernel, engine, stage code, the
+# host code that lays out the cells and partitions the blocks).
+KERNEL_SOURCES = ("cmx_internal.cuh", "cmx_stage.cuh", "cmx_engine.cuh", "cmx_quad.cuh",
+                  "cmx_single.cu", "cmx_kernels.h", "cmx_api.cu", "cmx_layout.cu",
+                  "cmx_layout.h", "cmx_problem.h")
+
+
 def kernel_source_hash():
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2603_03706_b300", "csrc")
-    for fn in sorted(os.listdir(d)):
-        if fn.endswith((".cu", ".cuh", ".h")):
-            h.update(open(os.path.join(d, fn), "rb").read())
+    for fn in KERNEL_SOURCES:
+        h.update(open(os.path.join(d, fn), "rb").read())
+    h.update(open(os.path.join(ROOT, "include", "cmx.h"), "rb").read())
     return h.hexdigest()[:16]
 
 
@@ -276,11 +283,14 @@ def batch_sweep(n_inst, T, stream):
     from paper_2603_03706_b300 import workloads as W
     probs = W.batch_sweep(n_inst=n_inst, T=T)
     cells = sum(p.ncells for p in probs)
+    # launch shape from the batch autotuner (trial batches of every k-th instance)
+    tuned = cmx.batch_autotune(probs, sample=64, attempts=20, stream=stream)
+    shape = dict(bx=tuned["bx"], by=tuned["by"], team=tuned["team"])
     # warm-up of both paths on a few instances
-    b = cmx.BatchSimulation(probs[:8], stream=stream)
+    b = cmx.BatchSimulation(probs[:8], stream=stream, **shape)
     b.run()
     b.close()
-    b = cmx.BatchSimulation(probs, stream=stream)
+    b = cmx.BatchSimulation(probs, stream=stream, **shape)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     st = b.run()
@@ -306,7 +316,8 @@ def batch_sweep(n_inst, T, stream):
             "cell_stage_updates_per_s": st["cell_stage_updates"] / t_batch,
             "sequential_cell_stage_updates_per_s": seq_updates / t_seq,
             "teams": info["teams"], "team_size": info["team_size"], "blocks": info["blocks"],
-            "graph": bool(info["graph"]), "workload": "batch_sweep (spheres 24^3..96^3, 1-3 modes)",
+            "graph": bool(info["graph"]), "window": [shape["bx"], shape["by"]],
+            "autotune_us": tuned["us"], "workload": "batch_sweep (spheres 24^3..96^3, 1-3 modes)",
             "timing": "wall clock, synchronised"}
 
 

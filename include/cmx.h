@@ -278,6 +278,16 @@ int cmx_batch_create(const cmx_instance *inst, int n, const cmx_solver *solver,
                      const cmx_batch_config *cfg, void *stream, cmx_batch **out);
 int cmx_batch_destroy(cmx_batch *b);
 
+/* Batch autotuner: for every candidate launch shape (window 32x8 or 32x16 (two sublattices:
+ * 32x8, 64x4) times team size automatic, 1, 2, 4, 8, 16), build a trial batch over every k-th
+ * instance (k = ceil(n / sample)), time one launch of `attempts` attempts per instance with CUDA
+ * events after a one-attempt warm-up launch, and destroy it.  cfg is read for use_graph and
+ * blocks_per_sm and receives the fastest bx, by, team.  us (may be NULL, 12 entries) gets the
+ * time of each candidate in microseconds (NaN: not runnable), *ncand the number of candidates. */
+int cmx_batch_autotune(const cmx_instance *inst, int n, const cmx_solver *solver, int sample,
+                       int attempts, void *stream, cmx_batch_config *cfg, double *us,
+                       int *ncand);
+
 /* Enqueue ONE launch in which every unfinished instance makes up to n_attempts attempts. */
 int cmx_batch_launch(cmx_batch *b, int n_attempts);
 

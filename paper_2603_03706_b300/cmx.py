@@ -132,6 +132,9 @@ SIGNATURES = {
     "cmx_adjoint_record": (C.c_int, [_P, C.c_int, C.c_longlong]),
     "cmx_adjoint": (C.c_int, [_P, C.c_void_p, C.c_void_p, C.c_int, C.POINTER(Grads)]),
     "cmx_adjoint_steps": (C.c_int, [_P, C.POINTER(C.c_longlong)]),
+    "cmx_batch_autotune": (C.c_int, [C.POINTER(Instance), C.c_int, C.POINTER(Solver), C.c_int,
+                                     C.c_int, C.c_void_p, C.POINTER(BatchConfig), C.c_void_p,
+                                     C.POINTER(C.c_int)]),
     "cmx_eval_rhs_noalloc": (C.c_int, [C.POINTER(Grid), C.c_void_p, C.POINTER(Material),
                                        C.POINTER(Modes), C.c_void_p, C.c_void_p, C.c_void_p,
                                        C.c_void_p, C.c_void_p, C.c_void_p]),
@@ -486,42 +489,70 @@ def _unpack_complex(v, N):
     return v[0:2 * N:2] + 1j * v[1:2 * N:2]
 
 
+def _instances(problems):
+    """cmx_instance array for a list of workloads.Problem (argument conversion only); returns
+    (array, arrays to keep alive, modes per instance, shapes)."""
+    keep = []
+    n = len(problems)
+    arr = (Instance * n)()
+    Ns, shapes = [], []
+    for i, p in enumerate(problems):
+        if p.u is not None:
+            raise ValueError("batched problems use uniform mode profiles (u = None)")
+        mask = np.ascontiguousarray(np.asarray(p.mask, np.uint8).reshape(-1))
+        om, ka, gr, gi = _f64(p.omega), _f64(p.kappa), _f64(p.g_re), _f64(p.g_im)
+        m0 = _f32(p.m0)
+        a0 = np.zeros(max(2 * p.nmodes, 1))
+        if p.nmodes:
+            ac = np.asarray(p.a0, complex).reshape(-1)
+            a0[0:2 * p.nmodes:2], a0[1:2 * p.nmodes:2] = ac.real, ac.imag
+        keep += [mask, om, ka, gr, gi, m0, a0]
+        ins = arr[i]
+        ins.grid = Grid(p.nx, p.ny, p.nz, p.cx, p.cy, p.cz, p.nsub)
+        ins.mask = mask.ctypes.data
+        ins.mat = Material(p.Ms, p.Aex, p.alpha, p.gamma, p.Ku, (C.c_double * 3)(*p.ku_axis),
+                           (C.c_double * 3)(*p.B0), (C.c_double * 3)(*p.Ndemag), p.BE)
+        md = Modes()
+        md.n_modes = p.nmodes
+        md.omega, md.kappa, md.g_re, md.g_im = _dptr(om), _dptr(ka), _dptr(gr), _dptr(gi)
+        md.u, md.u_on_device = None, 0
+        ins.modes = md
+        ins.m0 = m0.ctypes.data
+        ins.a0 = a0.ctypes.data
+        ins.T = p.T
+        Ns.append(p.nmodes)
+        shapes.append((p.nz, p.ny, p.nx))
+    return arr, keep, Ns, shapes
+
+
+def batch_autotune(problems, *, sample=64, attempts=20, blocks_per_sm=0, use_graph=True,
+                   stream=None) -> dict:
+    """cmx_batch_autotune: time the candidate launch shapes on trial batches of every k-th
+    problem and return the fastest (bx, by, team) with the times of all candidates."""
+    arr, keep, _, _ = _instances(problems)
+    p0 = problems[0]
+    sv = Solver(p0.rtol, p0.a_ref, p0.dt0, p0.dt_min, p0.dt_max, 0.0, 0, 0)
+    cfg = BatchConfig(0, 0, 0, blocks_per_sm, 1 if use_graph else 0)
+    us = np.full(12, np.nan)
+    nc = C.c_int()
+    rc = load().cmx_batch_autotune(arr, len(problems), C.byref(sv), int(sample), int(attempts),
+                                   _stream_handle(stream), C.byref(cfg), us.ctypes.data,
+                                   C.byref(nc))
+    if rc != OK:
+        raise CmxError(rc, f"cmx_batch_autotune: {load().cmx_status_string(rc).decode()}")
+    del keep
+    return dict(bx=cfg.bx, by=cfg.by, team=cfg.team, us=us[:nc.value].tolist())
+
+
 class BatchSimulation:
     """One cmx_batch handle (cmx_batch_* calls): independent problems in one persistent launch."""
 
     def __init__(self, problems, *, log_cap=0, trace_cap=0, sample_dt=0.0, solver=None,
                  bx=0, by=0, team=0, blocks_per_sm=0, use_graph=True, stream=None):
         lib = load()
-        keep = []
         n = len(problems)
-        arr = (Instance * n)()
-        self.N, self.shapes, self.nsub = [], [], problems[0].nsub
-        for i, p in enumerate(problems):
-            if p.u is not None:
-                raise ValueError("batched problems use uniform mode profiles (u = None)")
-            mask = np.ascontiguousarray(np.asarray(p.mask, np.uint8).reshape(-1))
-            om, ka, gr, gi = _f64(p.omega), _f64(p.kappa), _f64(p.g_re), _f64(p.g_im)
-            m0 = _f32(p.m0)
-            a0 = np.zeros(max(2 * p.nmodes, 1))
-            if p.nmodes:
-                ac = np.asarray(p.a0, complex).reshape(-1)
-                a0[0:2 * p.nmodes:2], a0[1:2 * p.nmodes:2] = ac.real, ac.imag
-            keep += [mask, om, ka, gr, gi, m0, a0]
-            ins = arr[i]
-            ins.grid = Grid(p.nx, p.ny, p.nz, p.cx, p.cy, p.cz, p.nsub)
-            ins.mask = mask.ctypes.data
-            ins.mat = Material(p.Ms, p.Aex, p.alpha, p.gamma, p.Ku, (C.c_double * 3)(*p.ku_axis),
-                               (C.c_double * 3)(*p.B0), (C.c_double * 3)(*p.Ndemag), p.BE)
-            md = Modes()
-            md.n_modes = p.nmodes
-            md.omega, md.kappa, md.g_re, md.g_im = _dptr(om), _dptr(ka), _dptr(gr), _dptr(gi)
-            md.u, md.u_on_device = None, 0
-            ins.modes = md
-            ins.m0 = m0.ctypes.data
-            ins.a0 = a0.ctypes.data
-            ins.T = p.T
-            self.N.append(p.nmodes)
-            self.shapes.append((p.nz, p.ny, p.nx))
+        arr, keep, self.N, self.shapes = _instances(problems)
+        self.nsub = problems[0].nsub
         p0 = problems[0]
         self.solver = solver or Solver(p0.rtol, p0.a_ref, p0.dt0, p0.dt_min, p0.dt_max, sample_dt,
                                        log_cap, trace_cap)

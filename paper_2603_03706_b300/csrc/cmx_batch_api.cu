@@ -523,6 +523,68 @@ int cmx_batch_run(cmx_batch *b, long long max_attempts, cmx_stats *total)
     return first_err;
 }
 
+int cmx_batch_autotune(const cmx_instance *inst, int n, const cmx_solver *solver, int sample,
+                       int attempts, void *stream, cmx_batch_config *cfg, double *us,
+                       int *ncand)
+{
+    if (!inst || n <= 0 || !solver || !cfg || attempts <= 0) return CMX_EINVAL;
+    if (sample <= 0) sample = n;
+    const int k = (n + sample - 1) / sample;
+    std::vector<cmx_instance> sub;
+    for (int i = 0; i < n; i += k) sub.push_back(inst[i]);
+    const int nsub = inst[0].grid.nsub;
+    const int win[2][2] = {{32, 8}, {nsub == 1 ? 32 : 64, nsub == 1 ? 16 : 4}};
+    const int teams[6] = {0, 1, 2, 4, 8, 16};
+    cmx_solver sv = *solver;
+    sv.log_cap = 0;
+    sv.trace_cap = 0;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return CMX_ECUDA;
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return CMX_ECUDA;
+    }
+    double best = 1e300;
+    cmx_batch_config bestc = *cfg;
+    int c = 0;
+    for (int w = 0; w < 2; w++)
+        for (int t = 0; t < 6; t++, c++) {
+            double v = NAN;
+            cmx_batch_config tc = *cfg;
+            tc.bx = win[w][0];
+            tc.by = win[w][1];
+            tc.team = teams[t];
+            cmx_batch *b = nullptr;
+            if (cmx_batch_create(sub.data(), (int)sub.size(), &sv, &tc, stream, &b) == CMX_OK) {
+                if (run_once(b, 1) == CMX_OK && cudaEventRecord(e0, st) == cudaSuccess &&
+                    run_once(b, attempts) == CMX_OK && cudaEventRecord(e1, st) == cudaSuccess &&
+                    cudaStreamSynchronize(st) == cudaSuccess) {
+                    float ms = 0.f;
+                    cudaEventElapsedTime(&ms, e0, e1);
+                    std::vector<Ctl> cl(b->n);
+                    bool ok = cudaMemcpy(cl.data(), b->ctls, b->n * sizeof(Ctl),
+                                         cudaMemcpyDeviceToHost) == cudaSuccess;
+                    for (const Ctl &x : cl) ok = ok && x.status == 0;
+                    if (ok) v = 1e3 * ms;
+                    if (ok && v < best && tc.team == 0) tc.team = b->team;
+                    if (ok && v < best) {
+                        best = v;
+                        bestc = tc;
+                    }
+                }
+                cmx_batch_destroy(b);
+            }
+            if (us) us[c] = v;
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (ncand) *ncand = c;
+    if (!(best < 1e300)) return CMX_ECUDA;
+    *cfg = bestc;
+    return CMX_OK;
+}
+
 int cmx_batch_get_a(cmx_batch *b, int i, double *a)
 {
     if (!b || i < 0 || i >= b->n || !a) return bfail(b, CMX_EINVAL, "bad argument");

@@ -112,3 +112,23 @@ def test_batch_rejects_profiles():
     p = W.multimode_sphere(nx=16, ny=16, nz=16)
     with pytest.raises(ValueError):
         cmx.BatchSimulation([p])
+
+
+def test_batch_autotune_picks_a_runnable_shape():
+    probs = small_batch(n_inst=9, seed=8)
+    t = cmx.batch_autotune(probs, sample=5, attempts=4)
+    assert (t["bx"], t["by"]) in ((32, 8), (32, 16)) and t["team"] >= 1, t
+    assert len(t["us"]) == 12 and np.nanmin(t["us"]) > 0
+    b = cmx.BatchSimulation(probs, log_cap=100, bx=t["bx"], by=t["by"], team=t["team"])
+    st = b.run(max_attempts=50)
+    assert st["attempts"] == 50 * len(probs) or st["t"] > 0
+    for i, p in enumerate(probs):
+        log = b.get_log(i)
+        dts = log["dt"][log["accepted"]]
+        it = O.Integrator(O.OracleProblem(p))
+        rc, olog = it.replay(dts)
+        assert rc == 0
+        ost = it.state()
+        m_orc = ost["m"].reshape(1, 3, p.nz, p.ny, p.nx)
+        assert np.abs(masked(p, b.get_m(i)) - masked(p, m_orc)).max() <= TOL_M
+    b.close()
