@@ -510,6 +510,8 @@ __device__ bool integrate(const Ctx &c, const Team &tm, SM &sm, Local &L, Coef &
         for (int t = threadIdx.x; t < se - sb; t += blockDim.x) sm.seg[t] = __ldg(&c.tiles[sb + t]);
     }
     __syncthreads();
+    stage_cache_rows(c, sm);
+    __syncthreads();
     bool ok = true;
     Pipe pp;
     for (;;) {

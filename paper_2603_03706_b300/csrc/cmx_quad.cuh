@@ -249,6 +249,12 @@ __device__ __forceinline__ void quad_cell(const Ctx &c, QuadSmem<HU> &sm, float 
     }
 }
 
+// Quad windows read their row entries from the table (no cache).
+template <bool HU>
+__device__ __forceinline__ void stage_cache_rows(const Ctx &, QuadSmem<HU> &)
+{
+}
+
 // Start of stage S: the row entries of the first planes and an L2 prefetch of the first plane
 // of the block's stream (the loads themselves are issued by stage_run).
 template <int S, bool HU>

@@ -122,6 +122,9 @@ __device__ __forceinline__ void cp_async_wait()
     asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
+// Row-table entries cached for the first planes of a block's stream.
+constexpr int ROWC = 16;
+
 // Shared memory of a block whose threads cover a WX x WY window: the interior
 // (WX-2) x (WY-2) cells are computed, the one-cell rim is the halo.  D planes of raw operands
 // (m_n and the slopes of the stage) are in flight as asynchronous copies while the block
@@ -151,6 +154,8 @@ struct StageSmem {
     float redmax[32];
     const float *kp[7];           // physical slope buffers in logical order
     int2 rows[8][WY];             // row-table entries of the window rows, by plane mod 8
+    int2 rowc[ROWC][WY];          // the same for the first ROWC planes of the stream (every
+                                  // stage starts there), filled once per launch
     int4 seg[MAX_BLOCK_SEGMENTS]; // this block's segments (x0, y0, z0, z1)
     int nseg;
 };
@@ -415,7 +420,8 @@ __device__ void tiles_begin(const Ctx &c, StageSmem<NS, WX, WY, HU> &sm, const f
         if (threadIdx.x < WY && g < pp.gend) {
             cursor_seek(sm, pp.cr, g);
             sm.rows[g & 7][threadIdx.x] =
-                row_entry(c, pp.cr.y0 - 1 + threadIdx.x, pp.cr.z0 - 1 + (g - pp.cr.off));
+                g < ROWC ? sm.rowc[g][threadIdx.x]
+                         : row_entry(c, pp.cr.y0 - 1 + threadIdx.x, pp.cr.z0 - 1 + (g - pp.cr.off));
         }
     __syncthreads();
     for (; pp.nq < D; pp.nq++) {
@@ -444,7 +450,8 @@ __device__ void tiles_run(const Ctx &c, StageSmem<NS, WX, WY, HU> &sm, float *ko
         if (threadIdx.x < WY && g < gend) {
             cursor_seek(sm, pp.cr, g);
             sm.rows[g & 7][threadIdx.x] =
-                row_entry(c, pp.cr.y0 - 1 + threadIdx.x, pp.cr.z0 - 1 + (g - pp.cr.off));
+                g < ROWC ? sm.rowc[g][threadIdx.x]
+                         : row_entry(c, pp.cr.y0 - 1 + threadIdx.x, pp.cr.z0 - 1 + (g - pp.cr.off));
         }
     };
     auto inner_at = [&](const Cursor &cu, int g) {
@@ -488,6 +495,23 @@ __device__ void tiles_run(const Ctx &c, StageSmem<NS, WX, WY, HU> &sm, float *ko
         compute_cell<NS, WX, WY, HU, S>(c, sm, kout, mnew, cf, p, ucur, tslot, rslot, acc);
     }
     cp_async_wait<0>();
+}
+
+// Row-table entries of the first ROWC planes of the block's stream into the cache (once per
+// launch, after the block's segments are known).
+template <int NS, int WX, int WY, bool HU>
+__device__ void stage_cache_rows(const Ctx &c, StageSmem<NS, WX, WY, HU> &sm)
+{
+    if (sm.nseg == 0) return;
+    int gend = 0;
+    for (int t = 0; t < sm.nseg; t++) gend += sm.seg[t].w - sm.seg[t].z + 2;
+    const int n = (gend < ROWC ? gend : ROWC) * WY;
+    for (int e = threadIdx.x; e < n; e += WX * WY) {
+        const int g = e / WY, r = e - g * WY;
+        Cursor cu = cursor_start(sm);
+        cursor_seek(sm, cu, g);
+        sm.rowc[g][r] = row_entry(c, cu.y0 - 1 + r, cu.z0 - 1 + (g - cu.off));
+    }
 }
 
 // Engine-facing names of the stage code of this window type (overloaded by smem type).
