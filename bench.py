@@ -98,9 +98,10 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(workload):
+def recorded_traffic(workload, attempts):
     """DRAM bytes per launch from a committed ncu capture, if it was taken on the current kernel
-    source (profiles/traffic.json: workload -> {bytes_per_launch, source_hash, ...})."""
+    source (profiles/traffic.json: workload -> {bytes per launch at the bench's attempts, or
+    bytes per attempt for workloads whose traffic grows with the attempts, source_hash, ...})."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         rec = json.load(open(path)).get(workload)
@@ -108,7 +109,11 @@ def recorded_traffic(workload):
         return None
     if not rec or rec.get("source_hash") != kernel_source_hash():
         return None
-    return rec.get("bytes_per_launch_at_bench_attempts")
+    if rec.get("bytes_per_launch_at_bench_attempts") is not None:
+        return rec["bytes_per_launch_at_bench_attempts"]
+    if rec.get("bytes_per_attempt") is not None:
+        return rec["bytes_per_attempt"] * attempts
+    return None
 
 
 def measured_peaks():
@@ -460,7 +465,7 @@ def main():
                        "parallelism": "replicas" if world > 1 else "single"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak_gbs, "unit": "GB/s",
                          "frac": achieved / peak_gbs,
-                         "traffic": recorded_traffic(p.name),
+                         "traffic": recorded_traffic(p.name, A),
                          "bytes_per_cell_attempt": bytes_per_cell_attempt(p),
                          "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else
                          "fallback 6400 GB/s"},
