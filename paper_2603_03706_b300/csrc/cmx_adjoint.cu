@@ -32,6 +32,7 @@ struct RevSmem {
     float bb[R][NQ][W];          // field adjoint Bbar of four planes (0 where absent)
     float pr[R][W];              // presence
     int2 rows[8][WY];
+    int2 rowc[ROWC][WY];         // row entries of the first ROWC planes of the stream
     int4 seg[MAX_BLOCK_SEGMENTS];
     int nseg;
     F2 red[32][MAXN + 1];
@@ -134,11 +135,22 @@ __device__ void rev_grid_reduce(const AdjArgs &A, F2 (*red)[MAXN + 1], double *o
     while (QP < nq) QP <<= 1;
     const int q = threadIdx.x & (QP - 1), grp = threadIdx.x / QP, ngrp = NT / QP;
     F2 s = {0.f, 0.f};
-    if (q < nq)
-        for (int b = grp; b < G; b += ngrp) {
-            const float2 v = __ldcg(A.part + (size_t)b * nq + q);
-            s = f2_add(s, {v.x, v.y});
+    if (q < nq) {
+        // all of this thread's partials in one round of loads, then the fixed-order sum
+        constexpr int KMAX = 8;
+        float2 v[KMAX];
+#pragma unroll
+        for (int k = 0; k < KMAX; k++) {
+            const int b = grp + k * ngrp;
+            v[k] = b < G ? __ldcg(A.part + (size_t)b * nq + q) : make_float2(0.f, 0.f);
         }
+#pragma unroll
+        for (int k = 0; k < KMAX; k++) s = f2_add(s, {v[k].x, v[k].y});
+        for (int b = grp + KMAX * ngrp; b < G; b += ngrp) {
+            const float2 w = __ldcg(A.part + (size_t)b * nq + q);
+            s = f2_add(s, {w.x, w.y});
+        }
+    }
     for (int o = 16; o >= QP; o >>= 1) s = f2_add(s, f2_shfl_xor(s, o));
     __syncthreads();   // red[] of the block reduction may still be read
     if (lane < QP && lane < nq) red[warp][lane] = s;
@@ -316,7 +328,8 @@ __device__ void rev_tiles(const AdjArgs &A, RevSmem<NS, WX, WY> &sm, const RevLo
     auto load_rows = [&](int g) {
         if (i < WY && g < gend) {
             cursor_seek(sm, crow, g);
-            sm.rows[g & 7][i] = row_entry(c, crow.y0 - 1 + i, crow.z0 - 1 + (g - crow.off));
+            sm.rows[g & 7][i] = g < ROWC ? sm.rowc[g][i]
+                                         : row_entry(c, crow.y0 - 1 + i, crow.z0 - 1 + (g - crow.off));
         }
     };
     auto issue = [&](int g, RevRaw<NQ, NWS> &rw) {
@@ -487,8 +500,10 @@ __device__ bool rev_stage(const AdjArgs &A, RevSmem<NS, WX, WY> &sm, RevLocal &L
     return true;
 }
 
+// One sublattice: two 256-thread blocks per SM (128 registers; the more resident warps hide the
+// per-plane latency better than the registers they cost); two sublattices: one block.
 template <int NS, int WX, int WY, bool HU>
-__global__ void __launch_bounds__(WX *WY, 1) rev_kernel(AdjArgs A)
+__global__ void __launch_bounds__(WX *WY, NS == 1 ? 2 : 1) rev_kernel(AdjArgs A)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     auto &sm = *reinterpret_cast<RevSmem<NS, WX, WY> *>(smem_raw);
@@ -523,6 +538,18 @@ __global__ void __launch_bounds__(WX *WY, 1) rev_kernel(AdjArgs A)
     if (tid == 0) {
         L.galpha = 0.0;
         L.bar_target = 0;
+    }
+    __syncthreads();
+    if (sm.nseg > 0) {   // row entries of the first planes of the stream, once per launch
+        int gend = 0;
+        for (int t = 0; t < sm.nseg; t++) gend += sm.seg[t].w - sm.seg[t].z + 2;
+        const int n = (gend < ROWC ? gend : ROWC) * WY;
+        for (int e = tid; e < n; e += WX * WY) {
+            const int g = e / WY, r = e - g * WY;
+            Cursor cu = cursor_start(sm);
+            cursor_seek(sm, cu, g);
+            sm.rowc[g][r] = row_entry(c, cu.y0 - 1 + r, cu.z0 - 1 + (g - cu.off));
+        }
     }
     __syncthreads();
     bool ok = true;
