@@ -184,13 +184,6 @@ int install_tiling(cmx_problem *h, const std::vector<Column> &cols, int blocks, 
     h->bz = bz;
     h->bps = occ;
     h->blocks = blocks;
-    if (h->part) cudaFree(h->part);
-    if (h->errpart) cudaFree(h->errpart);
-    h->part = nullptr;
-    h->errpart = nullptr;
-    if (dalloc(&h->part, (size_t)h->blocks * 2 * std::max(1, h->N)) != cudaSuccess ||
-        dalloc(&h->errpart, (size_t)h->blocks) != cudaSuccess)
-        return fail(h, CMX_ENOMEM, "partials");
     return CMX_OK;
 }
 
@@ -203,8 +196,6 @@ Ctx cmx_host::make_ctx(const cmx_problem *h)
     c.seg_begin = h->seg_begin;
     c.ntiles = h->ntiles;
     c.bz = h->bz;
-    c.part = h->part;
-    c.errpart = h->errpart;
     c.timeout_ns = h->timeout_ns;
     return c;
 }
@@ -306,7 +297,7 @@ void free_all(cmx_problem *h)
 {
     void *ptrs[] = {h->rows, h->active, h->box_of_cell, h->tiles, h->seg_begin, h->u,
                     h->mbuf[0], h->mbuf[1],
-                    h->ctl, h->part, h->errpart, h->log, h->log_a, h->log_mm, h->tr_t, h->tr_a,
+                    h->ctl, h->log, h->log_a, h->log_mm, h->tr_t, h->tr_a,
                     h->tr_mm, h->replay_dts, h->dense, h->ev_m, h->ev_k, h->ev_ctl};
     for (void *p : ptrs)
         if (p) cudaFree(p);

@@ -30,7 +30,7 @@ struct Inst {
     std::vector<int> begin;
     // offsets into the device pools
     size_t o_m[2] = {0, 0}, o_k[7] = {}, o_rows = 0, o_box = 0, o_act = 0, o_seg = 0,
-           o_begin = 0, o_part = 0, o_err = 0, o_log = 0, o_loga = 0, o_tr = 0, o_tra = 0;
+           o_begin = 0, o_log = 0, o_loga = 0, o_tr = 0, o_tra = 0;
     bool has_act = false;
 };
 
@@ -54,8 +54,6 @@ struct cmx_batch {
     int4 *segs = nullptr;
     Ctl *ctls = nullptr;
     Ctl **ctlp = nullptr;
-    float2 *part = nullptr;
-    float *errpart = nullptr;
     cmx_step *log = nullptr;
     double *logd = nullptr;      // log_a, log_mm
     double *trd = nullptr;       // tr_t, tr_a, tr_mm
@@ -118,8 +116,8 @@ __global__ void bscatter_kernel(const float *compact, float *dense, const int *b
 void free_batch(cmx_batch *b)
 {
     if (b->gexec) cudaGraphExecDestroy(b->gexec);
-    void *p[] = {b->fpool, b->rows, b->ipool, b->act, b->segs, b->ctls, b->ctlp, b->part,
-                 b->errpart, b->log, b->logd, b->trd, b->ctx, b->queue, b->qbegin, b->pending,
+    void *p[] = {b->fpool, b->rows, b->ipool, b->act, b->segs, b->ctls, b->ctlp,
+                 b->log, b->logd, b->trd, b->ctx, b->queue, b->qbegin, b->pending,
                  b->dense};
     for (void *q : p)
         if (q) cudaFree(q);
@@ -291,7 +289,7 @@ int cmx_batch_create(const cmx_instance *in, int n, const cmx_solver *solver,
     // pool sizes
     const int nq = 3 * nsub;
     const int lc = std::max(1, solver->log_cap), tc = std::max(1, solver->trace_cap);
-    size_t nf = 0, nrows = 0, nint = 0, nact = 0, nseg = 0, npart = 0, nlog = 0, nlogd = 0,
+    size_t nf = 0, nrows = 0, nint = 0, nact = 0, nseg = 0, nlog = 0, nlogd = 0,
            ntrd = 0, maxbox = 0;
     for (Inst &I : b->inst) {
         const size_t nc = up64((size_t)I.lay.ncell);
@@ -304,18 +302,14 @@ int cmx_batch_create(const cmx_instance *in, int n, const cmx_solver *solver,
         if (I.has_act) I.o_act = nact, nact += ((size_t)I.lay.ncell + 31) / 32;
         I.o_seg = nseg, nseg += I.segs.size();
         const int Q = 2 * std::max(1, I.N);
-        I.o_part = npart, npart += (size_t)K * Q;
-        I.o_err = I.o_part / Q;   // one error slot per block, K per instance
         I.o_log = nlog, nlog += lc;
         I.o_loga = nlogd, nlogd += 2 * (size_t)lc * Q;
         I.o_tr = ntrd, ntrd += tc + 2 * (size_t)tc * Q;
         maxbox = std::max(maxbox, (size_t)I.grid.nx * I.grid.ny * I.grid.nz);
     }
-    size_t nerr = 0;
-    for (Inst &I : b->inst) I.o_err = nerr, nerr += K;
     if (balloc(&b->fpool, nf) || balloc(&b->rows, nrows) || balloc(&b->ipool, nint) ||
         balloc(&b->act, nact) || balloc(&b->segs, nseg) || balloc(&b->ctls, (size_t)n) ||
-        balloc(&b->ctlp, (size_t)n) || balloc(&b->part, npart) || balloc(&b->errpart, nerr) ||
+        balloc(&b->ctlp, (size_t)n) ||
         balloc(&b->log, nlog) || balloc(&b->logd, nlogd) || balloc(&b->trd, ntrd) ||
         balloc(&b->ctx, (size_t)n) || balloc(&b->queue, queue.size()) ||
         balloc(&b->qbegin, qbegin.size()) || balloc(&b->pending, 1) ||
@@ -423,8 +417,6 @@ int cmx_batch_create(const cmx_instance *in, int n, const cmx_solver *solver,
         c.dt_max = solver->dt_max;
         c.sample_dt = solver->sample_dt;
         c.ctl = b->ctls + i;
-        c.part = b->part + I.o_part;
-        c.errpart = b->errpart + I.o_err;
         c.log = b->log + I.o_log;
         const int Q = 2 * std::max(1, I.N);
         c.log_a = b->logd + I.o_loga;

@@ -107,8 +107,6 @@ struct Ctx {
     // solver
     double rtol, a_ref, dt_min, dt_max, sample_dt;
     Ctl *ctl;
-    float2 *part;                    // [gridDim][2N] overlap partials (hi, lo pairs)
-    float *errpart;                  // [gridDim] block error maxima
     // log / trace
     cmx_step *log;
     double *log_a, *log_mm;

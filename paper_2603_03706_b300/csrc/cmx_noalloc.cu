@@ -136,11 +136,9 @@ extern "C" int cmx_eval_rhs_noalloc(const cmx_grid *grid, const uint8_t *mask,
     float *mc = cv.take<float>((size_t)nq * nc);
     float *kc = cv.take<float>((size_t)nq * nc);
     Ctl *ctl = cv.take<Ctl>(1);
-    float2 *part = cv.take<float2>((size_t)blocks * 2 * std::max(1, N));
-    float *errpart = cv.take<float>(blocks);
     float *udense = has_u && !modes->u_on_device ? cv.take<float>((size_t)N * nbox) : nullptr;
     if (!rows || !box || (lay.holes && !act) || !tiles || !sbeg || (has_u && !uc) || !mc ||
-        !kc || !ctl || !part || !errpart || (has_u && !modes->u_on_device && !udense))
+        !kc || !ctl || (has_u && !modes->u_on_device && !udense))
         return CMX_ESCRATCH;   // larger than CMX_NOALLOC_SCRATCH_BYTES
 
     // tables and inputs into the scratch (every field the kernel reads is written here)
@@ -222,8 +220,6 @@ extern "C" int cmx_eval_rhs_noalloc(const cmx_grid *grid, const uint8_t *mask,
     c.dt_min = 1e-18;
     c.dt_max = 1e-11;
     c.ctl = ctl;
-    c.part = part;
-    c.errpart = errpart;
     c.timeout_ns = 2000000000LL;
     c.stage_only = 1;
     if (launch_single(c, bx, by, blocks, s) != cudaSuccess) return CMX_ECUDA;

@@ -38,8 +38,6 @@ struct cmx_problem {
     float *mbuf[2] = {nullptr, nullptr};
     float *kbuf[7] = {};
     Ctl *ctl = nullptr;
-    float2 *part = nullptr;
-    float *errpart = nullptr;
     cmx_step *log = nullptr;
     double *log_a = nullptr, *log_mm = nullptr;
     double *tr_t = nullptr, *tr_a = nullptr, *tr_mm = nullptr;

@@ -232,7 +232,6 @@ __device__ __forceinline__ void issue_plane(const Ctx &c, StageSmem<NS, WX, WY, 
     if (g < gend) {
         const int slot = g % D;
         float *rp = sm.raw + (size_t)slot * NA * NQ * W;
-        const int q = g - cu.off;
         const int idx = corner ? -1 : row_index(c, sm.rows[g & 7][r], cu.x0 - 1 + col);
         sm.ridx[slot][i] = idx;
         if (idx >= 0) {
