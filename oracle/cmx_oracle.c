@@ -17,6 +17,8 @@
  *                    + diagonal demag + B_rf (+ inter-sublattice exchange -B_E m_other, AFM,
  *                    Sec. II G); for two sublattices the cavity couples to (m1 + m2)/2.
  *   time stepping    Dormand-Prince 5(4), FSAL; the paper only says "adaptive RK45" (Sec. III A).
+ *   drive            optional eta_n(t) added to da_n/dt (Eq. (1), (12)), a Gaussian pulse
+ *                    (Sec. IV A), evaluated at each stage's time t + c_s h.
  *   adjoint          orc_rhs_vjp / orc_adjoint: reverse-mode derivative of the replayed steps
  *                    (not in the paper; the gradient form added beside the integrator).
  *
@@ -52,6 +54,10 @@ typedef struct {
     double Ms, Aex, alpha, gamma, Ku, ku[3], B0[3], Nd[3], BE;
     const double *u; /* nmodes * nbox, or NULL: every profile is 1 */
     const double *omega, *kappa, *g_re, *g_im;
+    /* external drive eta_n(t) = (drive_re + i drive_im)_n exp(-(t - drive_t0)^2 / (2 sigma^2))
+       added to da_n/dt (Eq. (1), (12)); drive_re == NULL: no drive */
+    const double *drive_re, *drive_im;
+    double drive_t0, drive_sigma;
 } orc_problem;
 
 typedef struct {
@@ -312,6 +318,26 @@ void orc_state_get(const orc_state *S, double *m, double *a, double *t, double *
     }
 }
 
+/* The drive at time t added to the cavity slopes da (Eq. (1), (12)). */
+static void add_drive(const orc_problem *P, double t, double *da)
+{
+    if (!P->drive_re) return;
+    const double x = (t - P->drive_t0) / P->drive_sigma;
+    const double env = exp(-0.5 * x * x);
+    for (int n = 0; n < P->nmodes; n++) {
+        da[2 * n] += P->drive_re[n] * env;
+        da[2 * n + 1] += P->drive_im[n] * env;
+    }
+}
+
+/* Node c_s of stage s (0-based) of the tableau: the row sum of its couplings. */
+static double dp_node(int s)
+{
+    double c = 0.0;
+    for (int j = 0; j < 6; j++) c += DP_A[s][j];
+    return c;
+}
+
 /*
  * One Dormand-Prince attempt of size h from (S->m, S->a).  On return the 5th-order point y7 is
  * in (S->ym, S->ya), its slope in km[6]/ka[6] and the scaled error in *err.
@@ -325,6 +351,7 @@ static int dp_attempt(const orc_problem *P, orc_state *S, const orc_solver *sv, 
     if (!S->k1_valid) {
         int rc = orc_rhs(P, S->m, S->a, S->km[0], S->ka[0], mm);
         if (rc) return rc;
+        add_drive(P, S->t, S->ka[0]);
         S->k1_valid = 1;
     }
     for (int s = 1; s < 7; s++) {
@@ -341,6 +368,7 @@ static int dp_attempt(const orc_problem *P, orc_state *S, const orc_solver *sv, 
         }
         int rc = orc_rhs(P, S->ym, S->ya, S->km[s], S->ka[s], mm);
         if (rc) return rc;
+        add_drive(P, S->t + dp_node(s) * h, S->ka[s]);
     }
     memcpy(S->mm7, mm, 2 * N * sizeof(double));
 
@@ -691,7 +719,7 @@ int orc_rhs_vjp(const orc_problem *P, const double *m, const double *a, const do
  */
 int orc_adjoint(const orc_problem *P, const orc_solver *sv, const double *m0, const double *a0,
                 const double *dts, long n, const double *dL_da, const double *dL_dm,
-                double *gm0, double *ga0, orc_grads *G)
+                double *gm0, double *ga0, orc_grads *G, double t_start)
 {
     orc_state *S = orc_state_new(P);
     if (!S) return ORC_ENOMEM;
@@ -702,11 +730,12 @@ int orc_adjoint(const orc_problem *P, const orc_solver *sv, const double *m0, co
     double *Kst = malloc((size_t)(n > 0 ? n : 1) * nv * sizeof(double));
     double *Ast = malloc((size_t)(n > 0 ? n : 1) * na * sizeof(double));
     double *KAst = malloc((size_t)(n > 0 ? n : 1) * na * sizeof(double));
+    double *Tst = malloc((size_t)(n > 0 ? n : 1) * sizeof(double));
     double *Ym[7], *Ya[7], *Fm[7], *Fa[7];
     double *lm = calloc(nv, sizeof(double)), *la = calloc(na, sizeof(double));
     double *lkm = calloc(nv, sizeof(double)), *lka = calloc(na, sizeof(double));
     double *wkm = calloc(nv, sizeof(double)), *wka = calloc(na, sizeof(double));
-    int ok = Mst && Kst && Ast && KAst && lm && la && lkm && lka && wkm && wka;
+    int ok = Mst && Kst && Ast && KAst && Tst && lm && la && lkm && lka && wkm && wka;
     for (int s = 0; s < 7; s++) {
         Ym[s] = calloc(nv, sizeof(double));
         Fm[s] = calloc(nv, sizeof(double));
@@ -720,9 +749,10 @@ int orc_adjoint(const orc_problem *P, const orc_solver *sv, const double *m0, co
     }
 
     /* forward: keep (m_i, a_i, k1_i) of every step */
-    orc_state_set(S, m0, a0, 0.0, n > 0 ? dts[0] : 1.0);
+    orc_state_set(S, m0, a0, t_start, n > 0 ? dts[0] : 1.0);
     for (long i = 0; i < n; i++) {
         double err;
+        Tst[i] = S->t;
         memcpy(Mst + i * nv, S->m, nv * sizeof(double));
         memcpy(Ast + i * na, S->a, 2 * N * sizeof(double));
         rc = dp_attempt(P, S, sv, dts[i], &err);
@@ -742,6 +772,7 @@ int orc_adjoint(const orc_problem *P, const orc_solver *sv, const double *m0, co
         memcpy(S->a, Ast + i * na, 2 * N * sizeof(double));
         memcpy(S->km[0], Kst + i * nv, nv * sizeof(double));
         memcpy(S->ka[0], KAst + i * na, 2 * N * sizeof(double));
+        S->t = Tst[i];
         S->k1_valid = 1;
         rc = dp_attempt(P, S, sv, h, &err);
         if (rc) goto done;
@@ -824,6 +855,7 @@ done:
     free(Kst);
     free(Ast);
     free(KAst);
+    free(Tst);
     free(lm);
     free(la);
     free(lkm);

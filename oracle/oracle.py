@@ -51,7 +51,9 @@ class _Problem(C.Structure):
                 ("ku", C.c_double * 3), ("B0", C.c_double * 3), ("Nd", C.c_double * 3),
                 ("BE", C.c_double), ("u", C.POINTER(C.c_double)),
                 ("omega", C.POINTER(C.c_double)), ("kappa", C.POINTER(C.c_double)),
-                ("g_re", C.POINTER(C.c_double)), ("g_im", C.POINTER(C.c_double))]
+                ("g_re", C.POINTER(C.c_double)), ("g_im", C.POINTER(C.c_double)),
+                ("drive_re", C.POINTER(C.c_double)), ("drive_im", C.POINTER(C.c_double)),
+                ("drive_t0", C.c_double), ("drive_sigma", C.c_double)]
 
 
 class _Solver(C.Structure):
@@ -100,7 +102,7 @@ def lib():
         _lib.orc_rhs_vjp.argtypes = [P, dp, dp, dp, dp, dp, dp, G]
         _lib.orc_rhs_vjp.restype = C.c_int
         _lib.orc_adjoint.argtypes = [P, C.POINTER(_Solver), dp, dp, dp, C.c_long, dp, dp, dp,
-                                     dp, G]
+                                     dp, G, C.c_double]
         _lib.orc_adjoint.restype = C.c_int
     return _lib
 
@@ -134,6 +136,16 @@ class OracleProblem:
         s.u = _dptr(self.u) if self.u is not None else C.POINTER(C.c_double)()
         s.omega, s.kappa = _dptr(self.omega), _dptr(self.kappa)
         s.g_re, s.g_im = _dptr(self.g_re), _dptr(self.g_im)
+        drive = getattr(p, "drive", None)
+        if drive is not None:
+            d = np.asarray(drive, complex).reshape(-1)
+            self.drive_re = np.ascontiguousarray(d.real, np.float64)
+            self.drive_im = np.ascontiguousarray(d.imag, np.float64)
+            s.drive_re, s.drive_im = _dptr(self.drive_re), _dptr(self.drive_im)
+            s.drive_t0, s.drive_sigma = p.drive_t0, p.drive_sigma
+        else:
+            s.drive_re = s.drive_im = C.POINTER(C.c_double)()
+            s.drive_t0, s.drive_sigma = 0.0, 1.0
         self.s = s
         self.solver = _Solver(p.rtol, p.a_ref, p.dt_min, p.dt_max)
 
@@ -352,7 +364,7 @@ def rhs_vjp(op: OracleProblem, m, a, wm, wa):
     return d
 
 
-def adjoint(op: OracleProblem, m0, a0, dts, dL_da=None, dL_dm=None):
+def adjoint(op: OracleProblem, m0, a0, dts, dL_da=None, dL_dm=None, t0: float = 0.0):
     """Gradient of L(a_0..a_n, m_n) through the replayed steps dts (n = len(dts)).
 
     dL_da: (n+1, 2N) packed reals (row i = dL/d a_i) or None; dL_dm: flat like m or None.
@@ -375,7 +387,7 @@ def adjoint(op: OracleProblem, m0, a0, dts, dL_da=None, dL_dm=None):
     rc = lib().orc_adjoint(op.ref, C.byref(op.solver), _dptr(m0), _dptr(a0), _dptr(dts), n,
                            _dptr(la) if la is not None else null,
                            _dptr(lm) if lm is not None else null, _dptr(gm0), _dptr(ga0),
-                           C.byref(g.s))
+                           C.byref(g.s), float(t0))
     if rc:
         raise RuntimeError(f"orc_adjoint failed: {rc}")
     d = g.as_dict()

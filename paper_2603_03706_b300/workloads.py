@@ -68,6 +68,10 @@ class Problem:
     dt_min: float = 1e-18
     dt_max: float = 1e-11
     name: str = ""
+    # external drive eta_n(t) = drive_n exp(-(t - drive_t0)^2 / (2 drive_sigma^2)) on da_n/dt
+    drive: Optional[np.ndarray] = None   # (N,) complex amplitudes [1/s], or None
+    drive_t0: float = 0.1e-9
+    drive_sigma: float = 20e-12
 
     @property
     def nmodes(self) -> int:
