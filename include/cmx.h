@@ -193,6 +193,13 @@ int cmx_set_timeout(cmx_problem *h, long long ns);
  * the other blocks reach their wait limit; -1 disables.  Used only to test CMX_ETIMEOUT. */
 int cmx_debug_skip_arrival(cmx_problem *h, int block);
 
+/* External drive of the cavities (Eq. (1), (12)): eta_n(t) = (eta_re + i eta_im)_n
+ * exp(-(t - t0)^2 / (2 sigma^2)) is added to da_n/dt, evaluated at each stage's time (the
+ * Gaussian pulse of Sec. IV A: sigma = 20 ps, t0 = 0.1 ns).  eta_re, eta_im: host, n_modes
+ * each [1/s]; eta_re == NULL switches the drive off.  Applies to the following launches. */
+int cmx_set_drive(cmx_problem *h, const double *eta_re, const double *eta_im, double t0,
+                  double sigma);
+
 /* Autotuner: time `attempts` Dormand-Prince attempts (after a one-attempt warm-up) from the
  * current state with each compiled one-cell window (32x8, 32x16, 64x4; blocks_per_sm and bz of
  * the current tiling), restore the state after each trial (m, FSAL slope, control block; the
@@ -287,6 +294,12 @@ int cmx_batch_destroy(cmx_batch *b);
 int cmx_batch_autotune(const cmx_instance *inst, int n, const cmx_solver *solver, int sample,
                        int attempts, void *stream, cmx_batch_config *cfg, double *us,
                        int *ncand);
+
+/* The same drive for every instance: n_eta amplitudes (host arrays, n_eta <= CMX_MAX_MODES) for
+ * modes 0 .. n_eta-1, zero for higher modes; instance i uses its first n_modes(i).  See
+ * cmx_set_drive; eta_re == NULL switches the drive off. */
+int cmx_batch_set_drive(cmx_batch *b, const double *eta_re, const double *eta_im, int n_eta,
+                        double t0, double sigma);
 
 /* Enqueue ONE launch in which every unfinished instance makes up to n_attempts attempts. */
 int cmx_batch_launch(cmx_batch *b, int n_attempts);

@@ -129,6 +129,9 @@ SIGNATURES = {
                                  C.POINTER(C.c_longlong), C.POINTER(C.c_int)]),
     "cmx_batch_last_error": (C.c_char_p, [_P]),
     "cmx_autotune": (C.c_int, [_P, C.c_int, C.c_void_p, C.c_void_p]),
+    "cmx_set_drive": (C.c_int, [_P, C.c_void_p, C.c_void_p, C.c_double, C.c_double]),
+    "cmx_batch_set_drive": (C.c_int, [_P, C.c_void_p, C.c_void_p, C.c_int, C.c_double,
+                                      C.c_double]),
     "cmx_adjoint_record": (C.c_int, [_P, C.c_int, C.c_longlong]),
     "cmx_adjoint": (C.c_int, [_P, C.c_void_p, C.c_void_p, C.c_int, C.POINTER(Grads)]),
     "cmx_adjoint_steps": (C.c_int, [_P, C.POINTER(C.c_longlong)]),
@@ -247,6 +250,8 @@ class Simulation:
         sim = cls(g, p.mask, mt, p.omega, p.kappa, p.g_re, p.g_im,
                   p.u if u is None else u, sv, tl, stream)
         sim.set_state(p.m0, p.a0, 0.0)
+        if getattr(p, "drive", None) is not None:
+            sim.set_drive(p.drive, p.drive_t0, p.drive_sigma)
         return sim
 
     # -- lifetime ----------------------------------------------------------------------------
@@ -467,6 +472,19 @@ class Simulation:
     def debug_skip_arrival(self, block: int):
         self._check(load().cmx_debug_skip_arrival(self.h, int(block)), "debug_skip_arrival")
 
+    def set_drive(self, eta=None, t0: float = 0.1e-9, sigma: float = 20e-12):
+        """cmx_set_drive: Gaussian drive eta_n exp(-(t-t0)^2/(2 sigma^2)) on da_n/dt
+        (eta: N complex amplitudes [1/s]; None switches it off)."""
+        if eta is None:
+            self._check(load().cmx_set_drive(self.h, None, None, 0.0, 1.0), "set_drive")
+            return
+        e = np.asarray(eta, complex).reshape(-1)
+        if e.size != self.N:
+            raise ValueError("one drive amplitude per mode")
+        re, im = _f64(e.real), _f64(e.imag)
+        self._check(load().cmx_set_drive(self.h, re.ctypes.data, im.ctypes.data, float(t0),
+                                         float(sigma)), "set_drive")
+
     def autotune(self, attempts: int = 20) -> dict:
         """cmx_autotune: time the compiled windows from the current state, keep the fastest."""
         t = Tiling()
@@ -564,6 +582,21 @@ class BatchSimulation:
             raise CmxError(rc, f"cmx_batch_create: {lib.cmx_status_string(rc).decode()}")
         self.h = h
         self.n = n
+        if getattr(p0, "drive", None) is not None:
+            self.set_drive(p0.drive, p0.drive_t0, p0.drive_sigma)
+
+    def set_drive(self, eta=None, t0: float = 0.1e-9, sigma: float = 20e-12):
+        """cmx_batch_set_drive: the same Gaussian drive for every instance (eta: amplitudes
+        of modes 0.. [1/s]; None switches it off)."""
+        lib = load()
+        if eta is None:
+            rc = lib.cmx_batch_set_drive(self.h, None, None, 0, 0.0, 1.0)
+        else:
+            e = np.asarray(eta, complex).reshape(-1)
+            re, im = _f64(e.real), _f64(e.imag)
+            rc = lib.cmx_batch_set_drive(self.h, re.ctypes.data, im.ctypes.data, e.size,
+                                         float(t0), float(sigma))
+        self._check(rc, "batch_set_drive")
 
     def close(self):
         if getattr(self, "h", None):

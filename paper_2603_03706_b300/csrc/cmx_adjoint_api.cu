@@ -68,7 +68,7 @@ __global__ void adj_restore_kernel(Ctl *ctl, const double *slot, int N, const do
         ctl->mm_n[q] = slot[4 * N + q];
     }
     for (int j = 0; j < 7; j++) ctl->kphys[j] = j;
-    ctl->t = 0.0;
+    ctl->t = slot[6 * N];   // the checkpoint's time (the drive depends on it)
     ctl->T = INFINITY;
     ctl->dt = dts[0];
     ctl->mcur = 0;
@@ -219,7 +219,7 @@ int cmx_adjoint_record(cmx_problem *h, int every, long long max_steps)
         }
         CU(dalloc(&s->traj_m, (size_t)slots * nq * nc));
         CU(dalloc(&s->traj_k, (size_t)slots * nq * nc));
-        CU(dalloc(&s->traj_a, (size_t)slots * 6 * N));
+        CU(dalloc(&s->traj_a, (size_t)slots * traj_stride(N)));
         s->every = every;
         s->slots = (int)slots;
     }
@@ -349,8 +349,8 @@ int cmx_adjoint(cmx_problem *h, const double *dL_da, const float *dL_dm, int dL_
                            cudaMemcpyDeviceToDevice, st));
         CU(cudaMemcpyAsync(s->rk[0], s->traj_k + (size_t)q * nq * nc, nq * nc * sizeof(float),
                            cudaMemcpyDeviceToDevice, st));
-        adj_restore_kernel<<<1, 32, 0, st>>>(s->rctl, s->traj_a + (size_t)q * 6 * std::max(1, N),
-                                             N, s->dts + first, len);
+        adj_restore_kernel<<<1, 32, 0, st>>>(s->rctl, s->traj_a + (size_t)q * traj_stride(N), N,
+                                             s->dts + first, len);
         CU(cudaGetLastError());
         fc.rec_steps = (int)len;
         cudaError_t e = launch_single(fc, h->bx, h->by, h->blocks, st);

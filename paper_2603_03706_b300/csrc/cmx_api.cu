@@ -745,6 +745,27 @@ int cmx_debug_skip_arrival(cmx_problem *h, int block)
     return CMX_OK;
 }
 
+int cmx_set_drive(cmx_problem *h, const double *eta_re, const double *eta_im, double t0,
+                  double sigma)
+{
+    if (!h) return CMX_EINVAL;
+    Ctx &c = h->base;
+    if (!eta_re) {
+        c.has_drive = 0;
+        return CMX_OK;
+    }
+    if (!eta_im || !(sigma > 0) || !std::isfinite(t0))
+        return fail(h, CMX_EINVAL, "drive: eta_im, sigma > 0 and a finite t0 are needed");
+    for (int n = 0; n < MAXN; n++) {
+        c.drive_re[n] = n < h->N ? eta_re[n] : 0.0;
+        c.drive_im[n] = n < h->N ? eta_im[n] : 0.0;
+    }
+    c.drive_t0 = t0;
+    c.drive_inv_sigma = 1.0 / sigma;
+    c.has_drive = h->N > 0;
+    return CMX_OK;
+}
+
 int cmx_autotune(cmx_problem *h, int attempts, cmx_tiling *chosen, double *us_per_attempt)
 {
     if (!h || attempts <= 0) return fail(h, CMX_EINVAL, "bad argument");

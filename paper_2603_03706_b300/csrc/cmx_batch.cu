@@ -108,6 +108,26 @@ int batch_blocks_per_sm(int nsub, int bx, int by)
     return 0;
 }
 
+__global__ void batch_drive_kernel(Ctx *ctx, int n, DriveArgs d)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        Ctx &c = ctx[i];
+        for (int q = 0; q < MAXN; q++) {
+            c.drive_re[q] = q < c.nmodes ? d.re[q] : 0.0;
+            c.drive_im[q] = q < c.nmodes ? d.im[q] : 0.0;
+        }
+        c.drive_t0 = d.t0;
+        c.drive_inv_sigma = d.inv_sigma;
+        c.has_drive = d.on && c.nmodes > 0;
+    }
+}
+
+cudaError_t launch_batch_drive(Ctx *ctx, int n, const DriveArgs &d, cudaStream_t s)
+{
+    batch_drive_kernel<<<(n + 127) / 128, 128, 0, s>>>(ctx, n, d);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_batch_prep(Ctl *const *ctls, int n, long long max_attempts, cudaStream_t s)
 {
     batch_prep_kernel<<<(n + 255) / 256, 256, 0, s>>>(ctls, n, max_attempts);

@@ -515,6 +515,26 @@ int cmx_batch_run(cmx_batch *b, long long max_attempts, cmx_stats *total)
     return first_err;
 }
 
+int cmx_batch_set_drive(cmx_batch *b, const double *eta_re, const double *eta_im, int n_eta,
+                        double t0, double sigma)
+{
+    if (!b) return CMX_EINVAL;
+    if (eta_re && (!eta_im || n_eta < 0 || n_eta > MAXN || !(sigma > 0) || !std::isfinite(t0)))
+        return bfail(b, CMX_EINVAL,
+                      "drive: eta_im, 0 <= n_eta <= %d, sigma > 0 and a finite t0 are needed", MAXN);
+    DriveArgs d{};
+    d.on = eta_re ? 1 : 0;
+    for (int q = 0; q < n_eta && eta_re; q++) {
+        d.re[q] = eta_re[q];
+        d.im[q] = eta_im[q];
+    }
+    d.t0 = t0;
+    d.inv_sigma = eta_re ? 1.0 / sigma : 0.0;
+    BCU(launch_batch_drive(b->ctx, b->n, d, b->stream));
+    BCU(cudaStreamSynchronize(b->stream));
+    return CMX_OK;
+}
+
 int cmx_batch_autotune(const cmx_instance *inst, int n, const cmx_solver *solver, int sample,
                        int attempts, void *stream, cmx_batch_config *cfg, double *us,
                        int *ncand)

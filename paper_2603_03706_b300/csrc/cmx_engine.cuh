@@ -159,6 +159,20 @@ __device__ void controller(const Ctx &c, const Team &tm, Local &L, const double 
         double dr, di;
         cavity_rhs(L.mc, tid, L.as[2 * tid], L.as[2 * tid + 1], L.mm[2 * tid],
                    L.mm[2 * tid + 1], dr, di);
+        if (c.has_drive) {   // the drive at this stage's time t + c_S h
+            const double ts = S == 1 ? L.t : L.t + dp_c(S - 1) * L.h;
+            const double x = (ts - c.drive_t0) * c.drive_inv_sigma;
+            const double env = exp(-0.5 * x * x);
+            double er = c.drive_re[0], ei = c.drive_im[0];
+#pragma unroll
+            for (int u = 1; u < MAXN; u++)
+                if (tid == u) {
+                    er = c.drive_re[u];
+                    ei = c.drive_im[u];
+                }
+            dr += er * env;
+            di += ei * env;
+        }
         L.ka[S - 1][2 * tid] = dr;
         L.ka[S - 1][2 * tid + 1] = di;
         if (S == 7) {
@@ -183,12 +197,13 @@ __device__ void controller(const Ctx &c, const Team &tm, Local &L, const double 
         // adjoint stores: a rejected attempt's checkpoint is overwritten by the accepted retry
         const int slot = checkpoint_slot<S>(c, L);
         if (slot >= 0 && c.traj_a) {
-            double *d = c.traj_a + (size_t)slot * 6 * N;
+            double *d = c.traj_a + (size_t)slot * traj_stride(N);
             for (int q = 0; q < 2 * N; q++) {
                 d[q] = S == 7 ? L.as[q] : L.a[q];
                 d[2 * N + q] = L.ka[S - 1][q];
                 d[4 * N + q] = L.mm[q];
             }
+            d[6 * N] = S == 7 ? (L.last ? L.T : L.t + L.h) : L.t;
         }
         if (c.rec_a && L.replay && L.replay_pos < c.rec_steps) {
             double *d = c.rec_a + ((size_t)L.replay_pos * 7 + (S - 1)) * 4 * N;

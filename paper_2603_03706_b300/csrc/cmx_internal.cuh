@@ -34,6 +34,18 @@ __host__ __device__ constexpr double dp_a(int s, int j)
     return A[s][j];
 }
 
+// Node c_s of stage s+1: the row sum of its couplings (the stage's time is t + c_s h).
+__host__ __device__ constexpr double dp_c(int s)
+{
+    return dp_a(s, 0) + dp_a(s, 1) + dp_a(s, 2) + dp_a(s, 3) + dp_a(s, 4) + dp_a(s, 5);
+}
+
+// Doubles per checkpoint slot of the adjoint store: a, k1^a, <m^-> (2N each) and the time.
+__host__ __device__ constexpr int traj_stride(int nmodes)
+{
+    return 6 * nmodes + 2;
+}
+
 __host__ __device__ constexpr double dp_e(int j)
 {
     constexpr double E[7] = {71.0 / 57600, 0, -71.0 / 16695, 71.0 / 1920,
@@ -104,6 +116,11 @@ struct Ctx {
     double omega[MAXN], kappa[MAXN], gre[MAXN], gim[MAXN];
     double two_over_gamma, inv_nmag;
     double red_scale;                // fixed-point scale of the overlap sums (a power of two)
+    // external drive eta_n(t) = drive_n exp(-(t - drive_t0)^2 / (2 sigma^2)) on da_n/dt
+    // (Eq. (1), (12)); has_drive = 0: none
+    double drive_re[MAXN], drive_im[MAXN];
+    double drive_t0, drive_inv_sigma;
+    int has_drive;
     // solver
     double rtol, a_ref, dt_min, dt_max, sample_dt;
     Ctl *ctl;
@@ -120,7 +137,7 @@ struct Ctx {
     // k * traj_every accepted steps counted from traj_base (slot 0: the initial state):
     // m (renormalised) and the FSAL slope k1, and a, k1^a and <m^-> at the slope's point.
     float *traj_m, *traj_k;          // [slot][nsub*3][ncell]
-    double *traj_a;                  // [slot][3][2N]
+    double *traj_a;                  // [slot][traj_stride(N)]: a, k1^a, <m^->, t
     long long traj_base;
     int traj_every, traj_slots;
     // Stage record of a replay (NULL = off): replay step j stores its stage points

@@ -24,6 +24,13 @@ cudaError_t launch_batch(const BatchArgs &b, int nsub, int bx, int by, int block
 int batch_blocks_per_sm(int nsub, int bx, int by);
 cudaError_t launch_batch_prep(Ctl *const *ctls, int n, long long max_attempts, cudaStream_t s);
 cudaError_t launch_batch_pending(Ctl *const *ctls, int n, int *pending, cudaStream_t s);
+// the external drive written into every instance's context (first nmodes amplitudes each)
+struct DriveArgs {
+    double re[MAXN], im[MAXN];
+    double t0, inv_sigma;
+    int on;
+};
+cudaError_t launch_batch_drive(Ctx *ctx, int n, const DriveArgs &d, cudaStream_t s);
 
 // reverse sweep of the adjoint (cmx_adjoint.cu)
 // Scalar adjoint state in device memory, carried from one checkpoint interval to the previous.
