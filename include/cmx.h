@@ -301,6 +301,15 @@ int cmx_batch_autotune(const cmx_instance *inst, int n, const cmx_solver *solver
 int cmx_batch_set_drive(cmx_batch *b, const double *eta_re, const double *eta_im, int n_eta,
                         double t0, double sigma);
 
+/* Spectral map of the field sweep (the paper's spectra, Sec. IV A): for every instance,
+ * P_i(f) = |sum_k w_k a_mode(t_k) e^{+2 pi i f t_k}|^2 over its uniform trace samples with
+ * t_k >= t_start (Hann window w over those samples; the trace needs trace_cap > 0 and
+ * sample_dt > 0), at f = f0 + j df, j < nf [Hz].  out: host, n x nf doubles (row of an
+ * instance without mode `mode`: zeros).  Computed on the device from the device-resident
+ * traces. */
+int cmx_batch_spectrum(cmx_batch *b, int mode, double f0, double df, int nf, double t_start,
+                       double *out);
+
 /* Enqueue ONE launch in which every unfinished instance makes up to n_attempts attempts. */
 int cmx_batch_launch(cmx_batch *b, int n_attempts);
 

@@ -130,6 +130,8 @@ SIGNATURES = {
     "cmx_batch_last_error": (C.c_char_p, [_P]),
     "cmx_autotune": (C.c_int, [_P, C.c_int, C.c_void_p, C.c_void_p]),
     "cmx_set_drive": (C.c_int, [_P, C.c_void_p, C.c_void_p, C.c_double, C.c_double]),
+    "cmx_batch_spectrum": (C.c_int, [_P, C.c_int, C.c_double, C.c_double, C.c_int, C.c_double,
+                                     C.c_void_p]),
     "cmx_batch_set_drive": (C.c_int, [_P, C.c_void_p, C.c_void_p, C.c_int, C.c_double,
                                       C.c_double]),
     "cmx_adjoint_record": (C.c_int, [_P, C.c_int, C.c_longlong]),
@@ -584,6 +586,14 @@ class BatchSimulation:
         self.n = n
         if getattr(p0, "drive", None) is not None:
             self.set_drive(p0.drive, p0.drive_t0, p0.drive_sigma)
+
+    def spectrum(self, mode: int, f0: float, df: float, nf: int, t_start: float = 0.0):
+        """cmx_batch_spectrum: |windowed DFT|^2 of every instance's trace of a_mode at
+        f0 + j df (Hz); returns an (n, nf) array."""
+        out = np.zeros(self.n * int(nf))
+        self._check(load().cmx_batch_spectrum(self.h, int(mode), float(f0), float(df), int(nf),
+                                              float(t_start), out.ctypes.data), "batch_spectrum")
+        return out.reshape(self.n, int(nf))
 
     def set_drive(self, eta=None, t0: float = 0.1e-9, sigma: float = 20e-12):
         """cmx_batch_set_drive: the same Gaussian drive for every instance (eta: amplitudes

@@ -515,6 +515,45 @@ int cmx_batch_run(cmx_batch *b, long long max_attempts, cmx_stats *total)
     return first_err;
 }
 
+int cmx_batch_spectrum(cmx_batch *b, int mode, double f0, double df, int nf, double t_start,
+                       double *out)
+{
+    if (!b || !out || mode < 0 || mode >= MAXN || nf <= 0 || !(df > 0))
+        return bfail(b, CMX_EINVAL, "bad argument");
+    if (b->sv.trace_cap <= 0 || !(b->sv.sample_dt > 0))
+        return bfail(b, CMX_EINVAL, "the spectral map needs traces (trace_cap, sample_dt)");
+    const int tc = std::max(1, b->sv.trace_cap);
+    std::vector<SpecInst> hs(b->n);
+    for (int i = 0; i < b->n; i++) {
+        const Inst &I = b->inst[i];
+        const int Q = 2 * std::max(1, I.N);
+        hs[i].t = b->trd + I.o_tr;
+        hs[i].a = b->trd + I.o_tr + tc;
+        hs[i].ctl = b->ctls + i;
+        hs[i].q = Q;
+        hs[i].cap = tc;
+        hs[i].re = mode < I.N ? 2 * mode : -1;
+    }
+    SpecInst *ds = nullptr;
+    double *dout = nullptr;
+    BCU(balloc(&ds, (size_t)b->n));
+    if (balloc(&dout, (size_t)b->n * nf) != cudaSuccess) {
+        cudaFree(ds);
+        return bfail(b, CMX_ENOMEM, "spectrum buffer");
+    }
+    cudaError_t e = cudaMemcpyAsync(ds, hs.data(), b->n * sizeof(SpecInst),
+                                    cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess) e = launch_batch_spectrum(ds, b->n, f0, df, nf, t_start, dout, b->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(out, dout, (size_t)b->n * nf * sizeof(double), cudaMemcpyDeviceToHost,
+                            b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    cudaFree(ds);
+    cudaFree(dout);
+    if (e != cudaSuccess) return bfail(b, CMX_ECUDA, "spectrum: %s", cudaGetErrorString(e));
+    return CMX_OK;
+}
+
 int cmx_batch_set_drive(cmx_batch *b, const double *eta_re, const double *eta_im, int n_eta,
                         double t0, double sigma)
 {

@@ -31,6 +31,15 @@ struct DriveArgs {
     int on;
 };
 cudaError_t launch_batch_drive(Ctx *ctx, int n, const DriveArgs &d, cudaStream_t s);
+// spectral map of the instances' uniform traces (one windowed DFT per instance)
+struct SpecInst {
+    const double *t, *a;     // trace times and packed amplitudes [k][q]
+    const Ctl *ctl;          // trace_n
+    int q, cap;              // amplitude stride (2 max(N, 1)), trace capacity
+    int re;                  // column of Re a_mode, or -1 (the instance has no such mode)
+};
+cudaError_t launch_batch_spectrum(const SpecInst *si, int n, double f0, double df, int nf,
+                                  double t_start, double *out, cudaStream_t s);
 
 // reverse sweep of the adjoint (cmx_adjoint.cu)
 // Scalar adjoint state in device memory, carried from one checkpoint interval to the previous.

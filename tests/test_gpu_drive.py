@@ -85,3 +85,64 @@ def test_driven_batch_matches_oracle():
         assert amax > 1e-5
         assert np.abs(b.get_a(i) - st["a"]).max() <= TOL_A * amax
     b.close()
+
+
+def pulsed_sweep(fm_list, T, g=TP * 50e6):
+    """8^3 spheres, one cavity at 5 GHz pulsed at t0 = 0.1 ns, magnon frequency fm."""
+    n = 8
+    out = []
+    for fm in fm_list:
+        p = W.make_problem(n, n, n, 5e-9, W.sphere_mask(n, n, n), alpha=1e-4,
+                           B0=(0, 0, TP * fm / W.GAMMA), Nd=(1 / 3, 1 / 3, 1 / 3),
+                           omega=[TP * 5e9], kappa=[TP * 0.5e6], g_re=[g], g_im=[0.0],
+                           m0=W.tilted_state(1, n, n, n, 0.0, 0.0), a0=np.zeros(1, complex),
+                           T=T)
+        out.append(p.replace(drive=np.array([2e8 + 0j])))
+    return out
+
+
+def hann_dft(t, y, f, t_start=0.0):
+    keep = t >= t_start
+    t, y = t[keep], y[keep]
+    K = len(t)
+    w = 0.5 - 0.5 * np.cos(2 * np.pi * np.arange(K) / (K - 1))
+    return np.abs(np.exp(2j * np.pi * np.outer(f, t)) @ (w * y)) ** 2
+
+
+def test_spectral_map_is_the_windowed_dft_of_the_trace():
+    probs = pulsed_sweep([4.9e9, 5.0e9, 5.15e9], T=10e-9)
+    b = cmx.BatchSimulation(probs, trace_cap=2000, sample_dt=10e-12)
+    b.run()
+    f = 4.7e9 + 2e6 * np.arange(300)
+    P = b.spectrum(0, f[0], 2e6, len(f), t_start=0.2e-9)
+    for i in range(len(probs)):
+        tr = b.get_trace(i)
+        want = hann_dft(tr["t"], tr["a"][:, 0], f, t_start=0.2e-9)
+        assert np.abs(P[i] - want).max() <= 1e-9 * want.max(), i
+    b.close()
+
+
+def test_pulsed_field_sweep_spectral_peaks_follow_the_anticrossing():
+    """The paper's spectroscopy (Sec. IV A): pulse the cavity, map the spectrum across the field
+    sweep; the two strongest peaks sit on the branches of Eq. (6)."""
+    from paper_2603_03706_b300 import spectra
+    fms = [4.85e9, 4.95e9, 5.0e9, 5.05e9, 5.15e9]
+    probs = pulsed_sweep(fms, T=100e-9)
+    b = cmx.BatchSimulation(probs, trace_cap=6000, sample_dt=20e-12)
+    b.run()
+    df = 0.25e6
+    f = 4.7e9 + df * np.arange(2400)
+    P = b.spectrum(0, f[0], df, len(f), t_start=0.3e-9)
+    b.close()
+    for i, fm in enumerate(fms):
+        s = P[i]
+        peaks = [j for j in range(1, len(s) - 1) if s[j] >= s[j - 1] and s[j] > s[j + 1]]
+        top = sorted(peaks, key=lambda j: -s[j])[:2]
+        # parabolic refinement of each peak on the log power
+        fp = []
+        for j in top:
+            l, c, r = np.log(s[j - 1]), np.log(s[j]), np.log(s[j + 1])
+            fp.append(f[j] + 0.5 * df * (l - r) / (l - 2 * c + r))
+        wp, wm = spectra.polariton_branches(TP * 5e9, TP * fm, TP * 50e6)
+        want = sorted([wp.real / TP, wm.real / TP])
+        assert np.abs(np.sort(fp) - want).max() <= 2e6, (fm, sorted(fp), want)
