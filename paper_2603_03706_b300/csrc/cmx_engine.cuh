@@ -5,10 +5,11 @@
 // Every Dormand-Prince attempt runs inside one persistent launch with a barrier after each stage:
 // the cavity slope of a stage needs the overlap reduction over all cells (Eq. (18)).  The
 // barrier is a monotonic arrival counter of the team (one release-atomic per block, acquire
-// polling).  After it every block of the team reads all per-block partials and reduces them in
-// the same fixed order, then runs the same FP64 cavity update and step-size controller on its
-// own shared-memory copy of the integrator state: identical inputs and identical code give every
-// block the same decision, deterministic from run to run.  The team's block 0 records the step
+// polling).  Before arriving, every block adds its overlap sums into the team's accumulators as
+// fixed-point integers (exact, so the totals do not depend on the order of arrival); after it
+// every block reads the same totals and runs the same FP64 cavity update and step-size
+// controller on its own shared-memory copy of the integrator state: identical inputs and
+// identical code give every block the same decision, deterministic from run to run.  The team's block 0 records the step
 // log and the trace and writes the state back.  No step returns to the host (Sec. III A).
 #pragma once
 
@@ -392,11 +393,11 @@ __device__ void grid_reduce(const Ctx &c, const Team &tm, SM &sm, double *out, f
     __syncthreads();
 }
 
-// Team barrier: every block of the team adds 1 to a monotonic arrival counter with release semantics and
-// polls it with acquire loads until all blocks of this barrier have arrived.  Waits are bounded
-// by c.timeout_ns: on time-out the block sets CMX_ETIMEOUT and the run stops.  The block's
-// partials were written before the __syncthreads that precedes the release-add.  Returns false
-// if the run must stop.
+// Team barrier: every block of the team adds 1 to a monotonic arrival counter with release
+// semantics and polls it with acquire loads until all blocks of this barrier have arrived.
+// Waits are bounded by c.timeout_ns: on time-out the block sets CMX_ETIMEOUT and the run stops.
+// The block's accumulator additions were issued before the __syncthreads that precedes the
+// release-add.  Returns false if the run must stop.
 template <class SM>
 __device__ bool grid_barrier(const Ctx &c, const Team &tm, Local &L, int where)
 {

@@ -4,7 +4,7 @@
 // CUDA graph, plug-ins inside a host program that owns the device allocator, or processes under
 // a fixed device-memory budget.  This entry point evaluates f(m, a) with the same stage kernel
 // as cmx_eval_rhs but takes every scratch buffer (compact layout tables, compact m and slope,
-// control block, block partials) from one file-scope device array of CMX_NOALLOC_SCRATCH_BYTES.
+// control block) from one file-scope device array of CMX_NOALLOC_SCRATCH_BYTES.
 // That array exists on every device that loads the library, from load until process exit.
 #include <algorithm>
 #include <cstring>
