@@ -19,6 +19,8 @@
  *   time stepping    Dormand-Prince 5(4), FSAL; the paper only says "adaptive RK45" (Sec. III A).
  *   drive            optional eta_n(t) added to da_n/dt (Eq. (1), (12)), a Gaussian pulse
  *                    (Sec. IV A), evaluated at each stage's time t + c_s h.
+ *   extensions       optional backward coupling gb~_n of the feedback field (nonreciprocal
+ *                    coupling, Sec. II: h0 = 2 g_b / gamma) and self-Kerr -i K_n |a_n|^2 a_n.
  *   adjoint          orc_rhs_vjp / orc_adjoint: reverse-mode derivative of the replayed steps
  *                    (not in the paper; the gradient form added beside the integrator).
  *
@@ -58,6 +60,11 @@ typedef struct {
        added to da_n/dt (Eq. (1), (12)); drive_re == NULL: no drive */
     const double *drive_re, *drive_im;
     double drive_t0, drive_sigma;
+    /* nonreciprocal coupling: backward (cavity-to-magnon) coefficients of the feedback field,
+       B_rf,x = sum_n u_n (2/gamma) Re[gb~_n a_n] (Sec. II, h0 = 2 g_b / gamma); NULL: gb~ = g~ */
+    const double *gb_re, *gb_im;
+    /* self-Kerr term -i K_n |a_n|^2 a_n of the cavity equation; NULL: none */
+    const double *kerr;
 } orc_problem;
 
 typedef struct {
@@ -127,6 +134,10 @@ static long count_cells(const orc_problem *P)
     return n;
 }
 
+/* Backward (feedback) coupling of mode n: gb~ if given, else the forward g~. */
+static double gback_re(const orc_problem *P, int n) { return P->gb_re ? P->gb_re[n] : P->g_re[n]; }
+static double gback_im(const orc_problem *P, int n) { return P->gb_im ? P->gb_im[n] : P->g_im[n]; }
+
 static double profile(const orc_problem *P, int n, long cell)
 {
     return P->u ? P->u[(long)n * P->nx * P->ny * P->nz + cell] : 1.0;
@@ -179,7 +190,7 @@ int orc_rhs(const orc_problem *P, const double *m, const double *a, double *dm, 
     double hrf[64];
     if (N > 64 || ns < 1 || ns > 2) return ORC_EINVAL;
     for (int n = 0; n < N; n++) {
-        double re_ga = P->g_re[n] * a[2 * n] - P->g_im[n] * a[2 * n + 1];
+        double re_ga = gback_re(P, n) * a[2 * n] - gback_im(P, n) * a[2 * n + 1];
         hrf[n] = 2.0 / P->gamma * re_ga;
     }
 
@@ -246,6 +257,12 @@ int orc_rhs(const orc_problem *P, const double *m, const double *a, double *dm, 
         double pr = gr * mr - gi * mi, pi = gr * mi + gi * mr; /* g~ <m^-> */
         r += -pi;
         i += pr;
+        /* self-Kerr -i K |a|^2 a */
+        if (P->kerr) {
+            const double k2 = P->kerr[n] * (ar * ar + ai * ai);
+            r += k2 * ai;
+            i -= k2 * ar;
+        }
         da[2 * n] = r;
         da[2 * n + 1] = i;
     }
@@ -525,6 +542,8 @@ typedef struct {
     double *g_re, *g_im, *kappa, *omega; /* nmodes each: dL/d Re g~_n, dL/d Im g~_n, ... */
     double *alpha;                       /* 1 */
     double *u;                           /* nmodes * nbox (only with profiles) */
+    double *gb_re, *gb_im;               /* nmodes each, with nonreciprocal coupling */
+    double *kerr;                        /* nmodes, with a Kerr term */
 } orc_grads;
 
 /*
@@ -550,7 +569,7 @@ int orc_rhs_vjp(const orc_problem *P, const double *m, const double *a, const do
     const int want_u = P->u && G && G->u;
     double hrf[64], hbar[64], mm[128];
     for (int n = 0; n < N; n++) {
-        hrf[n] = 2.0 / P->gamma * (P->g_re[n] * a[2 * n] - P->g_im[n] * a[2 * n + 1]);
+        hrf[n] = 2.0 / P->gamma * (gback_re(P, n) * a[2 * n] - gback_im(P, n) * a[2 * n + 1]);
         hbar[n] = 0.0;
     }
     orc_overlap(P, m, mm);
@@ -664,13 +683,16 @@ int orc_rhs_vjp(const orc_problem *P, const double *m, const double *a, const do
     free(Bb);
     if (G && G->alpha) *G->alpha += galpha;
 
-    /* hrf_n = (2/gamma) (Re g~ Re a - Im g~ Im a) */
+    /* hrf_n = (2/gamma) (Re gb~ Re a - Im gb~ Im a); with reciprocal coupling gb~ is g~ and its
+       gradient goes to g~, otherwise to gb~ */
     for (int n = 0; n < N; n++) {
         const double c2 = 2.0 / P->gamma * hbar[n];
-        ga[2 * n] += c2 * P->g_re[n];
-        ga[2 * n + 1] -= c2 * P->g_im[n];
-        if (G && G->g_re) G->g_re[n] += c2 * a[2 * n];
-        if (G && G->g_im) G->g_im[n] -= c2 * a[2 * n + 1];
+        ga[2 * n] += c2 * gback_re(P, n);
+        ga[2 * n + 1] -= c2 * gback_im(P, n);
+        double *dre = P->gb_re ? (G ? G->gb_re : NULL) : (G ? G->g_re : NULL);
+        double *dim = P->gb_re ? (G ? G->gb_im : NULL) : (G ? G->g_im : NULL);
+        if (dre) dre[n] += c2 * a[2 * n];
+        if (dim) dim[n] -= c2 * a[2 * n + 1];
     }
 
     /* cavity slopes: da_re = -k ar + w ai - (gr mi + gi mr), da_im = -k ai - w ar + (gr mr - gi mi) */
@@ -681,6 +703,12 @@ int orc_rhs_vjp(const orc_problem *P, const double *m, const double *a, const do
         const double gr = P->g_re[n], gi = P->g_im[n], mr = mm[2 * n], mi = mm[2 * n + 1];
         ga[2 * n] += -P->kappa[n] * wr - P->omega[n] * wi;
         ga[2 * n + 1] += P->omega[n] * wr - P->kappa[n] * wi;
+        if (P->kerr) {   /* -i K |a|^2 a: (K|a|^2 ai, -K|a|^2 ar) */
+            const double K = P->kerr[n], s2 = ar * ar + ai * ai;
+            ga[2 * n] += wr * 2.0 * K * ar * ai - wi * K * (3.0 * ar * ar + ai * ai);
+            ga[2 * n + 1] += wr * K * (ar * ar + 3.0 * ai * ai) - wi * 2.0 * K * ar * ai;
+            if (G && G->kerr) G->kerr[n] += s2 * (wr * ai - wi * ar);
+        }
         if (G && G->g_re) G->g_re[n] += -mi * wr + mr * wi;
         if (G && G->g_im) G->g_im[n] += -mr * wr - mi * wi;
         if (G && G->kappa) G->kappa[n] += -ar * wr - ai * wi;

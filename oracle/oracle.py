@@ -53,7 +53,9 @@ class _Problem(C.Structure):
                 ("omega", C.POINTER(C.c_double)), ("kappa", C.POINTER(C.c_double)),
                 ("g_re", C.POINTER(C.c_double)), ("g_im", C.POINTER(C.c_double)),
                 ("drive_re", C.POINTER(C.c_double)), ("drive_im", C.POINTER(C.c_double)),
-                ("drive_t0", C.c_double), ("drive_sigma", C.c_double)]
+                ("drive_t0", C.c_double), ("drive_sigma", C.c_double),
+                ("gb_re", C.POINTER(C.c_double)), ("gb_im", C.POINTER(C.c_double)),
+                ("kerr", C.POINTER(C.c_double))]
 
 
 class _Solver(C.Structure):
@@ -71,7 +73,9 @@ class _Log(C.Structure):
 class _Grads(C.Structure):
     _fields_ = [("g_re", C.POINTER(C.c_double)), ("g_im", C.POINTER(C.c_double)),
                 ("kappa", C.POINTER(C.c_double)), ("omega", C.POINTER(C.c_double)),
-                ("alpha", C.POINTER(C.c_double)), ("u", C.POINTER(C.c_double))]
+                ("alpha", C.POINTER(C.c_double)), ("u", C.POINTER(C.c_double)),
+                ("gb_re", C.POINTER(C.c_double)), ("gb_im", C.POINTER(C.c_double)),
+                ("kerr", C.POINTER(C.c_double))]
 
 
 _lib = None
@@ -146,6 +150,20 @@ class OracleProblem:
         else:
             s.drive_re = s.drive_im = C.POINTER(C.c_double)()
             s.drive_t0, s.drive_sigma = 0.0, 1.0
+        gb = getattr(p, "g_back", None)
+        if gb is not None:
+            g = np.asarray(gb, complex).reshape(-1)
+            self.gb_re = np.ascontiguousarray(g.real, np.float64)
+            self.gb_im = np.ascontiguousarray(g.imag, np.float64)
+            s.gb_re, s.gb_im = _dptr(self.gb_re), _dptr(self.gb_im)
+        else:
+            s.gb_re = s.gb_im = C.POINTER(C.c_double)()
+        kerr = getattr(p, "kerr", None)
+        if kerr is not None:
+            self.kerr = np.ascontiguousarray(np.asarray(kerr, np.float64).reshape(-1))
+            s.kerr = _dptr(self.kerr)
+        else:
+            s.kerr = C.POINTER(C.c_double)()
         self.s = s
         self.solver = _Solver(p.rtol, p.a_ref, p.dt_min, p.dt_max)
 
@@ -332,6 +350,9 @@ class Grads:
         s.kappa, s.omega = _dptr(self.kappa), _dptr(self.omega)
         s.alpha = _dptr(self.alpha)
         s.u = _dptr(self.u) if self.u is not None else C.POINTER(C.c_double)()
+        self.gb_re, self.gb_im, self.kerr = np.zeros(N), np.zeros(N), np.zeros(N)
+        s.gb_re, s.gb_im = _dptr(self.gb_re), _dptr(self.gb_im)
+        s.kerr = _dptr(self.kerr)
         self.s = s
         self.N = op.N
 
@@ -341,6 +362,8 @@ class Grads:
                  kappa=self.kappa[:N].copy(), omega=self.omega[:N].copy(),
                  alpha=float(self.alpha[0]))
         d["u"] = None if self.u is None else self.u[:N].copy()
+        d["gb_re"], d["gb_im"] = self.gb_re[:N].copy(), self.gb_im[:N].copy()
+        d["kerr"] = self.kerr[:N].copy()
         return d
 
 

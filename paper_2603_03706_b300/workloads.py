@@ -72,6 +72,10 @@ class Problem:
     drive: Optional[np.ndarray] = None   # (N,) complex amplitudes [1/s], or None
     drive_t0: float = 0.1e-9
     drive_sigma: float = 20e-12
+    # nonreciprocal coupling: backward (cavity-to-magnon) coefficients of the feedback field,
+    # None = reciprocal (the forward g~); self-Kerr coefficients K_n [rad/s per |a|^2] or None
+    g_back: Optional[np.ndarray] = None
+    kerr: Optional[np.ndarray] = None
 
     @property
     def nmodes(self) -> int:
