@@ -200,6 +200,15 @@ int cmx_debug_skip_arrival(cmx_problem *h, int block);
 int cmx_set_drive(cmx_problem *h, const double *eta_re, const double *eta_im, double t0,
                   double sigma);
 
+/* Nonreciprocal coupling (Sec. II: separate forward and backward coefficients, h0 = 2 g_b /
+ * gamma): the feedback field uses B_rf,x = sum_n u_n (2/gamma) Re[gb~_n a_n] with the backward
+ * coefficients gb~ given here (host, n_modes each), while the cavity equation keeps the forward
+ * g~ of cmx_modes.  gb_re == NULL restores reciprocal coupling. */
+int cmx_set_backward_coupling(cmx_problem *h, const double *gb_re, const double *gb_im);
+
+/* Self-Kerr cavity term -i K_n |a_n|^2 a_n [rad/s per |a|^2] (host, n_modes; NULL: none). */
+int cmx_set_kerr(cmx_problem *h, const double *kerr);
+
 /* Autotuner: time `attempts` Dormand-Prince attempts (after a one-attempt warm-up) from the
  * current state with each compiled one-cell window (32x8, 32x16, 64x4; blocks_per_sm and bz of
  * the current tiling), restore the state after each trial (m, FSAL slope, control block; the
@@ -364,6 +373,9 @@ typedef struct {
     int m0_on_device;      /* m0 is a device pointer */
     double *u;             /* dense N*nbox: dL/d u_n(r); needs mode profiles; 0 outside */
     int u_on_device;       /* u is a device pointer */
+    double *gb_re, *gb_im; /* host, n_modes each: dL/d of the backward coupling (zero unless set
+                              by cmx_set_backward_coupling; otherwise in g_re, g_im) */
+    double *kerr;          /* host, n_modes: dL/d K_n */
 } cmx_grads;
 
 /* Arm the checkpoint store for the next run: call after cmx_set_state and before any launch.

@@ -77,7 +77,8 @@ class Grads(C.Structure):
     _fields_ = [("g_re", C.c_void_p), ("g_im", C.c_void_p), ("kappa", C.c_void_p),
                 ("omega", C.c_void_p), ("alpha", C.c_void_p), ("a0", C.c_void_p),
                 ("m0", C.c_void_p), ("m0_on_device", C.c_int), ("u", C.c_void_p),
-                ("u_on_device", C.c_int)]
+                ("u_on_device", C.c_int), ("gb_re", C.c_void_p), ("gb_im", C.c_void_p),
+                ("kerr", C.c_void_p)]
 
 
 class Step(C.Structure):
@@ -129,6 +130,8 @@ SIGNATURES = {
                                  C.POINTER(C.c_longlong), C.POINTER(C.c_int)]),
     "cmx_batch_last_error": (C.c_char_p, [_P]),
     "cmx_autotune": (C.c_int, [_P, C.c_int, C.c_void_p, C.c_void_p]),
+    "cmx_set_backward_coupling": (C.c_int, [_P, C.c_void_p, C.c_void_p]),
+    "cmx_set_kerr": (C.c_int, [_P, C.c_void_p]),
     "cmx_set_drive": (C.c_int, [_P, C.c_void_p, C.c_void_p, C.c_double, C.c_double]),
     "cmx_batch_spectrum": (C.c_int, [_P, C.c_int, C.c_double, C.c_double, C.c_int, C.c_double,
                                      C.c_void_p]),
@@ -254,6 +257,10 @@ class Simulation:
         sim.set_state(p.m0, p.a0, 0.0)
         if getattr(p, "drive", None) is not None:
             sim.set_drive(p.drive, p.drive_t0, p.drive_sigma)
+        if getattr(p, "g_back", None) is not None:
+            sim.set_backward_coupling(p.g_back)
+        if getattr(p, "kerr", None) is not None:
+            sim.set_kerr(p.kerr)
         return sim
 
     # -- lifetime ----------------------------------------------------------------------------
@@ -436,7 +443,8 @@ class Simulation:
         lm = None if dL_dm is None else _f32(dL_dm)
         if lm is not None and lm.size != 3 * self.nsub * self.nbox:
             raise ValueError("dL_dm size")
-        out = {k: np.zeros(max(N, 1)) for k in ("g_re", "g_im", "kappa", "omega")}
+        out = {k: np.zeros(max(N, 1))
+               for k in ("g_re", "g_im", "kappa", "omega", "gb_re", "gb_im", "kerr")}
         alpha = np.zeros(1)
         a0 = np.zeros(max(2 * N, 1))
         m0 = np.zeros(3 * self.nsub * self.nbox, np.float32) if want_m0 else None
@@ -444,7 +452,8 @@ class Simulation:
         g = Grads(out["g_re"].ctypes.data, out["g_im"].ctypes.data, out["kappa"].ctypes.data,
                   out["omega"].ctypes.data, alpha.ctypes.data, a0.ctypes.data,
                   m0.ctypes.data if m0 is not None else None, 0,
-                  u.ctypes.data if u is not None else None, 0)
+                  u.ctypes.data if u is not None else None, 0, out["gb_re"].ctypes.data,
+                  out["gb_im"].ctypes.data, out["kerr"].ctypes.data)
         self._check(load().cmx_adjoint(self.h, la.ctypes.data if la is not None else None,
                                        lm.ctypes.data if lm is not None else None, 0,
                                        C.byref(g)), "adjoint")
@@ -473,6 +482,29 @@ class Simulation:
 
     def debug_skip_arrival(self, block: int):
         self._check(load().cmx_debug_skip_arrival(self.h, int(block)), "debug_skip_arrival")
+
+    def set_backward_coupling(self, gb=None):
+        """cmx_set_backward_coupling: complex backward coefficients gb~_n of the feedback field
+        (nonreciprocal coupling); None restores reciprocal coupling."""
+        if gb is None:
+            self._check(load().cmx_set_backward_coupling(self.h, None, None), "backward_coupling")
+            return
+        g = np.asarray(gb, complex).reshape(-1)
+        if g.size != self.N:
+            raise ValueError("one backward coefficient per mode")
+        re, im = _f64(g.real), _f64(g.imag)
+        self._check(load().cmx_set_backward_coupling(self.h, re.ctypes.data, im.ctypes.data),
+                    "backward_coupling")
+
+    def set_kerr(self, kerr=None):
+        """cmx_set_kerr: self-Kerr coefficients K_n (None: no Kerr term)."""
+        if kerr is None:
+            self._check(load().cmx_set_kerr(self.h, None), "set_kerr")
+            return
+        k = _f64(kerr)
+        if k.size != self.N:
+            raise ValueError("one Kerr coefficient per mode")
+        self._check(load().cmx_set_kerr(self.h, k.ctypes.data), "set_kerr")
 
     def set_drive(self, eta=None, t0: float = 0.1e-9, sigma: float = 20e-12):
         """cmx_set_drive: Gaussian drive eta_n exp(-(t-t0)^2/(2 sigma^2)) on da_n/dt

@@ -44,8 +44,8 @@ struct RevLocal {
     double abar[2 * MAXN], k1a[2 * MAXN];
     double wa[2 * MAXN];         // cavity part of the slope adjoint w_S
     double as[2 * MAXN], mm[2 * MAXN];   // a_S and <m^->_S of the recorded forward
-    double mc[4 * MAXN];         // omega, kappa, Re g~, Im g~
-    double gacc[4 * MAXN];
+    double mc[MC * MAXN];        // mode constants (see MC)
+    double gacc[7 * MAXN];       // per mode: Re g~, Im g~, kappa, omega, Re gb~, Im gb~, K
     double galpha;
     double sums[MAXN + 1];
     double h;
@@ -444,14 +444,15 @@ __device__ bool rev_stage(const AdjArgs &A, RevSmem<NS, WX, WY> &sm, RevLocal &L
     }
     __syncthreads();
     if (tid < N) {
-        const double gr = L.mc[4 * tid + 2], gi = L.mc[4 * tid + 3];
+        const double *q = L.mc + MC * tid;
+        const double gr = q[2], gi = q[3], gbr = q[4], gbi = q[5];
         const double wr = L.wa[2 * tid], wi = L.wa[2 * tid + 1];
         // adjoint of <m^->_n from da/dt = ... + i g~ <m^->
         const double mbr = -gi * wr + gr * wi, mbi = -gr * wr - gi * wi;
         const double sc = c.inv_nmag / NS;
         L.ovr[tid] = (float)(sc * mbr);
         L.ovi[tid] = (float)(-sc * mbi);
-        L.hrf[tid] = (float)(c.two_over_gamma * (gr * L.as[2 * tid] - gi * L.as[2 * tid + 1]));
+        L.hrf[tid] = (float)(c.two_over_gamma * (gbr * L.as[2 * tid] - gbi * L.as[2 * tid + 1]));
     }
     __syncthreads();
     float acc[MAXN + 1];
@@ -464,23 +465,32 @@ __device__ bool rev_stage(const AdjArgs &A, RevSmem<NS, WX, WY> &sm, RevLocal &L
     if (tid < N) {
         const int n = tid;
         const double Sn = L.sums[n], tg = c.two_over_gamma;
-        const double w = L.mc[4 * n], k = L.mc[4 * n + 1], gr = L.mc[4 * n + 2],
-                     gi = L.mc[4 * n + 3];
+        const double *q = L.mc + MC * n;
+        const double w = q[0], k = q[1], gbr = q[4], gbi = q[5], K = q[6];
         const double wr = L.wa[2 * n], wi = L.wa[2 * n + 1];
         const double ar = L.as[2 * n], ai = L.as[2 * n + 1];
         const double mr = L.mm[2 * n], mi = L.mm[2 * n + 1];
-        double fr = -k * wr - w * wi + tg * gr * Sn;
-        double fi = w * wr - k * wi - tg * gi * Sn;
+        // feedback field adjoint through gb~ (the backward coupling), then the cavity equation
+        double fr = -k * wr - w * wi + tg * gbr * Sn;
+        double fi = w * wr - k * wi - tg * gbi * Sn;
+        // self-Kerr -i K |a|^2 a = (K |a|^2 ai, -K |a|^2 ar)
+        const double s2 = ar * ar + ai * ai;
+        fr += wr * 2.0 * K * ar * ai - wi * K * (3.0 * ar * ar + ai * ai);
+        fi += wr * K * (ar * ar + 3.0 * ai * ai) - wi * 2.0 * K * ar * ai;
         if (S == 7) {
             fr += L.abar[2 * n];
             fi += L.abar[2 * n + 1];
         }
         L.Fa[S - 1][2 * n] = fr;
         L.Fa[S - 1][2 * n + 1] = fi;
-        L.gacc[4 * n + 0] += -mi * wr + mr * wi + tg * ar * Sn;
-        L.gacc[4 * n + 1] += -mr * wr - mi * wi - tg * ai * Sn;
-        L.gacc[4 * n + 2] += -ar * wr - ai * wi;
-        L.gacc[4 * n + 3] += ai * wr - ar * wi;
+        const int fb = c.has_gb ? 4 : 0;   // feedback gradients: gb~ if separate, else g~
+        L.gacc[7 * n + 0] += -mi * wr + mr * wi;
+        L.gacc[7 * n + 1] += -mr * wr - mi * wi;
+        L.gacc[7 * n + fb] += tg * ar * Sn;
+        L.gacc[7 * n + fb + 1] -= tg * ai * Sn;
+        L.gacc[7 * n + 2] += -ar * wr - ai * wi;
+        L.gacc[7 * n + 3] += ai * wr - ar * wi;
+        L.gacc[7 * n + 6] += s2 * (wr * ai - wi * ar);
     }
     if (tid == 32) L.galpha += L.sums[N];
     __syncthreads();
@@ -519,22 +529,8 @@ __global__ void __launch_bounds__(WX *WY, NS == 1 ? 2 : 1) rev_kernel(AdjArgs A)
         L.abar[tid] = A.ctl->abar[tid];
         L.k1a[tid] = A.ctl->k1a[tid];
     }
-    if (tid < 4 * N) L.gacc[tid] = 0.0;
-    if (tid < N) {
-        double w = c.omega[0], ka = c.kappa[0], gr = c.gre[0], gi = c.gim[0];
-#pragma unroll
-        for (int u = 1; u < MAXN; u++)
-            if (tid == u) {
-                w = c.omega[u];
-                ka = c.kappa[u];
-                gr = c.gre[u];
-                gi = c.gim[u];
-            }
-        L.mc[4 * tid] = w;
-        L.mc[4 * tid + 1] = ka;
-        L.mc[4 * tid + 2] = gr;
-        L.mc[4 * tid + 3] = gi;
-    }
+    if (tid < 7 * N) L.gacc[tid] = 0.0;
+    if (tid < N) mode_constants(c, tid, L.mc + MC * tid);
     if (tid == 0) {
         L.galpha = 0.0;
         L.bar_target = 0;
@@ -566,7 +562,7 @@ __global__ void __launch_bounds__(WX *WY, NS == 1 ? 2 : 1) rev_kernel(AdjArgs A)
             A.ctl->abar[tid] = L.abar[tid];
             A.ctl->k1a[tid] = L.k1a[tid];
         }
-        if (tid < 4 * N) A.ctl->gacc[tid] += L.gacc[tid];
+        if (tid < 7 * N) A.ctl->gacc[tid] += L.gacc[tid];
         if (tid == 0) A.ctl->galpha += L.galpha;
     }
 }

@@ -381,10 +381,13 @@ int cmx_adjoint(cmx_problem *h, const double *dL_da, const float *dL_dm, int dL_
                     h->timeout_ns, ac.timeout_where);
     if (ac.status) return fail(h, ac.status, "reverse sweep status %d", ac.status);
     for (int k = 0; k < N; k++) {
-        if (g->g_re) g->g_re[k] = ac.gacc[4 * k + 0];
-        if (g->g_im) g->g_im[k] = ac.gacc[4 * k + 1];
-        if (g->kappa) g->kappa[k] = ac.gacc[4 * k + 2];
-        if (g->omega) g->omega[k] = ac.gacc[4 * k + 3];
+        if (g->g_re) g->g_re[k] = ac.gacc[7 * k + 0];
+        if (g->g_im) g->g_im[k] = ac.gacc[7 * k + 1];
+        if (g->kappa) g->kappa[k] = ac.gacc[7 * k + 2];
+        if (g->omega) g->omega[k] = ac.gacc[7 * k + 3];
+        if (g->gb_re) g->gb_re[k] = ac.gacc[7 * k + 4];
+        if (g->gb_im) g->gb_im[k] = ac.gacc[7 * k + 5];
+        if (g->kerr) g->kerr[k] = ac.gacc[7 * k + 6];
     }
     if (g->alpha) *g->alpha = ac.galpha;
     if (g->a0)

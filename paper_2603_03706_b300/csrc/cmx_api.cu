@@ -484,6 +484,8 @@ int cmx_create(const cmx_grid *grid, const uint8_t *mask, const cmx_material *ma
         c.kappa[n] = h->kappa[n];
         c.gre[n] = h->gre[n];
         c.gim[n] = h->gim[n];
+        c.gbre[n] = h->gre[n];   // reciprocal unless cmx_set_backward_coupling
+        c.gbim[n] = h->gim[n];
     }
     c.two_over_gamma = 2.0 / mat->gamma;
     c.inv_nmag = 1.0 / (double)h->ncell_mag;
@@ -742,6 +744,25 @@ int cmx_debug_skip_arrival(cmx_problem *h, int block)
 {
     if (!h || block >= h->blocks) return fail(h, CMX_EINVAL, "bad argument");
     h->skip_block = block;
+    return CMX_OK;
+}
+
+int cmx_set_backward_coupling(cmx_problem *h, const double *gb_re, const double *gb_im)
+{
+    if (!h || (gb_re && !gb_im)) return fail(h, CMX_EINVAL, "bad argument");
+    Ctx &c = h->base;
+    for (int n = 0; n < h->N; n++) {
+        c.gbre[n] = gb_re ? gb_re[n] : h->gre[n];
+        c.gbim[n] = gb_re ? gb_im[n] : h->gim[n];
+    }
+    c.has_gb = gb_re != nullptr;
+    return CMX_OK;
+}
+
+int cmx_set_kerr(cmx_problem *h, const double *kerr)
+{
+    if (!h) return CMX_EINVAL;
+    for (int n = 0; n < MAXN; n++) h->base.kerr[n] = (kerr && n < h->N) ? kerr[n] : 0.0;
     return CMX_OK;
 }
 

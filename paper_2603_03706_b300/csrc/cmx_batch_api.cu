@@ -406,7 +406,9 @@ int cmx_batch_create(const cmx_instance *in, int n, const cmx_solver *solver,
             c.omega[k] = I.omega[k];
             c.kappa[k] = I.kappa[k];
             c.gre[k] = I.gre[k];
+            c.gbre[k] = I.gre[k];   // reciprocal coupling
             c.gim[k] = I.gim[k];
+            c.gbim[k] = I.gim[k];
         }
         c.two_over_gamma = 2.0 / I.mat.gamma;
         c.inv_nmag = 1.0 / (double)I.lay.ncell_mag;

@@ -36,7 +36,7 @@ struct Local {
     const double *replay_dts;
     double mm[2 * MAXN], as[2 * MAXN];   // overlaps and cavity stage value of this stage
     double err_n[MAXN], amax_n[MAXN];    // per-mode error and amplitude (stage 7)
-    double mc[4 * MAXN];                 // mode constants: w, kappa, Re g~, Im g~
+    double mc[MC * MAXN];                // mode constants (see MC)
     unsigned bar_target;                 // arrival count that completes the next barrier
     int skip_block;
     int kphys[7];
@@ -134,15 +134,17 @@ __device__ __forceinline__ int checkpoint_slot(const Ctx &c, const Local &L)
     return slot < c.traj_slots ? (int)slot : -1;
 }
 
-// Cavity right-hand side (-i w - kappa) a + i g~ mm for one mode (Eq. (12), (19)); the mode
-// constants come from the block's shared copy (w, kappa, Re g~, Im g~).
+// Cavity right-hand side (-i w - kappa) a + i g~ mm - i K |a|^2 a for one mode (Eq. (12), (19),
+// with the optional self-Kerr term); the mode constants come from the block's shared copy.
 __device__ __forceinline__ void cavity_rhs(const double *mc, int n, double ar, double ai,
                                            double mr, double mi, double &dr, double &di)
 {
-    const double w = mc[4 * n], k = mc[4 * n + 1], gr = mc[4 * n + 2], gi = mc[4 * n + 3];
+    const double *q = mc + MC * n;
+    const double w = q[0], k = q[1], gr = q[2], gi = q[3], K = q[6];
     const double pr = gr * mr - gi * mi, pi = gr * mi + gi * mr;   // g~ <m^->
-    dr = -k * ar + w * ai - pi;
-    di = -k * ai - w * ar + pr;
+    const double k2 = K * (ar * ar + ai * ai);
+    dr = -k * ar + w * ai - pi + k2 * ai;
+    di = -k * ai - w * ar + pr - k2 * ar;
 }
 
 // Stage-S cavity update and, after stage 7, error norm, accept/reject and step-size control,
@@ -473,8 +475,8 @@ __device__ bool run_stage(const Ctx &c, const Team &tm, SM &sm, Local &L, Coef &
     if (tid == 96) cf.h = (float)h;
     __syncthreads();
     if (tid < N)
-        cf.hrf[tid] = (float)(c.two_over_gamma * (L.mc[4 * tid + 2] * L.as[2 * tid] -
-                                                  L.mc[4 * tid + 3] * L.as[2 * tid + 1]));
+        cf.hrf[tid] = (float)(c.two_over_gamma * (L.mc[MC * tid + 4] * L.as[2 * tid] -
+                                                  L.mc[MC * tid + 5] * L.as[2 * tid + 1]));
     __syncthreads();
     Acc acc;
 #pragma unroll
@@ -504,22 +506,7 @@ __device__ bool integrate(const Ctx &c, const Team &tm, SM &sm, Local &L, Coef &
                           double *s_sum, float &s_emax, int &s_stop)
 {
     if (threadIdx.x == 0) load_local(c, L);
-    if (threadIdx.x < c.nmodes) {
-        const int n = threadIdx.x;
-        double w = c.omega[0], ka = c.kappa[0], gr = c.gre[0], gi = c.gim[0];
-#pragma unroll
-        for (int u = 1; u < MAXN; u++)
-            if (n == u) {
-                w = c.omega[u];
-                ka = c.kappa[u];
-                gr = c.gre[u];
-                gi = c.gim[u];
-            }
-        L.mc[4 * n] = w;
-        L.mc[4 * n + 1] = ka;
-        L.mc[4 * n + 2] = gr;
-        L.mc[4 * n + 3] = gi;
-    }
+    if (threadIdx.x < c.nmodes) mode_constants(c, threadIdx.x, L.mc + MC * threadIdx.x);
     {
         const int sb = __ldg(&c.seg_begin[tm.rank]), se = __ldg(&c.seg_begin[tm.rank + 1]);
         if (threadIdx.x == 0) sm.nseg = se - sb;

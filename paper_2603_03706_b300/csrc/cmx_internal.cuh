@@ -11,6 +11,11 @@ namespace cmx {
 
 constexpr int MAXN = CMX_MAX_MODES;
 
+// Mode constants held per mode by the device code: w, kappa, Re g~, Im g~ (forward coupling, in
+// the cavity equation), Re gb~, Im gb~ (backward coupling, in the feedback field) and the
+// self-Kerr coefficient K.
+constexpr int MC = 7;
+
 // Longest segment (planes including its two halo planes) and most segments per block.
 constexpr int MAX_TILE_PLANES = 66;
 constexpr int MAX_BLOCK_SEGMENTS = 64;
@@ -114,6 +119,9 @@ struct Ctx {
     float pre, alpha;                // -gamma/(1+alpha^2), alpha
     // modes
     double omega[MAXN], kappa[MAXN], gre[MAXN], gim[MAXN];
+    double gbre[MAXN], gbim[MAXN];   // backward (feedback) coupling; equal to g~ unless set
+    double kerr[MAXN];               // self-Kerr -i K |a|^2 a (0: none)
+    int has_gb;                      // 1: nonreciprocal coupling (gradients of gb~ separate)
     double two_over_gamma, inv_nmag;
     double red_scale;                // fixed-point scale of the overlap sums (a power of two)
     // external drive eta_n(t) = drive_n exp(-(t - drive_t0)^2 / (2 sigma^2)) on da_n/dt

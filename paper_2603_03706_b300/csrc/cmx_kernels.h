@@ -46,7 +46,7 @@ cudaError_t launch_batch_spectrum(const SpecInst *si, int n, double f0, double d
 struct AdjCtl {
     double abar[2 * MAXN];           // dL/d a at the current step boundary
     double k1a[2 * MAXN];            // dL/d (cavity part of the FSAL slope)
-    double gacc[4 * MAXN];           // per mode: dL/d Re g~, dL/d Im g~, dL/d kappa, dL/d omega
+    double gacc[7 * MAXN];           // per mode: dL/d Re g~, Im g~, kappa, omega, Re gb~, Im gb~, K
     double galpha;                   // dL/d alpha
     unsigned int bar_count;          // arrival counter of the launch's barrier
     int status;

@@ -211,6 +211,8 @@ extern "C" int cmx_eval_rhs_noalloc(const cmx_grid *grid, const uint8_t *mask,
         c.kappa[n] = modes->kappa[n];
         c.gre[n] = modes->g_re[n];
         c.gim[n] = modes->g_im[n];
+        c.gbre[n] = modes->g_re[n];   // reciprocal coupling
+        c.gbim[n] = modes->g_im[n];
     }
     c.two_over_gamma = 2.0 / mat->gamma;
     c.inv_nmag = 1.0 / (double)lay.ncell_mag;

@@ -51,6 +51,26 @@ __device__ __forceinline__ float nanmax(float a, float b)
     return (a != a || b != b) ? __int_as_float(0x7fffffff) : fmaxf(a, b);
 }
 
+// The mode constants of mode n (MC doubles) from the context (select rather than index the
+// kernel-parameter arrays, which keeps them out of local memory).
+__device__ __forceinline__ void mode_constants(const Ctx &c, int n, double *out)
+{
+    double v[MC] = {c.omega[0], c.kappa[0], c.gre[0], c.gim[0], c.gbre[0], c.gbim[0], c.kerr[0]};
+#pragma unroll
+    for (int u = 1; u < MAXN; u++)
+        if (n == u) {
+            v[0] = c.omega[u];
+            v[1] = c.kappa[u];
+            v[2] = c.gre[u];
+            v[3] = c.gim[u];
+            v[4] = c.gbre[u];
+            v[5] = c.gbim[u];
+            v[6] = c.kerr[u];
+        }
+#pragma unroll
+    for (int q = 0; q < MC; q++) out[q] = v[q];
+}
+
 // Slopes read by stage S (1-based): those with a nonzero coupling, and at stage 7 also those
 // with a nonzero error weight.  Array 0 of a stage is m_n, arrays 1.. are these slopes.
 __host__ __device__ constexpr bool slope_used(int S, int j)
