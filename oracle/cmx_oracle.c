@@ -65,6 +65,9 @@ typedef struct {
     const double *gb_re, *gb_im;
     /* self-Kerr term -i K_n |a_n|^2 a_n of the cavity equation; NULL: none */
     const double *kerr;
+    /* 1: the cavity amplitudes are held fixed (da/dt = 0, no drive): the magnet-only
+       sub-integration of the operator-split scheme (orc_run_split) */
+    int cavity_frozen;
 } orc_problem;
 
 typedef struct {
@@ -263,8 +266,8 @@ int orc_rhs(const orc_problem *P, const double *m, const double *a, double *dm, 
             r += k2 * ai;
             i -= k2 * ar;
         }
-        da[2 * n] = r;
-        da[2 * n + 1] = i;
+        da[2 * n] = P->cavity_frozen ? 0.0 : r;
+        da[2 * n + 1] = P->cavity_frozen ? 0.0 : i;
     }
     return ORC_OK;
 }
@@ -338,7 +341,7 @@ void orc_state_get(const orc_state *S, double *m, double *a, double *t, double *
 /* The drive at time t added to the cavity slopes da (Eq. (1), (12)). */
 static void add_drive(const orc_problem *P, double t, double *da)
 {
-    if (!P->drive_re) return;
+    if (!P->drive_re || P->cavity_frozen) return;
     const double x = (t - P->drive_t0) / P->drive_sigma;
     const double env = exp(-0.5 * x * x);
     for (int n = 0; n < P->nmodes; n++) {
@@ -898,4 +901,73 @@ done:
     }
     orc_state_free(S);
     return rc;
+}
+
+/* ------------------------------------------------------------------------------------------- */
+/* Operator-split scheme of the paper's Python tier (Sec. III B / III C), for comparison.        */
+/* ------------------------------------------------------------------------------------------- */
+
+/* Cavity slope at amplitude a and time t with the overlaps mm held fixed:
+   (-i w - kappa) a + i g~ mm - i K |a|^2 a + eta(t). */
+static void split_cavity_slope(const orc_problem *P, const double *a, const double *mm, double t,
+                               double *da)
+{
+    for (int n = 0; n < P->nmodes; n++) {
+        const double ar = a[2 * n], ai = a[2 * n + 1];
+        const double gr = P->g_re[n], gi = P->g_im[n], mr = mm[2 * n], mi = mm[2 * n + 1];
+        double r = -P->kappa[n] * ar + P->omega[n] * ai - (gr * mi + gi * mr);
+        double i = -P->kappa[n] * ai - P->omega[n] * ar + (gr * mr - gi * mi);
+        if (P->kerr) {
+            const double k2 = P->kerr[n] * (ar * ar + ai * ai);
+            r += k2 * ai;
+            i -= k2 * ar;
+        }
+        da[2 * n] = r;
+        da[2 * n + 1] = i;
+    }
+    if (P->drive_re) {
+        const double x = (t - P->drive_t0) / P->drive_sigma;
+        const double env = exp(-0.5 * x * x);
+        for (int n = 0; n < P->nmodes; n++) {
+            da[2 * n] += P->drive_re[n] * env;
+            da[2 * n + 1] += P->drive_im[n] * env;
+        }
+    }
+}
+
+/*
+ * Lie splitting with interval ds, from S->t to T: at every interval start t_k = t_start + k ds
+ * the cavity takes one classical RK4 step of length ds with the overlaps frozen at those of the
+ * current magnetisation, then the magnet alone (cavity held at the new amplitudes, so the
+ * feedback field is fixed) is integrated adaptively to t_{k+1}.  First order in ds.
+ */
+int orc_run_split(const orc_problem *P, orc_state *S, const orc_solver *sv, double T, double ds,
+                  long max_attempts, orc_log *L)
+{
+    const int N = P->nmodes;
+    if (!(ds > 0.0) || N > 64) return ORC_EINVAL;
+    orc_problem Q = *P;
+    Q.cavity_frozen = 1;
+    double mm[128], k1[128], k2[128], k3[128], k4[128], y[128];
+    const double t_start = S->t;
+    for (long k = 0; S->t < T; k++) {
+        double t1 = t_start + (double)(k + 1) * ds;
+        if (t1 > T) t1 = T;
+        const double h = t1 - S->t;
+        orc_overlap(P, S->m, mm);
+        split_cavity_slope(P, S->a, mm, S->t, k1);
+        for (int q = 0; q < 2 * N; q++) y[q] = S->a[q] + 0.5 * h * k1[q];
+        split_cavity_slope(P, y, mm, S->t + 0.5 * h, k2);
+        for (int q = 0; q < 2 * N; q++) y[q] = S->a[q] + 0.5 * h * k2[q];
+        split_cavity_slope(P, y, mm, S->t + 0.5 * h, k3);
+        for (int q = 0; q < 2 * N; q++) y[q] = S->a[q] + h * k3[q];
+        split_cavity_slope(P, y, mm, S->t + h, k4);
+        for (int q = 0; q < 2 * N; q++)
+            S->a[q] += h / 6.0 * (k1[q] + 2.0 * k2[q] + 2.0 * k3[q] + k4[q]);
+        S->k1_valid = 0;   /* the feedback field changed with a */
+        int rc = orc_run(&Q, S, sv, t1, max_attempts, L);
+        if (rc) return rc;
+        if (S->t < t1) return ORC_ESTEPFAIL;   /* attempt budget exhausted */
+    }
+    return ORC_OK;
 }

@@ -12,6 +12,7 @@ Functions
 ``jacobian(op, m, a)``       central-difference Jacobian of the right-hand side (for the
                              linearised-eigenvalue pins, Sec. II B, F, G).
 ``tableau()``                the oracle's own Butcher tableau (for the order-condition pin).
+``Integrator.run_split``     the operator-split scheme of the paper's Python tier (comparison).
 ``rhs_vjp(op, m, a, wm, wa)`` transposed derivative of f applied to adjoint weights, with the
                              parameter gradients (g~_n, kappa_n, omega_n, alpha, u_n(r)).
 ``adjoint(op, m0, a0, dts, dL_da, dL_dm)``  gradient of a loss on the states a_0..a_n and m_n
@@ -55,7 +56,7 @@ class _Problem(C.Structure):
                 ("drive_re", C.POINTER(C.c_double)), ("drive_im", C.POINTER(C.c_double)),
                 ("drive_t0", C.c_double), ("drive_sigma", C.c_double),
                 ("gb_re", C.POINTER(C.c_double)), ("gb_im", C.POINTER(C.c_double)),
-                ("kerr", C.POINTER(C.c_double))]
+                ("kerr", C.POINTER(C.c_double)), ("cavity_frozen", C.c_int)]
 
 
 class _Solver(C.Structure):
@@ -101,6 +102,9 @@ def lib():
         _lib.orc_run.restype = C.c_int
         _lib.orc_replay.argtypes = [P, vp, C.POINTER(_Solver), dp, C.c_long, C.POINTER(_Log)]
         _lib.orc_replay.restype = C.c_int
+        _lib.orc_run_split.argtypes = [P, vp, C.POINTER(_Solver), C.c_double, C.c_double,
+                                       C.c_long, C.POINTER(_Log)]
+        _lib.orc_run_split.restype = C.c_int
         _lib.orc_tableau.argtypes = [dp, dp, dp]
         G = C.POINTER(_Grads)
         _lib.orc_rhs_vjp.argtypes = [P, dp, dp, dp, dp, dp, dp, G]
@@ -288,6 +292,14 @@ class Integrator:
         log = Log(log_cap, self.op.N)
         rc = lib().orc_run(self.op.ref, self.h, C.byref(self.op.solver), float(T),
                            int(max_attempts), C.byref(log.s))
+        return rc, log
+
+    def run_split(self, T: float, ds: float, max_attempts: int = 10 ** 9, log_cap: int = 0):
+        """Operator-split scheme (cavity RK4 with frozen overlaps, then the magnet alone) with
+        interval ds, to T."""
+        log = Log(log_cap, self.op.N)
+        rc = lib().orc_run_split(self.op.ref, self.h, C.byref(self.op.solver), float(T),
+                                 float(ds), int(max_attempts), C.byref(log.s))
         return rc, log
 
     def replay(self, dts, log: bool = True):
