@@ -200,6 +200,15 @@ int cmx_debug_skip_arrival(cmx_problem *h, int block);
 int cmx_set_drive(cmx_problem *h, const double *eta_re, const double *eta_im, double t0,
                   double sigma);
 
+/* Operator-split scheme of the paper's Python tier (Sec. III B/C), for comparison with the coupled
+ * integrator: every interval ds the cavity takes one classical RK4 step with the overlaps held at
+ * those of the current magnetisation, then the magnet alone is integrated adaptively to the next
+ * boundary with the cavity (and so the feedback field) held fixed.  First order in ds; still one
+ * persistent launch (the boundaries and cavity steps are handled by the device controller).
+ * ds = 0 returns to the coupled scheme.  Applies from the current state on; replays and the
+ * adjoint use the coupled scheme (cmx_adjoint_record fails while it is on). */
+int cmx_set_split(cmx_problem *h, double ds);
+
 /* Nonreciprocal coupling (Sec. II: separate forward and backward coefficients, h0 = 2 g_b /
  * gamma): the feedback field uses B_rf,x = sum_n u_n (2/gamma) Re[gb~_n a_n] with the backward
  * coefficients gb~ given here (host, n_modes each), while the cavity equation keeps the forward

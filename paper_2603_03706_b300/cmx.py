@@ -130,6 +130,7 @@ SIGNATURES = {
                                  C.POINTER(C.c_longlong), C.POINTER(C.c_int)]),
     "cmx_batch_last_error": (C.c_char_p, [_P]),
     "cmx_autotune": (C.c_int, [_P, C.c_int, C.c_void_p, C.c_void_p]),
+    "cmx_set_split": (C.c_int, [_P, C.c_double]),
     "cmx_set_backward_coupling": (C.c_int, [_P, C.c_void_p, C.c_void_p]),
     "cmx_set_kerr": (C.c_int, [_P, C.c_void_p]),
     "cmx_set_drive": (C.c_int, [_P, C.c_void_p, C.c_void_p, C.c_double, C.c_double]),
@@ -482,6 +483,10 @@ class Simulation:
 
     def debug_skip_arrival(self, block: int):
         self._check(load().cmx_debug_skip_arrival(self.h, int(block)), "debug_skip_arrival")
+
+    def set_split(self, ds: float):
+        """cmx_set_split: operator-split scheme with interval ds (0: the coupled scheme)."""
+        self._check(load().cmx_set_split(self.h, float(ds)), "set_split")
 
     def set_backward_coupling(self, gb=None):
         """cmx_set_backward_coupling: complex backward coefficients gb~_n of the feedback field

@@ -194,6 +194,8 @@ int cmx_adjoint_record(cmx_problem *h, int every, long long max_steps)
     if (rc) return rc;
     if (hc.k1_valid || hc.accepted != 0 || hc.attempts != 0)
         return fail(h, CMX_EINVAL, "cmx_adjoint_record must follow cmx_set_state directly");
+    if (h->base.split_dt > 0.0)
+        return fail(h, CMX_EINVAL, "the adjoint differentiates the coupled scheme, not the split one");
     if (!h->adj) h->adj = new AdjState();
     AdjState *s = h->adj;
     const int nq = 3 * h->grid.nsub, N = std::max(1, h->N);

@@ -318,6 +318,11 @@ int reset_ctl(cmx_problem *h, const double *a, double t)
     c.trace_next = t;
     c.skip_block = -1;
     c.max_launch_attempts = 1;
+    if (h->base.split_dt > 0.0) {   // operator-split scheme: a cavity step comes first
+        c.split_t0 = t;
+        c.split_next = t + h->base.split_dt;
+        c.split_pending = 1;
+    }
     CU(cudaMemcpyAsync(h->ctl, &c, sizeof c, cudaMemcpyHostToDevice, h->stream));
     CU(cudaStreamSynchronize(h->stream));
     return CMX_OK;
@@ -744,6 +749,25 @@ int cmx_debug_skip_arrival(cmx_problem *h, int block)
 {
     if (!h || block >= h->blocks) return fail(h, CMX_EINVAL, "bad argument");
     h->skip_block = block;
+    return CMX_OK;
+}
+
+int cmx_set_split(cmx_problem *h, double ds)
+{
+    if (!h || !(ds >= 0.0) || !std::isfinite(ds)) return fail(h, CMX_EINVAL, "bad argument");
+    if (ds > 0.0 && h->base.traj_m)
+        return fail(h, CMX_EINVAL, "the adjoint differentiates the coupled scheme, not the split one");
+    Ctl hc;
+    int rc = read_ctl(h, &hc);
+    if (rc) return rc;
+    h->base.split_dt = ds;
+    hc.split_t0 = hc.t;
+    hc.split_k = 0;
+    hc.split_next = hc.t + ds;
+    hc.split_pending = ds > 0.0;
+    hc.k1_valid = 0;   // the first slope follows the first cavity step
+    CU(cudaMemcpyAsync(h->ctl, &hc, sizeof hc, cudaMemcpyHostToDevice, h->stream));
+    CU(cudaStreamSynchronize(h->stream));
     return CMX_OK;
 }
 

@@ -31,6 +31,9 @@ struct Local {
     double ka[7][2 * MAXN];
     double mm_n[2 * MAXN];
     double trace_next;
+    double split_next, split_t0;
+    long long split_k;
+    int split_pending, at_split;
     long long attempts, accepted, launch_attempts, max_launch_attempts, rhs_evals;
     long long replay_pos, replay_n, log_n, trace_n;
     const double *replay_dts;
@@ -55,6 +58,11 @@ __device__ __forceinline__ void load_local(const Ctx &c, Local &L)
         for (int j = 0; j < 7; j++) L.ka[j][q] = g->ka[j][q];
     }
     L.trace_next = g->trace_next;
+    L.split_next = g->split_next;
+    L.split_t0 = g->split_t0;
+    L.split_k = g->split_k;
+    L.split_pending = g->split_pending;
+    L.at_split = 0;
     L.attempts = g->attempts;
     L.accepted = g->accepted;
     L.launch_attempts = g->launch_attempts;
@@ -89,6 +97,9 @@ __device__ __forceinline__ void store_local(const Ctx &c, const Local &L)
         for (int j = 0; j < 7; j++) g->ka[j][q] = L.ka[j][q];
     }
     g->trace_next = L.trace_next;
+    g->split_next = L.split_next;
+    g->split_k = L.split_k;
+    g->split_pending = L.split_pending;
     g->attempts = L.attempts;
     g->accepted = L.accepted;
     g->launch_attempts = L.launch_attempts;
@@ -105,10 +116,12 @@ __device__ __forceinline__ void store_local(const Ctx &c, const Local &L)
     __threadfence();
 }
 
-// Size of the next attempt: the replay list, or min(dt, dt_max) shortened to land on T.
+// Size of the next attempt: the replay list, or min(dt, dt_max) shortened to land on T (and,
+// in the operator-split scheme, on the next interval boundary).
 __device__ __forceinline__ void attempt_size(const Ctx &c, Local &L)
 {
     L.last = 0;
+    L.at_split = 0;
     if (L.replay) {
         L.h = L.replay_dts[L.replay_pos];
         return;
@@ -117,6 +130,11 @@ __device__ __forceinline__ void attempt_size(const Ctx &c, Local &L)
     if (L.t + L.h >= L.T) {
         L.h = L.T - L.t;
         L.last = 1;
+    }
+    if (c.split_dt > 0.0 && L.t + L.h >= L.split_next) {
+        L.h = L.split_next - L.t;
+        L.at_split = 1;
+        L.last = L.split_next >= L.T;
     }
 }
 
@@ -147,6 +165,47 @@ __device__ __forceinline__ void cavity_rhs(const double *mc, int n, double ar, d
     di = -k * ai - w * ar + pr - k2 * ar;
 }
 
+// Operator-split scheme: one classical RK4 step of the cavity from L.t to the next boundary
+// with the overlaps held at mm (those of the current magnetisation), on 2N real components,
+// run by one thread.  Same slope as cavity_rhs plus the drive.
+static __device__ __noinline__ void split_cavity_step(const Ctx &c, Local &L, const double *mm)
+{
+    const int N = c.nmodes;
+    const double h = L.split_next - L.t;
+    double a0[2 * MAXN], y[2 * MAXN], acc[2 * MAXN], k[2 * MAXN];
+    for (int q = 0; q < 2 * N; q++) a0[q] = y[q] = L.a[q];
+    for (int st = 0; st < 4; st++) {
+        const double ts = L.t + (st == 0 ? 0.0 : (st == 3 ? h : 0.5 * h));
+        double env = 0.0;
+        if (c.has_drive) {
+            const double x = (ts - c.drive_t0) * c.drive_inv_sigma;
+            env = exp(-0.5 * x * x);
+        }
+        for (int n = 0; n < N; n++) {
+            double dr, di;
+            cavity_rhs(L.mc, n, y[2 * n], y[2 * n + 1], mm[2 * n], mm[2 * n + 1], dr, di);
+            if (c.has_drive) {
+                double er = c.drive_re[0], ei = c.drive_im[0];
+                for (int u = 1; u < MAXN; u++)
+                    if (n == u) {
+                        er = c.drive_re[u];
+                        ei = c.drive_im[u];
+                    }
+                dr += er * env;
+                di += ei * env;
+            }
+            k[2 * n] = dr;
+            k[2 * n + 1] = di;
+        }
+        const double wgt = (st == 0 || st == 3) ? 1.0 : 2.0;
+        for (int q = 0; q < 2 * N; q++) {
+            acc[q] = (st == 0 ? 0.0 : acc[q]) + wgt * k[q];
+            if (st < 3) y[q] = a0[q] + (st == 2 ? h : 0.5 * h) * k[q];
+        }
+    }
+    for (int q = 0; q < 2 * N; q++) L.a[q] = a0[q] + h / 6.0 * acc[q];
+}
+
 // Stage-S cavity update and, after stage 7, error norm, accept/reject and step-size control,
 // on the block's copy L.  L.as holds the cavity stage value a_S (set before the stage), `sum`
 // the grid sums of the overlaps and `emax` the grid maximum of |e_m|.  The per-mode FP64 work
@@ -162,7 +221,10 @@ __device__ void controller(const Ctx &c, const Team &tm, Local &L, const double 
         double dr, di;
         cavity_rhs(L.mc, tid, L.as[2 * tid], L.as[2 * tid + 1], L.mm[2 * tid],
                    L.mm[2 * tid + 1], dr, di);
-        if (c.has_drive) {   // the drive at this stage's time t + c_S h
+        if (c.split_dt > 0.0 && !L.replay) {   // operator split: cavity held during magnet steps
+            dr = 0.0;
+            di = 0.0;
+        } else if (c.has_drive) {   // the drive at this stage's time t + c_S h
             const double ts = S == 1 ? L.t : L.t + dp_c(S - 1) * L.h;
             const double x = (ts - c.drive_t0) * c.drive_inv_sigma;
             const double env = exp(-0.5 * x * x);
@@ -220,6 +282,13 @@ __device__ void controller(const Ctx &c, const Team &tm, Local &L, const double 
         L.k1_valid = 1;
         for (int q = 0; q < 2 * N; q++) L.mm_n[q] = L.mm[q];
         if (c.stage_only) L.done = 1;
+        if (c.split_dt > 0.0 && L.split_pending && !c.stage_only && !L.replay) {
+            // cavity step over the coming interval with the overlaps of the current m; the
+            // slope just computed used the old feedback field: evaluate stage 1 again
+            split_cavity_step(c, L, L.mm);
+            L.split_pending = 0;
+            L.k1_valid = 0;
+        }
         return;
     }
     if (S != 7) return;
@@ -247,7 +316,7 @@ __device__ void controller(const Ctx &c, const Team &tm, Local &L, const double 
     double t1 = t0;
     const double *as = L.as, *mm = L.mm;
     if (accepted) {
-        t1 = L.last ? L.T : t0 + h;
+        t1 = L.last ? L.T : (L.at_split ? L.split_next : t0 + h);
         // uniform trace: cubic Hermite for a_n (end slopes k1, k7), linear for <m^->_n
         if (c.tr_cap > 0 && c.sample_dt > 0.0) {
             long long tn = L.trace_n;
@@ -281,6 +350,12 @@ __device__ void controller(const Ctx &c, const Team &tm, Local &L, const double 
         L.mcur ^= 1;
         L.t = t1;
         L.accepted += 1;
+        if (L.at_split && t1 < L.T) {   // boundary reached: cavity step before the next interval
+            L.split_k += 1;
+            L.split_next = fmin(L.split_t0 + (double)(L.split_k + 1) * c.split_dt, L.T);
+            L.split_pending = 1;
+            L.k1_valid = 0;
+        }
     }
     if (rec && li < c.log_cap) {
         cmx_step st;
@@ -525,11 +600,12 @@ __device__ bool integrate(const Ctx &c, const Team &tm, SM &sm, Local &L, Coef &
         }
         __syncthreads();
         if (s_stop) break;
-        if (!L.k1_valid) {
+        while (!L.k1_valid) {   // twice at an operator-split boundary (see controller<1>)
             if (!(ok = run_stage<1>(c, tm, sm, L, cf, s_sum, &s_emax, pp, false)))
                 break;
             if (c.stage_only) break;
         }
+        if (!ok || c.stage_only) break;
         if (!(ok = run_stage<2>(c, tm, sm, L, cf, s_sum, &s_emax, pp, false))) break;
         if (!(ok = run_stage<3>(c, tm, sm, L, cf, s_sum, &s_emax, pp, true))) break;
         if (!(ok = run_stage<4>(c, tm, sm, L, cf, s_sum, &s_emax, pp, true))) break;

@@ -87,6 +87,11 @@ struct Ctl {
     const double *replay_dts;
     long long log_n, trace_n;
     double trace_next;
+    // operator-split scheme (Ctx::split_dt > 0): next interval boundary, its index, the grid's
+    // origin, and a cavity step still to be taken at the current boundary
+    double split_next, split_t0;
+    long long split_k;
+    int split_pending;
     unsigned int bar_count, bar_gen; // grid barrier
     // Grid sums of the stage's overlaps as fixed-point integers (value x red_scale), and the bit
     // pattern of the grid max of |e_m|, in three sets used in turn by stage count mod 3: the
@@ -141,6 +146,7 @@ struct Ctx {
     long long timeout_ns;
     int stage_only;                  // 1: evaluate stage 1 once (cmx_eval_rhs) and stop
     int quad;                        // 1: quad windows (four x-cells per thread, align-4 rows)
+    double split_dt;                 // > 0: operator-split scheme with this interval
     // Checkpoint store of the adjoint (NULL = off): slot k holds the state after
     // k * traj_every accepted steps counted from traj_base (slot 0: the initial state):
     // m (renormalised) and the FSAL slope k1, and a, k1^a and <m^-> at the slope's point.
