@@ -46,8 +46,9 @@ def test_energy_transfer_value_and_gradient():
     a = torch.tensor([[[0.01, 0.002], [0.0, 0.0]], [[0.005, 0.0], [0.003, -0.004]]],
                      dtype=torch.float64, requires_grad=True)
     L = AD.energy_transfer(a, 0, 1)
-    assert abs(float(L) - (0.003 ** 2 + 0.004 ** 2) / (0.01 ** 2 + 0.002 ** 2)) < 1e-15
+    Lv = L.item()
+    assert abs(Lv - (0.003 ** 2 + 0.004 ** 2) / (0.01 ** 2 + 0.002 ** 2)) < 1e-15
     L.backward()
     e0 = 0.01 ** 2 + 0.002 ** 2
     assert np.allclose(a.grad[1, 1].numpy(), 2 * np.array([0.003, -0.004]) / e0)
-    assert np.allclose(a.grad[0, 0].numpy(), -2 * float(L) / e0 * np.array([0.01, 0.002]))
+    assert np.allclose(a.grad[0, 0].numpy(), -2 * Lv / e0 * np.array([0.01, 0.002]))
