@@ -14,8 +14,6 @@ __global__ void __launch_bounds__(WX *WY, (WX * WY <= 256 ? 2 : 1)) batch_kernel
     auto &sm = *reinterpret_cast<StageSmem<NS, WX, WY, false> *>(smem_raw);
     __shared__ Local L;
     __shared__ Coef cf;
-    __shared__ double s_sum[2 * MAXN];
-    __shared__ float s_emax;
     __shared__ int s_stop;
     __shared__ __align__(16) Ctx sc;
     const int team = blockIdx.x / B.team_size, rank = blockIdx.x % B.team_size;
@@ -29,7 +27,7 @@ __global__ void __launch_bounds__(WX *WY, (WX * WY <= 256 ? 2 : 1)) batch_kernel
             dst[w] = __ldg(src + w);
         __syncthreads();
         const Team tm{rank, B.team_size, &sc.ctl->bar_count};
-        integrate(sc, tm, sm, L, cf, s_sum, s_emax, s_stop);
+        integrate(sc, tm, sm, L, cf, s_stop);
     }
 }
 

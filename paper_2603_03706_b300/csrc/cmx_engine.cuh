@@ -38,8 +38,9 @@ struct Local {
     long long replay_pos, replay_n, log_n, trace_n;
     const double *replay_dts;
     double mm[2 * MAXN], as[2 * MAXN];   // overlaps and cavity stage value of this stage
-    double err_n[MAXN], amax_n[MAXN];    // per-mode error and amplitude (stage 7)
     double mc[MC * MAXN];                // mode constants (see MC)
+    double rs;                           // fixed-point overlap sum -> <m^->: 1 / (scale N_c)
+    float rtolf, inv_rtolf, areff;       // error-norm constants in FP32
     unsigned bar_target;                 // arrival count that completes the next barrier
     int skip_block;
     int kphys[7];
@@ -206,21 +207,71 @@ static __device__ __noinline__ void split_cavity_step(const Ctx &c, Local &L, co
     for (int q = 0; q < 2 * N; q++) L.a[q] = a0[q] + h / 6.0 * acc[q];
 }
 
-// Stage-S cavity update and, after stage 7, error norm, accept/reject and step-size control,
-// on the block's copy L.  L.as holds the cavity stage value a_S (set before the stage), `sum`
-// the grid sums of the overlaps and `emax` the grid maximum of |e_m|.  The per-mode FP64 work
-// runs on 2N threads; the decision itself on thread 0.  Only block 0 writes log and trace.
+// Cavity value a_S of mode n (both components) for stage S of the current attempt and its
+// feedback coefficient hrf_n = (2/gamma) Re[gb~_n a_{n,S}] (Eq. (5), (13)), from the slopes of
+// the earlier stages; run by mode thread n.  Even and odd slopes go into separate partial sums,
+// which halves the dependent FP64 chain.
 template <int S>
-__device__ void controller(const Ctx &c, const Team &tm, Local &L, const double *sum, float emax)
+__device__ __forceinline__ void cavity_stage_value(const Ctx &c, Local &L, Coef &cf, int n)
+{
+    const double h = L.h;
+    double r0 = L.a[2 * n], i0 = L.a[2 * n + 1], r1 = 0.0, i1 = 0.0;
+#pragma unroll
+    for (int j = 0; j < S - 1; j++) {
+        if (dp_a(S - 1, j) == 0.0) continue;
+        const double w = h * dp_a(S - 1, j);
+        if (j & 1) {
+            r1 += w * L.ka[j][2 * n];
+            i1 += w * L.ka[j][2 * n + 1];
+        } else {
+            r0 += w * L.ka[j][2 * n];
+            i0 += w * L.ka[j][2 * n + 1];
+        }
+    }
+    const double vr = r0 + r1, vi = i0 + i1;
+    L.as[2 * n] = vr;
+    L.as[2 * n + 1] = vi;
+    cf.hrf[n] = (float)(c.two_over_gamma * (L.mc[MC * n + 4] * vr - L.mc[MC * n + 5] * vi));
+}
+
+// The FP32 stage coefficients h a_Sj of the whole attempt, entry q of rows S = 2..7, run by 36
+// threads once the attempt's size is known (the coefficient is selected, then multiplied once).
+__device__ __forceinline__ void attempt_coefficients(Coef &cf, double h, int q)
+{
+    double a = 0.0;
+#pragma unroll
+    for (int s = 1; s < 7; s++)
+#pragma unroll
+        for (int j = 0; j < 6; j++)
+            if (q == (s - 1) * 6 + j) a = dp_a(s, j);
+    cf.cf[1 + q / 6][q % 6] = (float)(h * a);
+}
+
+// Work after the barrier of stage S, on warp 0 (the caller's block barrier follows).  Mode
+// thread n (lane n < N) owns mode n: from its grid sums (fixed point: sre, sim) it forms the
+// overlap <m^->_n (Eq. (18)), the cavity slope (Eq. (12), (19), with the drive and the Kerr
+// term), the adjoint stores of its components and, before stage 7, the next stage's cavity
+// value and feedback coefficient.  After stage 7 the lanes take the scaled error norm (FP32,
+// warp maximum over the modes) and the accept decision, each lane the same, and update their
+// own components of the state; lane 0 keeps the scalar part (time, counters, step size, log).
+// Only the team's rank 0 writes log, trace and adjoint stores.  FP64 has a long dependent
+// latency on this GPU, so this part runs without block barriers and with short FP64 chains.
+template <int S>
+__device__ void controller(const Ctx &c, const Team &tm, Local &L, Coef &cf, long long sre,
+                           long long sim, float emax)
 {
     const int N = c.nmodes;
-    const int tid = threadIdx.x;
-    if (tid < 2 * N) L.mm[tid] = sum[tid] * c.inv_nmag;
-    __syncthreads();
-    if (tid < N) {
-        double dr, di;
-        cavity_rhs(L.mc, tid, L.as[2 * tid], L.as[2 * tid + 1], L.mm[2 * tid],
-                   L.mm[2 * tid + 1], dr, di);
+    const int lane = threadIdx.x;
+    if (lane >= 32) return;
+    const int n = lane;
+    const bool mt = n < N;
+    const bool rec = tm.rank == 0;
+    const long long li = L.log_n;
+    double mr = 0.0, mi = 0.0, dr = 0.0, di = 0.0;
+    if (mt) {
+        mr = (double)sre * L.rs;
+        mi = (double)sim * L.rs;
+        cavity_rhs(L.mc, n, L.as[2 * n], L.as[2 * n + 1], mr, mi, dr, di);
         if (c.split_dt > 0.0 && !L.replay) {   // operator split: cavity held during magnet steps
             dr = 0.0;
             di = 0.0;
@@ -231,94 +282,112 @@ __device__ void controller(const Ctx &c, const Team &tm, Local &L, const double 
             double er = c.drive_re[0], ei = c.drive_im[0];
 #pragma unroll
             for (int u = 1; u < MAXN; u++)
-                if (tid == u) {
+                if (n == u) {
                     er = c.drive_re[u];
                     ei = c.drive_im[u];
                 }
             dr += er * env;
             di += ei * env;
         }
-        L.ka[S - 1][2 * tid] = dr;
-        L.ka[S - 1][2 * tid + 1] = di;
-        if (S == 7) {
-            double er = 0.0, ei = 0.0;
-#pragma unroll
-            for (int j = 0; j < 7; j++) {
-                const double kr = j == 6 ? dr : L.ka[j][2 * tid];
-                const double ki = j == 6 ? di : L.ka[j][2 * tid + 1];
-                er += dp_e(j) * kr;
-                ei += dp_e(j) * ki;
+        L.mm[2 * n] = mr;
+        L.mm[2 * n + 1] = mi;
+        L.ka[S - 1][2 * n] = dr;
+        L.ka[S - 1][2 * n + 1] = di;
+        if (rec) {
+            // adjoint stores: a rejected attempt's checkpoint is overwritten by the accepted retry
+            const int slot = checkpoint_slot<S>(c, L);
+            if (slot >= 0 && c.traj_a) {
+                double *d = c.traj_a + (size_t)slot * traj_stride(N);
+                d[2 * n] = S == 7 ? L.as[2 * n] : L.a[2 * n];
+                d[2 * n + 1] = S == 7 ? L.as[2 * n + 1] : L.a[2 * n + 1];
+                d[2 * N + 2 * n] = dr;
+                d[2 * N + 2 * n + 1] = di;
+                d[4 * N + 2 * n] = mr;
+                d[4 * N + 2 * n + 1] = mi;
+                if (n == 0) d[6 * N] = S == 7 ? (L.last ? L.T : L.t + L.h) : L.t;
             }
-            // magnitudes in FP32: they only scale the error norm
-            L.err_n[tid] = (double)(fabsf((float)L.h) * hypotf((float)er, (float)ei));
-            L.amax_n[tid] = (double)fmaxf(hypotf((float)L.a[2 * tid], (float)L.a[2 * tid + 1]),
-                                          hypotf((float)L.as[2 * tid], (float)L.as[2 * tid + 1]));
+            if (c.rec_a && L.replay && L.replay_pos < c.rec_steps) {
+                double *d = c.rec_a + ((size_t)L.replay_pos * 7 + (S - 1)) * 4 * N;
+                d[2 * n] = L.as[2 * n];
+                d[2 * n + 1] = L.as[2 * n + 1];
+                d[2 * N + 2 * n] = mr;
+                d[2 * N + 2 * n + 1] = mi;
+            }
         }
+        if (S == 1) {
+            L.mm_n[2 * n] = mr;
+            L.mm_n[2 * n + 1] = mi;
+        }
+        if (S >= 2 && S < 7) cavity_stage_value<(S < 7 ? S + 1 : 7)>(c, L, cf, n);
     }
-    __syncthreads();
-    if (tid != 0) return;
-    L.rhs_evals += 1;
-    if (tm.rank == 0) {
-        // adjoint stores: a rejected attempt's checkpoint is overwritten by the accepted retry
-        const int slot = checkpoint_slot<S>(c, L);
-        if (slot >= 0 && c.traj_a) {
-            double *d = c.traj_a + (size_t)slot * traj_stride(N);
-            for (int q = 0; q < 2 * N; q++) {
-                d[q] = S == 7 ? L.as[q] : L.a[q];
-                d[2 * N + q] = L.ka[S - 1][q];
-                d[4 * N + q] = L.mm[q];
-            }
-            d[6 * N] = S == 7 ? (L.last ? L.T : L.t + L.h) : L.t;
-        }
-        if (c.rec_a && L.replay && L.replay_pos < c.rec_steps) {
-            double *d = c.rec_a + ((size_t)L.replay_pos * 7 + (S - 1)) * 4 * N;
-            for (int q = 0; q < 2 * N; q++) {
-                d[q] = L.as[q];
-                d[2 * N + q] = L.mm[q];
+    if (S != 7) {
+        if (lane == 0) {
+            L.rhs_evals += 1;
+            if (S == 1) {
+                L.k1_valid = 1;
+                if (c.stage_only) L.done = 1;
             }
         }
-    }
-    if (S == 1) {
-        L.k1_valid = 1;
-        for (int q = 0; q < 2 * N; q++) L.mm_n[q] = L.mm[q];
-        if (c.stage_only) L.done = 1;
-        if (c.split_dt > 0.0 && L.split_pending && !c.stage_only && !L.replay) {
+        if (S == 1 && c.split_dt > 0.0 && L.split_pending && !c.stage_only && !L.replay) {
             // cavity step over the coming interval with the overlaps of the current m; the
             // slope just computed used the old feedback field: evaluate stage 1 again
-            split_cavity_step(c, L, L.mm);
-            L.split_pending = 0;
-            L.k1_valid = 0;
+            __syncwarp();
+            if (lane == 0) {
+                split_cavity_step(c, L, L.mm);
+                L.split_pending = 0;
+                L.k1_valid = 0;
+            }
         }
         return;
     }
-    if (S != 7) return;
 
-    // scaled error norm
-    const double h = L.h;
-    double ea = 0.0, amax = 0.0;
-    for (int n = 0; n < N; n++) {
-        if (L.err_n[n] > ea || L.err_n[n] != L.err_n[n]) ea = L.err_n[n];
-        amax = fmax(amax, L.amax_n[n]);
+    // stage 7: error estimate of mode n (even and odd weights in separate partial sums)
+    float en = 0.f, an = 0.f;
+    if (mt) {
+        double r0 = 0.0, i0 = 0.0, r1 = 0.0, i1 = 0.0;
+#pragma unroll
+        for (int j = 0; j < 7; j++) {
+            if (dp_e(j) == 0.0) continue;
+            const double kr = j == 6 ? dr : L.ka[j][2 * n];
+            const double ki = j == 6 ? di : L.ka[j][2 * n + 1];
+            if (j & 1) {
+                r1 += dp_e(j) * kr;
+                i1 += dp_e(j) * ki;
+            } else {
+                r0 += dp_e(j) * kr;
+                i0 += dp_e(j) * ki;
+            }
+        }
+        // magnitudes in FP32: they only scale the error norm
+        en = fabsf((float)L.h) * hypotf((float)(r0 + r1), (float)(i0 + i1));
+        an = fmaxf(hypotf((float)L.a[2 * n], (float)L.a[2 * n + 1]),
+                   hypotf((float)L.as[2 * n], (float)L.as[2 * n + 1]));
     }
-    const double e1 = (double)emax / c.rtol;
-    const double e2 = ea / (c.rtol * fmax(c.a_ref, amax));
-    const double err = (e1 > e2 || e1 != e1) ? e1 : e2;
-    if (!isfinite(err)) {
-        L.status = CMX_ENAN;
-        L.done = 1;
+    // maxima over the mode lanes 0..MAXN-1 (lanes >= N hold 0); NaN propagates in the error
+#pragma unroll
+    for (int o = MAXN / 2; o > 0; o >>= 1) {
+        en = nanmax(en, __shfl_xor_sync(0xffffffffu, en, o));
+        an = fmaxf(an, __shfl_xor_sync(0xffffffffu, an, o));
     }
-    const int accepted = L.status == 0 && (L.replay || err <= 1.0);
-    const bool rec = tm.rank == 0;
-    const long long li = L.log_n;
-    L.attempts += 1;
-    L.launch_attempts += 1;
-    const double t0 = L.t;
-    double t1 = t0;
-    const double *as = L.as, *mm = L.mm;
-    if (accepted) {
-        t1 = L.last ? L.T : (L.at_split ? L.split_next : t0 + h);
-        // uniform trace: cubic Hermite for a_n (end slopes k1, k7), linear for <m^->_n
-        if (c.tr_cap > 0 && c.sample_dt > 0.0) {
+    // scaled error norm: magnet max-norm against rtol, cavity against rtol max(a_ref, |a|)
+    const float e1 = emax * L.inv_rtolf;
+    const float e2 = en / (L.rtolf * fmaxf(L.areff, an));
+    const float err = (e1 > e2 || e1 != e1) ? e1 : e2;
+    const bool finite = isfinite(err);
+    const int accepted = finite && L.status == 0 && (L.replay || err <= 1.f);
+    const double h = L.h, t0 = L.t;
+    __syncwarp();
+    if (lane == 0) {
+        L.attempts += 1;
+        L.launch_attempts += 1;
+        if (!finite) {
+            L.status = CMX_ENAN;
+            L.done = 1;
+        }
+        const double t1 = L.last ? L.T : (L.at_split ? L.split_next : t0 + h);
+        // uniform trace: cubic Hermite for a_n (end slopes k1, k7), linear for <m^->_n; it
+        // reads the state at t0, which the mode lanes replace only after this block
+        if (accepted && c.tr_cap > 0 && c.sample_dt > 0.0) {
             long long tn = L.trace_n;
             double ts = L.trace_next;
             while (tn < c.tr_cap && ts <= t1) {
@@ -329,8 +398,8 @@ __device__ void controller(const Ctx &c, const Team &tm, Local &L, const double 
                     c.tr_t[tn] = ts;
                     for (int q = 0; q < 2 * N; q++) {
                         c.tr_a[tn * 2 * N + q] = h00 * L.a[q] + h10 * h * L.ka[0][q] +
-                                                 h01 * as[q] + h11 * h * L.ka[6][q];
-                        c.tr_mm[tn * 2 * N + q] = (1 - th) * L.mm_n[q] + th * mm[q];
+                                                 h01 * L.as[q] + h11 * h * L.ka[6][q];
+                        c.tr_mm[tn * 2 * N + q] = (1 - th) * L.mm_n[q] + th * L.mm[q];
                     }
                 }
                 tn++;
@@ -339,62 +408,68 @@ __device__ void controller(const Ctx &c, const Team &tm, Local &L, const double 
             L.trace_n = tn;
             L.trace_next = ts;
         }
-        for (int q = 0; q < 2 * N; q++) {
-            L.a[q] = as[q];
-            L.ka[0][q] = L.ka[6][q];
-            L.mm_n[q] = mm[q];
+        if (rec && li < c.log_cap) {
+            cmx_step st;
+            st.t = accepted ? t1 : t0;
+            st.dt = h;
+            st.err = (double)err;
+            st.accepted = accepted;
+            st.pad = 0;
+            c.log[li] = st;
         }
-        const int k0 = L.kphys[0];
-        L.kphys[0] = L.kphys[6];
-        L.kphys[6] = k0;
-        L.mcur ^= 1;
-        L.t = t1;
-        L.accepted += 1;
-        if (L.at_split && t1 < L.T) {   // boundary reached: cavity step before the next interval
-            L.split_k += 1;
-            L.split_next = fmin(L.split_t0 + (double)(L.split_k + 1) * c.split_dt, L.T);
-            L.split_pending = 1;
-            L.k1_valid = 0;
-        }
-    }
-    if (rec && li < c.log_cap) {
-        cmx_step st;
-        st.t = accepted ? t1 : t0;
-        st.dt = h;
-        st.err = err;
-        st.accepted = accepted;
-        st.pad = 0;
-        c.log[li] = st;
-        if (accepted)
-            for (int q = 0; q < 2 * N; q++) {
-                c.log_a[li * 2 * N + q] = as[q];
-                c.log_mm[li * 2 * N + q] = mm[q];
-            }
-    }
-    L.log_n = li + 1;
-
-    if (L.replay) {
-        L.replay_pos += 1;
-        if (L.replay_pos >= L.replay_n) L.done = 1;
-    } else if (L.status == 0) {
-        // step factor in FP32 (FP64 pow has a very long latency here)
-        const float ef = (float)err;
-        double fac = ef > 0.f ? (double)(0.9f * powf(ef, -0.2f)) : 5.0;
-        fac = fmin(5.0, fmax(0.2, fac));
+        L.log_n = li + 1;
+        L.rhs_evals += 1;
         if (accepted) {
-            if (L.last_rejected && fac > 1.0) fac = 1.0;
-            L.last_rejected = 0;
-            L.dt = fmin(h * fac, c.dt_max);
-        } else {
-            L.last_rejected = 1;
-            L.dt = h * fac;
-            if (L.dt < c.dt_min) {
-                L.status = CMX_ESTEPFAIL;
-                L.done = 1;
+            const int k0 = L.kphys[0];
+            L.kphys[0] = L.kphys[6];
+            L.kphys[6] = k0;
+            L.mcur ^= 1;
+            L.t = t1;
+            L.accepted += 1;
+            if (L.at_split && t1 < L.T) {   // boundary reached: cavity step before the next interval
+                L.split_k += 1;
+                L.split_next = fmin(L.split_t0 + (double)(L.split_k + 1) * c.split_dt, L.T);
+                L.split_pending = 1;
+                L.k1_valid = 0;
             }
         }
+        if (L.replay) {
+            L.replay_pos += 1;
+            if (L.replay_pos >= L.replay_n) L.done = 1;
+        } else if (L.status == 0) {
+            // step factor in FP32 (FP64 pow has a very long latency here)
+            double fac = err > 0.f ? (double)(0.9f * powf(err, -0.2f)) : 5.0;
+            fac = fmin(5.0, fmax(0.2, fac));
+            if (accepted) {
+                if (L.last_rejected && fac > 1.0) fac = 1.0;
+                L.last_rejected = 0;
+                L.dt = fmin(h * fac, c.dt_max);
+            } else {
+                L.last_rejected = 1;
+                L.dt = h * fac;
+                if (L.dt < c.dt_min) {
+                    L.status = CMX_ESTEPFAIL;
+                    L.done = 1;
+                }
+            }
+        }
+        if (L.t >= L.T || L.launch_attempts >= L.max_launch_attempts) L.done = 1;
     }
-    if (L.t >= L.T || L.launch_attempts >= L.max_launch_attempts) L.done = 1;
+    __syncwarp();
+    if (mt && accepted) {   // the accepted step's state, FSAL slope and log entry of mode n
+        if (rec && li < c.log_cap) {
+            c.log_a[li * 2 * N + 2 * n] = L.as[2 * n];
+            c.log_a[li * 2 * N + 2 * n + 1] = L.as[2 * n + 1];
+            c.log_mm[li * 2 * N + 2 * n] = mr;
+            c.log_mm[li * 2 * N + 2 * n + 1] = mi;
+        }
+        L.a[2 * n] = L.as[2 * n];
+        L.a[2 * n + 1] = L.as[2 * n + 1];
+        L.ka[0][2 * n] = dr;
+        L.ka[0][2 * n + 1] = di;
+        L.mm_n[2 * n] = mr;
+        L.mm_n[2 * n + 1] = mi;
+    }
 }
 
 // Block sum of the per-thread overlap accumulators (compensated pairs, fixed shuffle order)
@@ -449,27 +524,6 @@ __device__ __forceinline__ void red_add_release(unsigned *p, unsigned v)
     asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-// After the barrier: the grid sums of set `set`, identical for every block.  The team's rank 0
-// then clears the set that stage count + 2 will use (every block has finished reading it: it
-// was read before the arrival at this barrier).
-template <class SM>
-__device__ void grid_reduce(const Ctx &c, const Team &tm, SM &sm, double *out, float *emax, int set)
-{
-    const int Q = 2 * c.nmodes;
-    volatile Ctl *g = c.ctl;
-    if ((int)threadIdx.x < Q) out[threadIdx.x] = (double)g->racc[set][threadIdx.x] / c.red_scale;
-    if ((int)threadIdx.x == Q) {
-        const unsigned bits = g->remax[set];
-        *emax = g->range_error ? __int_as_float(0x7fffffff) : __uint_as_float(bits);
-    }
-    if (tm.rank == 0) {
-        const int clr = (set + 2) % 3;
-        if ((int)threadIdx.x < Q) g->racc[clr][threadIdx.x] = 0;
-        if ((int)threadIdx.x == Q) g->remax[clr] = 0u;
-    }
-    __syncthreads();
-}
-
 // Team barrier: every block of the team adds 1 to a monotonic arrival counter with release
 // semantics and polls it with acquire loads until all blocks of this barrier have arrived.
 // Waits are bounded by c.timeout_ns: on time-out the block sets CMX_ETIMEOUT and the run stops.
@@ -522,14 +576,18 @@ __device__ __forceinline__ const float *slope_buffer(const Ctx &c, int kj)
 }
 
 // One stage.  If `begun`, the copy pipeline of this stage was started by the previous stage
-// (right after its barrier).  After the barrier this stage starts the next one (S < 7) before
-// it reduces the partials and updates the cavity, so those latencies overlap the first copies.
+// (right after its barrier), which also formed this stage's cavity value; the first two stages
+// of an attempt form it here (and at stage 2 the FP32 coefficients of the whole attempt).
+// After the barrier the mode threads read the grid sums of set `set` (identical for every
+// block), this stage starts the next one's copies (S < 7), so that the read latency and the
+// controller overlap the first copies, and warp 0 runs the controller.  The team's rank 0
+// clears the set that stage count + 2 will use: every block read it before arriving at this
+// barrier.
 template <int S, class SM>
-__device__ bool run_stage(const Ctx &c, const Team &tm, SM &sm, Local &L, Coef &cf,
-                          double *s_sum, float *s_emax, Pipe &pp, bool begun)
+__device__ bool run_stage(const Ctx &c, const Team &tm, SM &sm, Local &L, Coef &cf, Pipe &pp,
+                          bool begun)
 {
     const int tid = threadIdx.x, N = c.nmodes;
-    const double h = L.h;
     const float *mn = L.mcur ? c.m[1] : c.m[0];
     float *mnew = L.mcur ? c.m[0] : c.m[1];
     if (!begun) {
@@ -537,22 +595,12 @@ __device__ bool run_stage(const Ctx &c, const Team &tm, SM &sm, Local &L, Coef &
         __syncthreads();
         stage_begin<S>(c, sm, mn, pp);
     }
-    // cavity stage value a_S = a_n + h sum_j a_Sj k^a_j (FP64, one thread per real component)
-    if (tid < 2 * N) {
-        double v = L.a[tid];
-#pragma unroll
-        for (int j = 0; j < S - 1; j++)
-            if (dp_a(S - 1, j) != 0.0) v += h * dp_a(S - 1, j) * L.ka[j][tid];
-        L.as[tid] = v;
+    if (S <= 2) {
+        if (tid < N) cavity_stage_value<S>(c, L, cf, tid);
+        if (S == 2 && tid >= 32 && tid < 32 + 36) attempt_coefficients(cf, L.h, tid - 32);
+        if (S == 2 && tid == 96) cf.h = (float)L.h;
+        __syncthreads();
     }
-    if (tid >= 32 && tid < 38) cf.cf[tid - 32] = (float)(h * (tid - 32 < S - 1 ? dp_a(S - 1, tid - 32) : 0.0));
-    if (tid >= 64 && tid < 71) cf.e[tid - 64] = (float)dp_e(tid - 64);
-    if (tid == 96) cf.h = (float)h;
-    __syncthreads();
-    if (tid < N)
-        cf.hrf[tid] = (float)(c.two_over_gamma * (L.mc[MC * tid + 4] * L.as[2 * tid] -
-                                                  L.mc[MC * tid + 5] * L.as[2 * tid + 1]));
-    __syncthreads();
     Acc acc;
 #pragma unroll
     for (int n = 0; n < MAXN; n++) acc.re[n] = acc.im[n] = 0.f;
@@ -565,9 +613,27 @@ __device__ bool run_stage(const Ctx &c, const Team &tm, SM &sm, Local &L, Coef &
     const int set = (int)(L.rhs_evals % 3);
     block_reduce(c, tm, sm, acc, set);
     if (!grid_barrier<SM>(c, tm, L, S)) return false;
+    long long sre = 0, sim = 0;
+    float emax = 0.f;
+    {
+        const volatile Ctl *g = c.ctl;
+        if (tid < N) {
+            sre = g->racc[set][2 * tid];
+            sim = g->racc[set][2 * tid + 1];
+        }
+        if (S == 7 && tid < 32) {
+            const unsigned bits = g->remax[set];
+            emax = g->range_error ? __int_as_float(0x7fffffff) : __uint_as_float(bits);
+        }
+        if (tm.rank == 0 && tid >= 32 && tid <= 32 + 2 * N) {
+            volatile Ctl *w = c.ctl;
+            const int clr = (set + 2) % 3, q = tid - 32;
+            if (q < 2 * N) w->racc[clr][q] = 0;
+            else w->remax[clr] = 0u;
+        }
+    }
     if (S >= 2 && S < 7 && !c.stage_only) stage_begin<(S < 7 ? S + 1 : 7)>(c, sm, mn, pp);
-    grid_reduce(c, tm, sm, s_sum, s_emax, set);
-    controller<S>(c, tm, L, s_sum, *s_emax);
+    controller<S>(c, tm, L, cf, sre, sim, emax);
     __syncthreads();
     return true;
 }
@@ -577,10 +643,16 @@ __device__ bool run_stage(const Ctx &c, const Team &tm, SM &sm, Local &L, Coef &
 // problem is done (t >= T, replay end, attempt budget of the launch, or an error).  The team's
 // rank-0 block writes the state back.  Returns false if the run stopped on a device error.
 template <class SM>
-__device__ bool integrate(const Ctx &c, const Team &tm, SM &sm, Local &L, Coef &cf,
-                          double *s_sum, float &s_emax, int &s_stop)
+__device__ bool integrate(const Ctx &c, const Team &tm, SM &sm, Local &L, Coef &cf, int &s_stop)
 {
-    if (threadIdx.x == 0) load_local(c, L);
+    if (threadIdx.x == 0) {
+        load_local(c, L);
+        L.rs = c.inv_nmag / c.red_scale;   // exact: the scale is a power of two
+        L.rtolf = (float)c.rtol;
+        L.inv_rtolf = (float)(1.0 / c.rtol);
+        L.areff = (float)c.a_ref;
+    }
+    if (threadIdx.x >= 32 && threadIdx.x < 39) cf.e[threadIdx.x - 32] = (float)dp_e(threadIdx.x - 32);
     if (threadIdx.x < c.nmodes) mode_constants(c, threadIdx.x, L.mc + MC * threadIdx.x);
     {
         const int sb = __ldg(&c.seg_begin[tm.rank]), se = __ldg(&c.seg_begin[tm.rank + 1]);
@@ -601,17 +673,17 @@ __device__ bool integrate(const Ctx &c, const Team &tm, SM &sm, Local &L, Coef &
         __syncthreads();
         if (s_stop) break;
         while (!L.k1_valid) {   // twice at an operator-split boundary (see controller<1>)
-            if (!(ok = run_stage<1>(c, tm, sm, L, cf, s_sum, &s_emax, pp, false)))
+            if (!(ok = run_stage<1>(c, tm, sm, L, cf, pp, false)))
                 break;
             if (c.stage_only) break;
         }
         if (!ok || c.stage_only) break;
-        if (!(ok = run_stage<2>(c, tm, sm, L, cf, s_sum, &s_emax, pp, false))) break;
-        if (!(ok = run_stage<3>(c, tm, sm, L, cf, s_sum, &s_emax, pp, true))) break;
-        if (!(ok = run_stage<4>(c, tm, sm, L, cf, s_sum, &s_emax, pp, true))) break;
-        if (!(ok = run_stage<5>(c, tm, sm, L, cf, s_sum, &s_emax, pp, true))) break;
-        if (!(ok = run_stage<6>(c, tm, sm, L, cf, s_sum, &s_emax, pp, true))) break;
-        if (!(ok = run_stage<7>(c, tm, sm, L, cf, s_sum, &s_emax, pp, true))) break;
+        if (!(ok = run_stage<2>(c, tm, sm, L, cf, pp, false))) break;
+        if (!(ok = run_stage<3>(c, tm, sm, L, cf, pp, true))) break;
+        if (!(ok = run_stage<4>(c, tm, sm, L, cf, pp, true))) break;
+        if (!(ok = run_stage<5>(c, tm, sm, L, cf, pp, true))) break;
+        if (!(ok = run_stage<6>(c, tm, sm, L, cf, pp, true))) break;
+        if (!(ok = run_stage<7>(c, tm, sm, L, cf, pp, true))) break;
     }
     if (ok && tm.rank == 0 && threadIdx.x == 0) store_local(c, L);
     __syncthreads();

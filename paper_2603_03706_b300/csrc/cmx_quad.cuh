@@ -326,7 +326,7 @@ __device__ void stage_run(const Ctx &c, QuadSmem<HU> &sm, float *kout, const flo
                 for (int a = 1; a < NA; a++) {
                     const int j = array_slope(S, a);
                     const float4 kj = src[(size_t)(a * 3 + k) * nt];
-                    if (dp_a(S - 1, j) != 0.0) acc4 = f4fma(cf.cf[j], kj, acc4);
+                    if (dp_a(S - 1, j) != 0.0) acc4 = f4fma(cf.cf[S - 1][j], kj, acc4);
                     if (S == 7 && dp_e(j) != 0.0) e4 = f4fma(cf.e[j], kj, e4);
                 }
             }

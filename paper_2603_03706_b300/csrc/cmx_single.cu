@@ -19,11 +19,9 @@ __global__ void __launch_bounds__(WX *WY, (MinBlocks<NS, WX * WY>::value)) run_k
     auto &sm = *reinterpret_cast<StageSmem<NS, WX, WY, HU> *>(smem_raw);
     __shared__ Local L;
     __shared__ Coef cf;
-    __shared__ double s_sum[2 * MAXN];
-    __shared__ float s_emax;
     __shared__ int s_stop;
     const Team tm{(int)blockIdx.x, (int)gridDim.x, &c.ctl->bar_count};
-    integrate(c, tm, sm, L, cf, s_sum, s_emax, s_stop);
+    integrate(c, tm, sm, L, cf, s_stop);
 }
 
 // Quad windows (one sublattice): wq x wy threads, four x-cells each; one block per SM.
@@ -34,11 +32,9 @@ __global__ void __launch_bounds__(QMAX_NT, 1) run_kernel_quad(Ctx c, int wq, int
     QuadSmem<HU> sm = quad_smem<HU>(smem_raw, wq, wy, c.nmodes);
     __shared__ Local L;
     __shared__ Coef cf;
-    __shared__ double s_sum[2 * MAXN];
-    __shared__ float s_emax;
     __shared__ int s_stop;
     const Team tm{(int)blockIdx.x, (int)gridDim.x, &c.ctl->bar_count};
-    integrate(c, tm, sm, L, cf, s_sum, s_emax, s_stop);
+    integrate(c, tm, sm, L, cf, s_stop);
 }
 
 // ---------------------------------------------------------------------------------------------

@@ -213,10 +213,11 @@ struct Acc {
     float emax;
 };
 
-// FP32 stage coefficients: cf[j] = h a_Sj, e[j] = E_j, h, and the feedback field per unit
-// profile of each mode, hrf[n] = (2/gamma) Re[g~_n a_{n,S}] (Eq. (5), (13)).
+// FP32 stage coefficients of the current attempt: cf[S-1][j] = h a_Sj for every stage S, e[j] =
+// E_j, h, and the feedback field per unit profile of each mode at the current stage,
+// hrf[n] = (2/gamma) Re[g~_n a_{n,S}] (Eq. (5), (13)).
 struct Coef {
-    float cf[6];
+    float cf[7][6];
     float e[7];
     float h;
     float hrf[MAXN];
@@ -291,7 +292,7 @@ __device__ __forceinline__ void combine_plane(const Ctx &c, StageSmem<NS, WX, WY
             for (int a = 1; a < NA; a++) {
                 const int j = array_slope(S, a);
                 const float kj = rp[(a * NQ + k) * W + i];
-                if (dp_a(S - 1, j) != 0.0) acc = fmaf(cf.cf[j], kj, acc);
+                if (dp_a(S - 1, j) != 0.0) acc = fmaf(cf.cf[S - 1][j], kj, acc);
                 if (S == 7 && dp_e(j) != 0.0) es = fmaf(cf.e[j], kj, es);
             }
         }
