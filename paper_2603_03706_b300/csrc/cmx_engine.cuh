@@ -24,6 +24,9 @@ struct Team {
     unsigned *bar;
 };
 
+// Per-component cavity constants: LC doubles per real component (see component_constants).
+constexpr int LC = 7;
+
 // Block-local copy of the integrator state.
 struct Local {
     double t, dt, T, h;
@@ -39,8 +42,11 @@ struct Local {
     const double *replay_dts;
     double mm[2 * MAXN], as[2 * MAXN];   // overlaps and cavity stage value of this stage
     double mc[MC * MAXN];                // mode constants (see MC)
+    double lc[LC][2 * MAXN];             // per-component cavity constants (component_constants)
+    double hw[7][6];                     // h a_Sj of the current attempt (rows S-1 = 2..6)
     double rs;                           // fixed-point overlap sum -> <m^->: 1 / (scale N_c)
     float rtolf, inv_rtolf, areff;       // error-norm constants in FP32
+    int has_kerr, has_split;
     unsigned bar_target;                 // arrival count that completes the next barrier
     int skip_block;
     int kphys[7];
@@ -207,36 +213,60 @@ static __device__ __noinline__ void split_cavity_step(const Ctx &c, Local &L, co
     for (int q = 0; q < 2 * N; q++) L.a[q] = a0[q] + h / 6.0 * acc[q];
 }
 
-// Cavity value a_S of mode n (both components) for stage S of the current attempt and its
-// feedback coefficient hrf_n = (2/gamma) Re[gb~_n a_{n,S}] (Eq. (5), (13)), from the slopes of
-// the earlier stages; run by mode thread n.  Even and odd slopes go into separate partial sums,
-// which halves the dependent FP64 chain.
-template <int S>
-__device__ __forceinline__ void cavity_stage_value(const Ctx &c, Local &L, Coef &cf, int n)
+// Cavity constants of real component q = 2n + c of mode n (c = 0: real part, 1: imaginary
+// part), with the sign s = +1 / -1 of the component folded in.  Lane q then forms its component
+// of the slope of Eq. (12), (19) with the self-Kerr term from its own and its partner's values,
+//     d_q = -kappa x + s (w + K |a|^2) x' - s g_r y' - g_i y,
+// x, x' the cavity values and y, y' the overlaps of lane q and of its partner q ^ 1.  lc[5] is
+// the lane's share of the feedback coefficient (2/gamma) Re[gb~ a] (pair sum of lc[5] x) and
+// lc[6] the drive amplitude of the component.
+__device__ __forceinline__ void component_constants(const Ctx &c, int q, Local &L)
 {
-    const double h = L.h;
-    double r0 = L.a[2 * n], i0 = L.a[2 * n + 1], r1 = 0.0, i1 = 0.0;
+    double v[MC];
+    mode_constants(c, q >> 1, v);
+    const int n = q >> 1;
+    double dre = c.drive_re[0], dim = c.drive_im[0];
 #pragma unroll
-    for (int j = 0; j < S - 1; j++) {
-        if (dp_a(S - 1, j) == 0.0) continue;
-        const double w = h * dp_a(S - 1, j);
-        if (j & 1) {
-            r1 += w * L.ka[j][2 * n];
-            i1 += w * L.ka[j][2 * n + 1];
-        } else {
-            r0 += w * L.ka[j][2 * n];
-            i0 += w * L.ka[j][2 * n + 1];
+    for (int u = 1; u < MAXN; u++)
+        if (n == u) {
+            dre = c.drive_re[u];
+            dim = c.drive_im[u];
         }
-    }
-    const double vr = r0 + r1, vi = i0 + i1;
-    L.as[2 * n] = vr;
-    L.as[2 * n + 1] = vi;
-    cf.hrf[n] = (float)(c.two_over_gamma * (L.mc[MC * n + 4] * vr - L.mc[MC * n + 5] * vi));
+    const bool im = q & 1;
+    L.lc[0][q] = -v[1];
+    L.lc[1][q] = im ? -v[0] : v[0];
+    L.lc[2][q] = im ? v[2] : -v[2];
+    L.lc[3][q] = -v[3];
+    L.lc[4][q] = im ? -v[6] : v[6];
+    L.lc[5][q] = c.two_over_gamma * (im ? -v[5] : v[4]);
+    L.lc[6][q] = im ? dim : dre;
 }
 
-// The FP32 stage coefficients h a_Sj of the whole attempt, entry q of rows S = 2..7, run by 36
-// threads once the attempt's size is known (the coefficient is selected, then multiplied once).
-__device__ __forceinline__ void attempt_coefficients(Coef &cf, double h, int q)
+// Cavity value a_S of stage S of the current attempt, one real component per lane of warp 0
+// (lane q < 2N when `own`), and the feedback coefficient of each mode, hrf_n = (2/gamma)
+// Re[gb~_n a_{n,S}] (Eq. (5), (13)), as the sum over the mode's two lanes.  Called by all lanes
+// of warp 0.  One FP64 instruction per slope: the weights h a_Sj come from the attempt's table.
+template <int S>
+__device__ __forceinline__ void cavity_stage_value(Local &L, Coef &cf, int q, bool own)
+{
+    double v = 0.0;
+    if (own) {
+        v = L.a[q];
+#pragma unroll
+        for (int j = 0; j < S - 1; j++)
+            if (dp_a(S - 1, j) != 0.0)
+                v += (S == 2 ? L.h * dp_a(1, 0) : L.hw[S - 1][j]) * L.ka[j][q];
+        L.as[q] = v;
+    }
+    double p = own ? L.lc[5][q] * v : 0.0;
+    p += __shfl_xor_sync(0xffffffffu, p, 1);
+    if (own && !(q & 1)) cf.hrf[q >> 1] = (float)p;
+}
+
+// The weights h a_Sj of the whole attempt, entry q of rows S = 2..7, in FP64 for the cavity and
+// FP32 for the magnet's stage combination; run by 36 threads once the attempt's size is known
+// (the coefficient is selected, then multiplied once).
+__device__ __forceinline__ void attempt_coefficients(Coef &cf, Local &L, double h, int q)
 {
     double a = 0.0;
 #pragma unroll
@@ -244,95 +274,83 @@ __device__ __forceinline__ void attempt_coefficients(Coef &cf, double h, int q)
 #pragma unroll
         for (int j = 0; j < 6; j++)
             if (q == (s - 1) * 6 + j) a = dp_a(s, j);
-    cf.cf[1 + q / 6][q % 6] = (float)(h * a);
+    const double w = h * a;
+    L.hw[1 + q / 6][q % 6] = w;
+    cf.cf[1 + q / 6][q % 6] = (float)w;
 }
 
-// Work after the barrier of stage S, on warp 0 (the caller's block barrier follows).  Mode
-// thread n (lane n < N) owns mode n: from its grid sums (fixed point: sre, sim) it forms the
-// overlap <m^->_n (Eq. (18)), the cavity slope (Eq. (12), (19), with the drive and the Kerr
-// term), the adjoint stores of its components and, before stage 7, the next stage's cavity
-// value and feedback coefficient.  After stage 7 the lanes take the scaled error norm (FP32,
-// warp maximum over the modes) and the accept decision, each lane the same, and update their
-// own components of the state; lane 0 keeps the scalar part (time, counters, step size, log).
-// Only the team's rank 0 writes log, trace and adjoint stores.  FP64 has a long dependent
-// latency on this GPU, so this part runs without block barriers and with short FP64 chains.
+// Work after the barrier of stage S, on warp 0 (the caller's block barrier follows).  Lane
+// q < 2N owns real component q = 2n + c of mode n: from its grid sum (fixed point, `sq`) it
+// forms its component of the overlap <m^->_n (Eq. (18)) and of the cavity slope (Eq. (12),
+// (19), with the drive and the Kerr term), its adjoint stores and, before stage 7, its component
+// of the next stage's cavity value.  After stage 7 the lanes take the scaled error norm (FP32,
+// warp maximum) and the accept decision, each lane the same, and update their own components of
+// the state; lane 0 keeps the scalar part (time, counters, step size, log).  Only the team's
+// rank 0 writes log, trace and adjoint stores.  An FP64 warp instruction occupies the FP64 pipe
+// for tens of cycles on this GPU whatever the number of active lanes, so the part is written
+// for few FP64 instructions (one component per lane, per-lane constants, no block barrier).
 template <int S>
-__device__ void controller(const Ctx &c, const Team &tm, Local &L, Coef &cf, long long sre,
-                           long long sim, float emax)
+__device__ void controller(const Ctx &c, const Team &tm, Local &L, Coef &cf, long long sq,
+                           float emax)
 {
     const int N = c.nmodes;
-    const int lane = threadIdx.x;
-    if (lane >= 32) return;
-    const int n = lane;
-    const bool mt = n < N;
+    const int q = threadIdx.x;
+    if (q >= 32) return;
+    const bool own = q < 2 * N;
     const bool rec = tm.rank == 0;
     const long long li = L.log_n;
-    double mr = 0.0, mi = 0.0, dr = 0.0, di = 0.0;
-    if (mt) {
-        mr = (double)sre * L.rs;
-        mi = (double)sim * L.rs;
-        cavity_rhs(L.mc, n, L.as[2 * n], L.as[2 * n + 1], mr, mi, dr, di);
-        if (c.split_dt > 0.0 && !L.replay) {   // operator split: cavity held during magnet steps
-            dr = 0.0;
-            di = 0.0;
+    const double y = own ? (double)sq * L.rs : 0.0;
+    const double yo = __shfl_xor_sync(0xffffffffu, y, 1);
+    double d = 0.0;
+    if (own) {
+        const double x = L.as[q], xo = L.as[q ^ 1];
+        double t = L.lc[1][q];
+        if (L.has_kerr) t = fma(L.lc[4][q], fma(x, x, xo * xo), t);
+        d = L.lc[0][q] * x;
+        d = fma(t, xo, d);
+        d = fma(L.lc[2][q], yo, d);
+        d = fma(L.lc[3][q], y, d);
+        if (L.has_split && !L.replay) {   // operator split: cavity held during magnet steps
+            d = 0.0;
         } else if (c.has_drive) {   // the drive at this stage's time t + c_S h
             const double ts = S == 1 ? L.t : L.t + dp_c(S - 1) * L.h;
-            const double x = (ts - c.drive_t0) * c.drive_inv_sigma;
-            const double env = exp(-0.5 * x * x);
-            double er = c.drive_re[0], ei = c.drive_im[0];
-#pragma unroll
-            for (int u = 1; u < MAXN; u++)
-                if (n == u) {
-                    er = c.drive_re[u];
-                    ei = c.drive_im[u];
-                }
-            dr += er * env;
-            di += ei * env;
+            const double xe = (ts - c.drive_t0) * c.drive_inv_sigma;
+            d += L.lc[6][q] * exp(-0.5 * xe * xe);
         }
-        L.mm[2 * n] = mr;
-        L.mm[2 * n + 1] = mi;
-        L.ka[S - 1][2 * n] = dr;
-        L.ka[S - 1][2 * n + 1] = di;
+        L.mm[q] = y;
+        L.ka[S - 1][q] = d;
         if (rec) {
             // adjoint stores: a rejected attempt's checkpoint is overwritten by the accepted retry
             const int slot = checkpoint_slot<S>(c, L);
             if (slot >= 0 && c.traj_a) {
-                double *d = c.traj_a + (size_t)slot * traj_stride(N);
-                d[2 * n] = S == 7 ? L.as[2 * n] : L.a[2 * n];
-                d[2 * n + 1] = S == 7 ? L.as[2 * n + 1] : L.a[2 * n + 1];
-                d[2 * N + 2 * n] = dr;
-                d[2 * N + 2 * n + 1] = di;
-                d[4 * N + 2 * n] = mr;
-                d[4 * N + 2 * n + 1] = mi;
-                if (n == 0) d[6 * N] = S == 7 ? (L.last ? L.T : L.t + L.h) : L.t;
+                double *dd = c.traj_a + (size_t)slot * traj_stride(N);
+                dd[q] = S == 7 ? L.as[q] : L.a[q];
+                dd[2 * N + q] = d;
+                dd[4 * N + q] = y;
+                if (q == 0) dd[6 * N] = S == 7 ? (L.last ? L.T : L.t + L.h) : L.t;
             }
             if (c.rec_a && L.replay && L.replay_pos < c.rec_steps) {
-                double *d = c.rec_a + ((size_t)L.replay_pos * 7 + (S - 1)) * 4 * N;
-                d[2 * n] = L.as[2 * n];
-                d[2 * n + 1] = L.as[2 * n + 1];
-                d[2 * N + 2 * n] = mr;
-                d[2 * N + 2 * n + 1] = mi;
+                double *dd = c.rec_a + ((size_t)L.replay_pos * 7 + (S - 1)) * 4 * N;
+                dd[q] = L.as[q];
+                dd[2 * N + q] = y;
             }
         }
-        if (S == 1) {
-            L.mm_n[2 * n] = mr;
-            L.mm_n[2 * n + 1] = mi;
-        }
-        if (S >= 2 && S < 7) cavity_stage_value<(S < 7 ? S + 1 : 7)>(c, L, cf, n);
+        if (S == 1) L.mm_n[q] = y;
     }
+    if (S >= 2 && S < 7) cavity_stage_value<(S < 7 ? S + 1 : 7)>(L, cf, q, own);
     if (S != 7) {
-        if (lane == 0) {
+        if (q == 0) {
             L.rhs_evals += 1;
             if (S == 1) {
                 L.k1_valid = 1;
                 if (c.stage_only) L.done = 1;
             }
         }
-        if (S == 1 && c.split_dt > 0.0 && L.split_pending && !c.stage_only && !L.replay) {
+        if (S == 1 && L.has_split && L.split_pending && !c.stage_only && !L.replay) {
             // cavity step over the coming interval with the overlaps of the current m; the
             // slope just computed used the old feedback field: evaluate stage 1 again
             __syncwarp();
-            if (lane == 0) {
+            if (q == 0) {
                 split_cavity_step(c, L, L.mm);
                 L.split_pending = 0;
                 L.k1_valid = 0;
@@ -341,31 +359,22 @@ __device__ void controller(const Ctx &c, const Team &tm, Local &L, Coef &cf, lon
         return;
     }
 
-    // stage 7: error estimate of mode n (even and odd weights in separate partial sums)
-    float en = 0.f, an = 0.f;
-    if (mt) {
-        double r0 = 0.0, i0 = 0.0, r1 = 0.0, i1 = 0.0;
+    // stage 7: error estimate of the lane's component; magnitudes in FP32 (they only scale the
+    // error norm), maxima over lanes 0 .. 2 MAXN - 1 (lanes >= 2N hold 0, NaN propagates)
+    double e = 0.0;
+    if (own) {
 #pragma unroll
-        for (int j = 0; j < 7; j++) {
-            if (dp_e(j) == 0.0) continue;
-            const double kr = j == 6 ? dr : L.ka[j][2 * n];
-            const double ki = j == 6 ? di : L.ka[j][2 * n + 1];
-            if (j & 1) {
-                r1 += dp_e(j) * kr;
-                i1 += dp_e(j) * ki;
-            } else {
-                r0 += dp_e(j) * kr;
-                i0 += dp_e(j) * ki;
-            }
-        }
-        // magnitudes in FP32: they only scale the error norm
-        en = fabsf((float)L.h) * hypotf((float)(r0 + r1), (float)(i0 + i1));
-        an = fmaxf(hypotf((float)L.a[2 * n], (float)L.a[2 * n + 1]),
-                   hypotf((float)L.as[2 * n], (float)L.as[2 * n + 1]));
+        for (int j = 0; j < 7; j++)
+            if (dp_e(j) != 0.0) e += dp_e(j) * (j == 6 ? d : L.ka[j][q]);
     }
-    // maxima over the mode lanes 0..MAXN-1 (lanes >= N hold 0); NaN propagates in the error
+    const float ef = (float)e, af = own ? (float)L.a[q] : 0.f, sf = own ? (float)L.as[q] : 0.f;
+    const float efo = __shfl_xor_sync(0xffffffffu, ef, 1);
+    const float afo = __shfl_xor_sync(0xffffffffu, af, 1);
+    const float sfo = __shfl_xor_sync(0xffffffffu, sf, 1);
+    float en = own ? cf.h * hypotf(ef, efo) : 0.f;
+    float an = own ? fmaxf(hypotf(af, afo), hypotf(sf, sfo)) : 0.f;
 #pragma unroll
-    for (int o = MAXN / 2; o > 0; o >>= 1) {
+    for (int o = MAXN; o > 0; o >>= 1) {
         en = nanmax(en, __shfl_xor_sync(0xffffffffu, en, o));
         an = fmaxf(an, __shfl_xor_sync(0xffffffffu, an, o));
     }
@@ -377,7 +386,7 @@ __device__ void controller(const Ctx &c, const Team &tm, Local &L, Coef &cf, lon
     const int accepted = finite && L.status == 0 && (L.replay || err <= 1.f);
     const double h = L.h, t0 = L.t;
     __syncwarp();
-    if (lane == 0) {
+    if (q == 0) {
         L.attempts += 1;
         L.launch_attempts += 1;
         if (!finite) {
@@ -386,7 +395,7 @@ __device__ void controller(const Ctx &c, const Team &tm, Local &L, Coef &cf, lon
         }
         const double t1 = L.last ? L.T : (L.at_split ? L.split_next : t0 + h);
         // uniform trace: cubic Hermite for a_n (end slopes k1, k7), linear for <m^->_n; it
-        // reads the state at t0, which the mode lanes replace only after this block
+        // reads the state at t0, which the lanes replace only after this block
         if (accepted && c.tr_cap > 0 && c.sample_dt > 0.0) {
             long long tn = L.trace_n;
             double ts = L.trace_next;
@@ -396,10 +405,10 @@ __device__ void controller(const Ctx &c, const Team &tm, Local &L, Coef &cf, lon
                 const double h01 = (3 - 2 * th) * th * th, h11 = (th - 1) * th * th;
                 if (rec) {
                     c.tr_t[tn] = ts;
-                    for (int q = 0; q < 2 * N; q++) {
-                        c.tr_a[tn * 2 * N + q] = h00 * L.a[q] + h10 * h * L.ka[0][q] +
-                                                 h01 * L.as[q] + h11 * h * L.ka[6][q];
-                        c.tr_mm[tn * 2 * N + q] = (1 - th) * L.mm_n[q] + th * L.mm[q];
+                    for (int k = 0; k < 2 * N; k++) {
+                        c.tr_a[tn * 2 * N + k] = h00 * L.a[k] + h10 * h * L.ka[0][k] +
+                                                 h01 * L.as[k] + h11 * h * L.ka[6][k];
+                        c.tr_mm[tn * 2 * N + k] = (1 - th) * L.mm_n[k] + th * L.mm[k];
                     }
                 }
                 tn++;
@@ -435,13 +444,14 @@ __device__ void controller(const Ctx &c, const Team &tm, Local &L, Coef &cf, lon
         }
         if (L.replay) {
             L.replay_pos += 1;
-            if (L.replay_pos >= L.replay_n) L.done = 1;
+            if (L.replay_pos >= L.replay_n || L.t >= L.T) L.done = 1;
         } else if (L.status == 0) {
-            // step factor in FP32 (FP64 pow has a very long latency here)
-            double fac = err > 0.f ? (double)(0.9f * powf(err, -0.2f)) : 5.0;
-            fac = fmin(5.0, fmax(0.2, fac));
+            // step factor 0.9 err^(-1/5) clamped to [0.2, 5], in FP32 (FP64 pow has a very long
+            // latency here); the clamp bounds themselves are exact in FP64
+            const float ff = err > 0.f ? 0.9f * powf(err, -0.2f) : 5.f;
+            double fac = ff >= 5.f ? 5.0 : (ff < 0.2f ? 0.2 : (double)ff);
             if (accepted) {
-                if (L.last_rejected && fac > 1.0) fac = 1.0;
+                if (L.last_rejected && ff > 1.f) fac = 1.0;
                 L.last_rejected = 0;
                 L.dt = fmin(h * fac, c.dt_max);
             } else {
@@ -453,22 +463,18 @@ __device__ void controller(const Ctx &c, const Team &tm, Local &L, Coef &cf, lon
                 }
             }
         }
-        if (L.t >= L.T || L.launch_attempts >= L.max_launch_attempts) L.done = 1;
+        // t reaches T only through an accepted last step (attempt_size lands it on T)
+        if ((accepted && L.last) || L.launch_attempts >= L.max_launch_attempts) L.done = 1;
     }
     __syncwarp();
-    if (mt && accepted) {   // the accepted step's state, FSAL slope and log entry of mode n
+    if (own && accepted) {   // the accepted step's state, FSAL slope and log entry of component q
         if (rec && li < c.log_cap) {
-            c.log_a[li * 2 * N + 2 * n] = L.as[2 * n];
-            c.log_a[li * 2 * N + 2 * n + 1] = L.as[2 * n + 1];
-            c.log_mm[li * 2 * N + 2 * n] = mr;
-            c.log_mm[li * 2 * N + 2 * n + 1] = mi;
+            c.log_a[li * 2 * N + q] = L.as[q];
+            c.log_mm[li * 2 * N + q] = y;
         }
-        L.a[2 * n] = L.as[2 * n];
-        L.a[2 * n + 1] = L.as[2 * n + 1];
-        L.ka[0][2 * n] = dr;
-        L.ka[0][2 * n + 1] = di;
-        L.mm_n[2 * n] = mr;
-        L.mm_n[2 * n + 1] = mi;
+        L.a[q] = L.as[q];
+        L.ka[0][q] = d;
+        L.mm_n[q] = y;
     }
 }
 
@@ -577,8 +583,8 @@ __device__ __forceinline__ const float *slope_buffer(const Ctx &c, int kj)
 
 // One stage.  If `begun`, the copy pipeline of this stage was started by the previous stage
 // (right after its barrier), which also formed this stage's cavity value; the first two stages
-// of an attempt form it here (and at stage 2 the FP32 coefficients of the whole attempt).
-// After the barrier the mode threads read the grid sums of set `set` (identical for every
+// of an attempt form it here (and at stage 2 the weights h a_Sj of the whole attempt).
+// After the barrier the component lanes read the grid sums of set `set` (identical for every
 // block), this stage starts the next one's copies (S < 7), so that the read latency and the
 // controller overlap the first copies, and warp 0 runs the controller.  The team's rank 0
 // clears the set that stage count + 2 will use: every block read it before arriving at this
@@ -596,8 +602,8 @@ __device__ bool run_stage(const Ctx &c, const Team &tm, SM &sm, Local &L, Coef &
         stage_begin<S>(c, sm, mn, pp);
     }
     if (S <= 2) {
-        if (tid < N) cavity_stage_value<S>(c, L, cf, tid);
-        if (S == 2 && tid >= 32 && tid < 32 + 36) attempt_coefficients(cf, L.h, tid - 32);
+        if (tid < 32) cavity_stage_value<S>(L, cf, tid, tid < 2 * N);
+        if (S == 2 && tid >= 32 && tid < 32 + 36) attempt_coefficients(cf, L, L.h, tid - 32);
         if (S == 2 && tid == 96) cf.h = (float)L.h;
         __syncthreads();
     }
@@ -613,14 +619,11 @@ __device__ bool run_stage(const Ctx &c, const Team &tm, SM &sm, Local &L, Coef &
     const int set = (int)(L.rhs_evals % 3);
     block_reduce(c, tm, sm, acc, set);
     if (!grid_barrier<SM>(c, tm, L, S)) return false;
-    long long sre = 0, sim = 0;
+    long long sq = 0;
     float emax = 0.f;
     {
         const volatile Ctl *g = c.ctl;
-        if (tid < N) {
-            sre = g->racc[set][2 * tid];
-            sim = g->racc[set][2 * tid + 1];
-        }
+        if (tid < 2 * N) sq = g->racc[set][tid];
         if (S == 7 && tid < 32) {
             const unsigned bits = g->remax[set];
             emax = g->range_error ? __int_as_float(0x7fffffff) : __uint_as_float(bits);
@@ -633,7 +636,7 @@ __device__ bool run_stage(const Ctx &c, const Team &tm, SM &sm, Local &L, Coef &
         }
     }
     if (S >= 2 && S < 7 && !c.stage_only) stage_begin<(S < 7 ? S + 1 : 7)>(c, sm, mn, pp);
-    controller<S>(c, tm, L, cf, sre, sim, emax);
+    controller<S>(c, tm, L, cf, sq, emax);
     __syncthreads();
     return true;
 }
@@ -651,7 +654,14 @@ __device__ bool integrate(const Ctx &c, const Team &tm, SM &sm, Local &L, Coef &
         L.rtolf = (float)c.rtol;
         L.inv_rtolf = (float)(1.0 / c.rtol);
         L.areff = (float)c.a_ref;
+        int hk = 0;
+#pragma unroll
+        for (int u = 0; u < MAXN; u++)
+            if (u < c.nmodes && c.kerr[u] != 0.0) hk = 1;
+        L.has_kerr = hk;
+        L.has_split = c.split_dt > 0.0;
     }
+    if (threadIdx.x < 2 * c.nmodes) component_constants(c, threadIdx.x, L);
     if (threadIdx.x >= 32 && threadIdx.x < 39) cf.e[threadIdx.x - 32] = (float)dp_e(threadIdx.x - 32);
     if (threadIdx.x < c.nmodes) mode_constants(c, threadIdx.x, L.mc + MC * threadIdx.x);
     {
