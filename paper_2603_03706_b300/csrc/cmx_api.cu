@@ -495,6 +495,7 @@ int cmx_create(const cmx_grid *grid, const uint8_t *mask, const cmx_material *ma
     c.two_over_gamma = 2.0 / mat->gamma;
     c.inv_nmag = 1.0 / (double)h->ncell_mag;
     c.red_scale = overlap_scale(umax * (double)h->ncell_mag);
+    c.umax = (float)umax;
     c.rtol = solver->rtol;
     c.a_ref = solver->a_ref;
     c.dt_min = solver->dt_min;

@@ -413,6 +413,7 @@ int cmx_batch_create(const cmx_instance *in, int n, const cmx_solver *solver,
         c.two_over_gamma = 2.0 / I.mat.gamma;
         c.inv_nmag = 1.0 / (double)I.lay.ncell_mag;
         c.red_scale = overlap_scale((double)I.lay.ncell_mag);   // no profiles: |u| = 1
+        c.umax = 1.f;
         c.rtol = solver->rtol;
         c.a_ref = solver->a_ref;
         c.dt_min = solver->dt_min;

@@ -46,6 +46,8 @@ struct Local {
     double hw[7][6];                     // h a_Sj of the current attempt (rows S-1 = 2..6)
     double rs;                           // fixed-point overlap sum -> <m^->: 1 / (scale N_c)
     float rtolf, inv_rtolf, areff;       // error-norm constants in FP32
+    float tscale;                        // per-thread fixed-point scale of the overlap partials
+    int tshift;                          // block sum (units 2^-20 / tscale) -> units 1 / red_scale
     int has_kerr, has_split;
     unsigned bar_target;                 // arrival count that completes the next barrier
     int skip_block;
@@ -478,50 +480,60 @@ __device__ void controller(const Ctx &c, const Team &tm, Local &L, Coef &cf, lon
     }
 }
 
-// Block sum of the per-thread overlap accumulators (compensated pairs, fixed shuffle order)
-// and block max of |e_m|, added into accumulator set `set` of the control block: the sums as
-// fixed-point integers (exact, so their total does not depend on the order of the blocks), the
-// maximum through an integer max on the bit pattern of the non-negative float.
+// Block sum of the per-thread overlap accumulators and block max of |e_m|, added into
+// accumulator set `set` of the control block.  Each thread scales its FP32 partials by L.tscale
+// (a power of two that keeps a partial below 2^24 in magnitude) and splits each into two int32
+// digits, the integer part and the remainder in units of 2^-20; a warp sums each digit exactly in
+// one redux instruction, the block in int64, and the total is added into the grid's fixed-point
+// sum (scale red_scale), so it does not depend on the order of the blocks.  A partial outside
+// the range (an unstable or non-finite state) sets range_error, which the controller turns into
+// CMX_ENAN.  The maximum goes through an integer max on the bit pattern of the non-negative
+// float (NaN is largest).
 template <class SM>
-__device__ void block_reduce(const Ctx &c, const Team &tm, SM &sm, const Acc &acc, int set)
+__device__ void block_reduce(const Ctx &c, const Team &tm, SM &sm, const Acc &acc, int set,
+                             const Local &L)
 {
     const int NT = blockDim.x, NW = NT / 32;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const float ts = L.tscale;
+    bool bad = false;
 #pragma unroll
     for (int n = 0; n < MAXN; n++) {
         if (n >= c.nmodes) break;
-        F2 r = {acc.re[n], 0.f}, i = {acc.im[n], 0.f};
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            r = f2_add(r, f2_shfl_xor(r, o));
-            i = f2_add(i, f2_shfl_xor(i, o));
-        }
-        if (lane == 0) {
-            sm.red[warp][2 * n] = r;
-            sm.red[warp][2 * n + 1] = i;
+        for (int k = 0; k < 2; k++) {
+            const float v = (k ? acc.im[n] : acc.re[n]) * ts;
+            bad |= !(fabsf(v) <= 16777216.f);
+            const float vh = rintf(v);   // exact below 2^24; v - vh is exact as well
+            const int dh = __reduce_add_sync(0xffffffffu, __float2int_rn(vh));
+            const int dl = __reduce_add_sync(0xffffffffu, __float2int_rn((v - vh) * 1048576.f));
+            if (lane == 0) {
+                sm.red[warp][2 * n + k].hi = __int_as_float(dh);
+                sm.red[warp][2 * n + k].lo = __int_as_float(dl);
+            }
         }
     }
-    float e = acc.emax;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) e = nanmax(e, __shfl_xor_sync(0xffffffffu, e, o));
-    if (lane == 0) sm.redmax[warp] = e;
+    const unsigned e = __reduce_max_sync(0xffffffffu, __float_as_uint(acc.emax));
+    if (lane == 0) sm.redmax[warp] = __uint_as_float(e);
+    if (bad) atomicExch(&c.ctl->range_error, 1);
     __syncthreads();
     const int Q = 2 * c.nmodes;
     if (threadIdx.x < Q) {
-        F2 s = {0.f, 0.f};
-        for (int w = 0; w < NW; w++) s = f2_add(s, sm.red[w][threadIdx.x]);
-        const double v = ((double)s.hi + (double)s.lo) * c.red_scale;
-        if (fabs(v) < 4.0e18) {
-            atomicAdd(reinterpret_cast<unsigned long long *>(&c.ctl->racc[set][threadIdx.x]),
-                      (unsigned long long)__double2ll_rn(v));
-        } else {
-            atomicExch(&c.ctl->range_error, 1);
+        long long sh = 0, sl = 0;
+        for (int w = 0; w < NW; w++) {
+            sh += __float_as_int(sm.red[w][threadIdx.x].hi);
+            sl += __float_as_int(sm.red[w][threadIdx.x].lo);
         }
+        long long v = sh * (1ll << 20) + sl;   // units of 2^-20 / tscale
+        const int d = L.tshift;                  // to units of 1 / red_scale
+        v = d >= 0 ? v * (1ll << d) : (v + (1ll << (-d - 1))) >> (-d);
+        atomicAdd(reinterpret_cast<unsigned long long *>(&c.ctl->racc[set][threadIdx.x]),
+                  (unsigned long long)v);
     }
     if (threadIdx.x == NT - 1) {
-        float m = 0.f;
-        for (int w = 0; w < NW; w++) m = nanmax(m, sm.redmax[w]);
-        atomicMax(&c.ctl->remax[set], __float_as_uint(m));
+        unsigned m = 0u;
+        for (int w = 0; w < NW; w++) m = max(m, __float_as_uint(sm.redmax[w]));
+        atomicMax(&c.ctl->remax[set], m);
     }
 }
 
@@ -617,7 +629,7 @@ __device__ bool run_stage(const Ctx &c, const Team &tm, SM &sm, Local &L, Coef &
                           ? (int)L.replay_pos : -1;
     stage_run<S>(c, sm, (float *)sm.kp[S - 1], mn, mnew, cf, pp, tslot, rslot, acc);
     const int set = (int)(L.rhs_evals % 3);
-    block_reduce(c, tm, sm, acc, set);
+    block_reduce(c, tm, sm, acc, set, L);
     if (!grid_barrier<SM>(c, tm, L, S)) return false;
     long long sq = 0;
     float emax = 0.f;
@@ -671,6 +683,18 @@ __device__ bool integrate(const Ctx &c, const Team &tm, SM &sm, Local &L, Coef &
     }
     __syncthreads();
     stage_cache_rows(c, sm);
+    if (threadIdx.x == 0) {
+        // fixed-point scale of this block's overlap partials: a thread computes at most P cells
+        // per stage (interior planes of the block's segments, four cells each in quad windows),
+        // each contributing at most |u| |m| <= 2 umax
+        int P = 0;
+        for (int t = 0; t < sm.nseg; t++) P += sm.seg[t].w - sm.seg[t].z;
+        P *= c.quad > 1 ? c.quad : 1;
+        const float bound = 2.f * (float)(P > 1 ? P : 1) * fmaxf(c.umax, 1.f);
+        const int k = 24 - (int)ceilf(log2f(bound));
+        L.tscale = ldexpf(1.f, k);
+        L.tshift = ilogb(c.red_scale) - k - 20;
+    }
     __syncthreads();
     bool ok = true;
     Pipe pp;

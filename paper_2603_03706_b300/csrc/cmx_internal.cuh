@@ -129,6 +129,7 @@ struct Ctx {
     int has_gb;                      // 1: nonreciprocal coupling (gradients of gb~ separate)
     double two_over_gamma, inv_nmag;
     double red_scale;                // fixed-point scale of the overlap sums (a power of two)
+    float umax;                      // bound on |u_n(r)| (1 without profiles)
     // external drive eta_n(t) = drive_n exp(-(t - drive_t0)^2 / (2 sigma^2)) on da_n/dt
     // (Eq. (1), (12)); has_drive = 0: none
     double drive_re[MAXN], drive_im[MAXN];

@@ -217,6 +217,7 @@ extern "C" int cmx_eval_rhs_noalloc(const cmx_grid *grid, const uint8_t *mask,
     c.two_over_gamma = 2.0 / mat->gamma;
     c.inv_nmag = 1.0 / (double)lay.ncell_mag;
     c.red_scale = overlap_scale((has_u ? 256.0 : 1.0) * (double)lay.ncell_mag);
+    c.umax = has_u ? 256.f : 1.f;
     c.rtol = 1e-6;
     c.a_ref = 1e-3;
     c.dt_min = 1e-18;
