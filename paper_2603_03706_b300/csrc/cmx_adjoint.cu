@@ -473,10 +473,13 @@ __device__ bool rev_stage(const AdjArgs &A, RevSmem<NS, WX, WY> &sm, RevLocal &L
         // feedback field adjoint through gb~ (the backward coupling), then the cavity equation
         double fr = -k * wr - w * wi + tg * gbr * Sn;
         double fi = w * wr - k * wi - tg * gbi * Sn;
-        // self-Kerr -i K |a|^2 a = (K |a|^2 ai, -K |a|^2 ar)
+        // self-Kerr -i K |a|^2 a = (K |a|^2 ai, -K |a|^2 ar); its Jacobian terms vanish at K = 0,
+        // and FP64 instructions are expensive on this part of the stage
         const double s2 = ar * ar + ai * ai;
-        fr += wr * 2.0 * K * ar * ai - wi * K * (3.0 * ar * ar + ai * ai);
-        fi += wr * K * (ar * ar + 3.0 * ai * ai) - wi * 2.0 * K * ar * ai;
+        if (K != 0.0) {
+            fr += wr * 2.0 * K * ar * ai - wi * K * (3.0 * ar * ar + ai * ai);
+            fi += wr * K * (ar * ar + 3.0 * ai * ai) - wi * 2.0 * K * ar * ai;
+        }
         if (S == 7) {
             fr += L.abar[2 * n];
             fi += L.abar[2 * n + 1];
