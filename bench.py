@@ -40,7 +40,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="cmx", choices=["cmx", "reference"])
-    ap.add_argument("--workload", default="multimode_sphere",
+    ap.add_argument("--workload", default="afm_film",
                     choices=["multimode_sphere", "afm_film", "full_box", "single_sphere"])
     ap.add_argument("--attempts", type=int, default=0, help="DP attempts per launch (0: auto)")
     ap.add_argument("--box", default="256,256,128", help="full_box grid nx,ny,nz")
@@ -49,12 +49,14 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--no-sub", action="store_true",
+                    help="skip the other single-problem workloads and the 8^3 sphere record")
     ap.add_argument("--adjoint-T", type=float, default=20e-9,
                     help="end time of the adjoint measurement (64^3 sphere, 3 modes)")
     ap.add_argument("--adjoint-every", type=int, default=200)
     ap.add_argument("--no-batch", action="store_true")
-    ap.add_argument("--batch-n", type=int, default=256, help="instances of the batched sweep")
-    ap.add_argument("--batch-T", type=float, default=2e-9, help="end time of every instance")
+    ap.add_argument("--batch-n", type=int, default=512, help="instances of the batched sweep")
+    ap.add_argument("--batch-T", type=float, default=30e-9, help="end time of every instance")
     return ap.parse_args()
 
 
@@ -315,7 +317,16 @@ def batch_sweep(n_inst, T, stream):
     t_seq = time.perf_counter() - t0
     for s in sims:
         s.close()
+    # algorithmic bytes of the batched run: the single-problem bytes model per magnetic cell and
+    # attempt (uniform profiles), times the cell-attempts it performed
+    peaks = measured_peaks()
+    peak_gbs = peaks.get("hbm_gbs", 6400.0)
+    achieved = bytes_per_cell_attempt(probs[0]) * st["cell_stage_updates"] / 6.0 / t_batch / 1e9
     return {"value": n_inst / t_batch, "unit": "sims/s", "sequential": n_inst / t_seq,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak_gbs, "unit": "GB/s",
+                         "frac": achieved / peak_gbs, "traffic": None,
+                         "bytes_per_cell_attempt": bytes_per_cell_attempt(probs[0]),
+                         "timing": "wall clock of the whole batched run"},
             "speedup_vs_sequential": t_seq / t_batch, "instances": n_inst, "T": T,
             "cells_total": cells, "batch_s": t_batch, "sequential_s": t_seq,
             "cell_stage_updates_per_s": st["cell_stage_updates"] / t_batch,
@@ -363,18 +374,12 @@ def run_reference(args):
     print(json.dumps(line))
 
 
-def main():
-    args = parse()
-    if args.impl == "reference":
-        return run_reference(args)
-    import numpy as np
+def time_workload(p, stream, steps, warmup, attempts=0, tiling=None, clocks_for=None):
+    """Device-timed launches of one workload: autotuned window (unless given), A attempts per
+    launch (about 20 ms of work at the HBM roofline, 8..2000), L2 flushed before every timed
+    launch, CUDA events on the integrator's stream.  Returns the record and the open handle."""
     import torch
     from paper_2603_03706_b300 import cmx
-
-    rank, world, local = dist_setup(args.gpus)
-    p = make_workload(args.workload, args.box)
-    stream = torch.cuda.Stream()
-    tiling = tuple(int(v) for v in args.tiling.split(",")) if args.tiling else None
     sim = cmx.Simulation.from_problem(p, stream=stream, tiling=tiling)
     tuned = None
     if tiling is None:
@@ -382,42 +387,107 @@ def main():
         torch.cuda.synchronize()
     ncell = sim.ncells()[0]
     bpa = bytes_per_cell_attempt(p) * ncell
-    # attempts per launch: about 20 ms of work per step at the HBM roofline
     peaks = measured_peaks()
     peak_gbs = peaks.get("hbm_gbs", 6400.0)
-    A = args.attempts or max(8, min(2000, int(0.02 * peak_gbs * 1e9 / bpa)))
-    T_far = 1.0                                   # never reached within a benchmark step
+    A = attempts or max(8, min(2000, int(0.02 * peak_gbs * 1e9 / bpa)))
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MiB > L2
-
-    def step():
-        sim.launch(T_far, A)
-
     with torch.cuda.stream(stream):
-        for _ in range(args.warmup):
+        for _ in range(warmup):
             flush.zero_()
-            step()
-        sim.sync()
+            sim.launch(1.0, A)           # T = 1 s is never reached within a launch
         st0 = sim.sync()
         evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-               for _ in range(args.steps)]
+               for _ in range(steps)]
         torch.cuda.synchronize()
-        if world > 1:
-            torch.distributed.barrier()
-        with ClockSampler(local) as clk:
-            for i in range(args.steps):
+        if clocks_for is not None:
+            clocks_for()
+        with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
+            for i in range(steps):
                 flush.zero_()
                 evs[i][0].record(stream)
-                step()
+                sim.launch(1.0, A)
                 evs[i][1].record(stream)
             torch.cuda.synchronize()
         st1 = sim.sync()
+    del flush
     times = [a.elapsed_time(b) * 1e-3 for a, b in evs]
     t_total = sum(times)
-    t_total_max = barrier_and_max(t_total, world)
     updates = st1["cell_stage_updates"] - st0["cell_stage_updates"]
-    attempts = st1["attempts"] - st0["attempts"]
+    attempts_done = st1["attempts"] - st0["attempts"]
+    achieved = bpa * (attempts_done / steps) / (t_total / steps) / 1e9
+    rec = {
+        "workload": p.name, "value": updates / t_total, "unit": UNIT,
+        "ms_per_step": 1e3 * t_total / steps, "steps": steps, "warmup": warmup,
+        "us_per_attempt": 1e6 * t_total / max(attempts_done, 1),
+        "cells": ncell, "grid": [p.nx, p.ny, p.nz], "nsub": p.nsub, "modes": p.nmodes,
+        "attempts_per_step": A, "rhs_evals_per_step": updates / ncell / steps,
+        "dt_max": p.dt_max, "l2": "flushed between timed steps (256 MiB write)",
+        "tiling": sim.get_tiling(), "autotune_us_per_attempt": tuned and tuned["us_per_attempt"],
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak_gbs, "unit": "GB/s",
+                     "frac": achieved / peak_gbs,
+                     "traffic": recorded_traffic(p.name, A),
+                     "bytes_per_cell_attempt": bytes_per_cell_attempt(p),
+                     "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else
+                     "fallback 6400 GB/s"},
+        "clocks": clk.summary(),
+    }
+    return rec, sim, t_total, updates
+
+
+def single_sphere_record(stream):
+    """Latency-bound 8^3 sphere (280 cells, one mode): device time per attempt of one long
+    launch, and the wall time of the whole 20 ns integration through cmx_run."""
+    import torch
+    from paper_2603_03706_b300 import cmx
+    from paper_2603_03706_b300 import workloads as W
+    p = W.single_sphere(T=20e-9)
+    sim = cmx.Simulation.from_problem(p, stream=stream)
+    sim.run(0.2e-9)                                   # warm-up
+    sim.set_state(p.m0, p.a0)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    sim.launch(1.0, 2000)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    us = e0.elapsed_time(e1) * 1e3 / 2000
+    sim.set_state(p.m0, p.a0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    st = sim.run(p.T)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    tl = sim.get_tiling()
+    sim.close()
+    return {"workload": p.name, "cells": p.ncells, "us_per_attempt": us,
+            "cell_stage_updates_per_s": 6 * p.ncells / (us * 1e-6),
+            "T": p.T, "wall_s_to_T": wall, "attempts_to_T": st["attempts"],
+            "accepted_to_T": st["accepted"], "launches_to_T": st["launches"], "tiling": tl,
+            "timing": "us_per_attempt: CUDA events over one 2000-attempt launch; wall_s_to_T: "
+                      "cmx_run from t = 0 to T, synchronised"}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import numpy as np
+    import torch
+
+    rank, world, local = dist_setup(args.gpus)
+    p = make_workload(args.workload, args.box)
+    stream = torch.cuda.Stream()
+    tiling = tuple(int(v) for v in args.tiling.split(",")) if args.tiling else None
+
+    def sync_ranks():
+        if world > 1:
+            torch.distributed.barrier()
+
+    rec, sim, t_total, updates = time_workload(p, stream, args.steps, args.warmup,
+                                               args.attempts, tiling, clocks_for=sync_ranks)
+    A = rec["attempts_per_step"]
+    t_total_max = barrier_and_max(t_total, world)
     value = updates * world / t_total_max
-    achieved = bpa * (attempts / args.steps) / (t_total / args.steps) / 1e9
 
     # end to end through the public API: pinned host buffers in and out every step
     e2e = None
@@ -427,17 +497,16 @@ def main():
         a0 = np.asarray(p.a0)
         for _ in range(2):
             sim.set_state(m_host, a0)
-            sim.launch(T_far, A)
+            sim.launch(1.0, A)
             sim.get_a()
             sim.get_m(out=m_out)
         torch.cuda.synchronize()
-        if world > 1:
-            torch.distributed.barrier()
+        sync_ranks()
         u0 = 0
         t0 = time.perf_counter()
         for _ in range(args.steps):
             sim.set_state(m_host, a0)
-            sim.launch(T_far, A)
+            sim.launch(1.0, A)
             st = sim.sync()
             u0 += st["cell_stage_updates"]
             sim.get_a()
@@ -448,35 +517,35 @@ def main():
         d2h = m_out.numel() * 4 + 16 * p.nmodes
         e2e = {"value": u0 * world / te, "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h}
+    sim.close()
 
+    line = None
     if rank == 0:
-        clocks = clk.summary()
-        tl = sim.get_tiling()
+        config = {k: rec[k] for k in ("workload", "cells", "grid", "nsub", "modes",
+                                      "attempts_per_step", "rhs_evals_per_step", "dt_max", "l2",
+                                      "tiling", "autotune_us_per_attempt")}
+        config["parallelism"] = "replicas" if world > 1 else "single"
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * t_total_max / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-            "data": "synthetic",
-            "config": {"workload": p.name, "cells": ncell, "grid": [p.nx, p.ny, p.nz],
-                       "nsub": p.nsub, "modes": p.nmodes, "attempts_per_step": A,
-                       "rhs_evals_per_step": updates / ncell / args.steps,
-                       "dt_max": p.dt_max, "l2": "flushed between timed steps (256 MiB write)",
-                       "tiling": tl, "autotune_us_per_attempt": tuned and tuned["us_per_attempt"],
-                       "parallelism": "replicas" if world > 1 else "single"},
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak_gbs, "unit": "GB/s",
-                         "frac": achieved / peak_gbs,
-                         "traffic": recorded_traffic(p.name, A),
-                         "bytes_per_cell_attempt": bytes_per_cell_attempt(p),
-                         "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else
-                         "fallback 6400 GB/s"},
-            "clocks": clocks,
-            "gpu_launches": 2 * args.steps,
-            "e2e": e2e,
+            "data": "synthetic", "config": config, "roofline": rec["roofline"],
+            "clocks": rec["clocks"], "gpu_launches": 2 * args.steps, "e2e": e2e,
         }
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(p, args.cpu_seconds)
-    sim.close()
-    if rank == 0:
+        if not args.no_sub:
+            # the other single-problem workloads, each with its own roofline record
+            subs = []
+            for name in ("multimode_sphere", "full_box"):
+                if name == args.workload:
+                    continue
+                q = make_workload(name, "256,256,128")
+                r, s2, _, _ = time_workload(q, stream, 5, 3)
+                s2.close()
+                subs.append(r)
+            line["workloads"] = subs
+            line["single_sphere"] = single_sphere_record(stream)
         if not args.no_adjoint:
             line["adjoint"] = adjoint_ratio(args.adjoint_T, args.adjoint_every, stream)
         if not args.no_batch:

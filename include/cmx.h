@@ -236,9 +236,11 @@ const char *cmx_status_string(int status);
 /* ------------------------------------------------------------------------------------------
  * Right-hand-side evaluation without device allocation (no counterpart in the paper).
  *
- * For callers that cannot call cudaMalloc: code that runs while a stream is captured into a
- * CUDA graph, plug-ins living inside a host program that owns the device allocator, processes
- * under a fixed device-memory budget.  It computes the same f(m, a) as cmx_eval_rhs, with the
+ * For callers that cannot call cudaMalloc: plug-ins living inside a host program whose own
+ * allocator owns all device memory (a cudaMalloc behind its back breaks its accounting or
+ * fails because it has reserved the memory), and services under a fixed device-memory budget
+ * that must not meet an out-of-memory error after start-up.  It computes the same f(m, a) as
+ * cmx_eval_rhs, with the
  * same stage kernel, but allocates nothing: no cudaMalloc, no cudaFree, no allocating library
  * routine.  Every scratch buffer (compact layout tables, compact m and slope, control block,
  * block partials) is carved from one file-scope device array of CMX_NOALLOC_SCRATCH_BYTES
@@ -255,7 +257,8 @@ const char *cmx_status_string(int status);
  * the one array and it keeps the last call's contents: calls that overlap on the GPU (other
  * host threads, other streams) race and must be serialised by the caller.
  * Returns CMX_ESCRATCH when the problem's buffers need more than CMX_NOALLOC_SCRATCH_BYTES
- * (about 150k stored cells for one sublattice with no profiles), CMX_EINVAL on bad arguments. */
+ * (28 bytes per stored cell for one sublattice with no profiles, about 600k cells; with two
+ * host-side profiles 44 bytes, about 380k cells), CMX_EINVAL on bad arguments. */
 #define CMX_NOALLOC_SCRATCH_BYTES (16u << 20)
 int cmx_eval_rhs_noalloc(const cmx_grid *grid, const uint8_t *mask, const cmx_material *mat,
                          const cmx_modes *modes, const float *m, const double *a, float *dm,

@@ -726,9 +726,11 @@ class BatchSimulation:
         return dict(zip(("teams", "team_size", "blocks", "cells", "graph"), [x.value for x in v]))
 
 
-def eval_rhs_noalloc(p, m_dev, dm_dev, a=None, stream=None):
+def eval_rhs_noalloc(p, m_dev, dm_dev, a=None, stream=None, u_dev=None):
     """cmx_eval_rhs_noalloc for a workloads.Problem: m_dev, dm_dev are device pointers (or CUDA
-    tensors) of dense-box float32 arrays.  Returns (da, mm) complex; raises CmxError."""
+    tensors) of dense-box float32 arrays; u_dev (optional) a device pointer or CUDA tensor of the
+    dense-box profiles, used instead of the host copy p.u.  Returns (da, mm) complex; raises
+    CmxError."""
     lib = load()
     g = Grid(p.nx, p.ny, p.nz, p.cx, p.cy, p.cz, p.nsub)
     mt = Material(p.Ms, p.Aex, p.alpha, p.gamma, p.Ku, (C.c_double * 3)(*p.ku_axis),
@@ -739,7 +741,9 @@ def eval_rhs_noalloc(p, m_dev, dm_dev, a=None, stream=None):
     md.n_modes = p.nmodes
     md.omega, md.kappa, md.g_re, md.g_im = _dptr(om), _dptr(ka), _dptr(gr), _dptr(gi)
     uu = None
-    if p.u is not None:
+    if u_dev is not None:
+        md.u, md.u_on_device = _dev_ptr(u_dev), 1
+    elif p.u is not None:
         uu = _f32(p.u)
         md.u, md.u_on_device = uu.ctypes.data, 0
     else:

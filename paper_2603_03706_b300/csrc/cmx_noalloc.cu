@@ -1,12 +1,13 @@
 // Right-hand-side evaluation that allocates no device memory (cmx_eval_rhs_noalloc).
 //
-// Some callers cannot call cudaMalloc: code running while a stream is being captured into a
-// CUDA graph, plug-ins inside a host program that owns the device allocator, or processes under
-// a fixed device-memory budget.  This entry point evaluates f(m, a) with the same stage kernel
+// Some callers cannot call cudaMalloc: plug-ins inside a host program whose own allocator owns
+// all device memory, or services under a fixed device-memory budget that must not meet an
+// out-of-memory error after start-up.  This entry point evaluates f(m, a) with the same stage kernel
 // as cmx_eval_rhs but takes every scratch buffer (compact layout tables, compact m and slope,
 // control block) from one file-scope device array of CMX_NOALLOC_SCRATCH_BYTES.
 // That array exists on every device that loads the library, from load until process exit.
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <vector>
 
@@ -100,6 +101,7 @@ extern "C" int cmx_eval_rhs_noalloc(const cmx_grid *grid, const uint8_t *mask,
     if (N > 0 && (!modes->omega || !modes->kappa || !modes->g_re || !modes->g_im)) return CMX_EINVAL;
     const cudaStream_t s = (cudaStream_t)stream;
     const long long nbox = (long long)grid->nx * grid->ny * grid->nz;
+    if (nbox > (1LL << 31) - 1) return CMX_EINVAL;   // box indices are 32-bit
     const int nq = 3 * grid->nsub;
 
     // host-side layout and partition (host memory only)
@@ -112,6 +114,18 @@ extern "C" int cmx_eval_rhs_noalloc(const cmx_grid *grid, const uint8_t *mask,
         return CMX_ECUDA;
     const int bx = 32, by = 8;
     const bool has_u = N > 0 && modes->u;
+    // bound on |u| for the fixed-point overlap sums: measured over the magnetic cells for host
+    // profiles (as cmx_create does), 256 for device profiles (a larger value stops the
+    // evaluation with CMX_ENAN through the range check of the block sums)
+    double umax = 1.0;
+    if (has_u && !modes->u_on_device) {
+        for (int n = 0; n < N; n++)
+            for (long long i = 0; i < nbox; i++)
+                if (mask[i]) umax = std::max(umax, (double)std::fabs(modes->u[n * nbox + i]));
+        if (!(umax < 1e30)) return CMX_EINVAL;   // non-finite profile
+    } else if (has_u) {
+        umax = 256.0;
+    }
     const int occ = single_blocks_per_sm(grid->nsub, bx, by, has_u);
     if (occ <= 0) return CMX_ECUDA;
     const std::vector<Column> cols = build_columns(lay, bx, by);
@@ -216,8 +230,8 @@ extern "C" int cmx_eval_rhs_noalloc(const cmx_grid *grid, const uint8_t *mask,
     }
     c.two_over_gamma = 2.0 / mat->gamma;
     c.inv_nmag = 1.0 / (double)lay.ncell_mag;
-    c.red_scale = overlap_scale((has_u ? 256.0 : 1.0) * (double)lay.ncell_mag);
-    c.umax = has_u ? 256.f : 1.f;
+    c.red_scale = overlap_scale(umax * (double)lay.ncell_mag);
+    c.umax = (float)umax;
     c.rtol = 1e-6;
     c.a_ref = 1e-3;
     c.dt_min = 1e-18;

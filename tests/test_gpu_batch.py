@@ -13,7 +13,7 @@ from oracle import oracle as O
 from paper_2603_03706_b300 import cmx, spectra
 from paper_2603_03706_b300 import workloads as W
 
-from gpu_util import TOL_A, TOL_M, f32_state, masked
+from gpu_util import TOL_A, TOL_M, check_step_log, f32_state, masked
 
 pytestmark = pytest.mark.gpu
 TP = 2 * math.pi
@@ -54,6 +54,51 @@ def test_batch_instances_replay_against_oracle(team):
         dm = np.abs(masked(p, b.get_m(i)) - masked(p, m_orc)).max()
         da = np.abs(b.get_a(i) - st["a"]).max() / np.abs(olog.view()["a"]).max()
         assert dm <= TOL_M and da <= TOL_A, (i, dm, da)
+        check_step_log(p, log, olog.view())
+    b.close()
+
+
+def medium_batch(sizes=(24, 30, 36, 42, 48), seed=17):
+    """Spheres of 24^3 .. 48^3 cells (7,208 .. 57,864 magnetic cells), 1-3 modes each, B0 swept
+    across the anticrossing: the lower end of the batched sweep's size range."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i, n in enumerate(sizes):
+        nm = 1 + i % 3
+        fm = 4.8e9 + 0.4e9 * i / max(len(sizes) - 1, 1)
+        p = W.make_problem(n, n, n, 5e-9, W.sphere_mask(n, n, n), alpha=1e-3,
+                           B0=(0, 0, TP * fm / W.GAMMA), Nd=(1 / 3, 1 / 3, 1 / 3),
+                           omega=TP * np.array([5.0e9, 4.85e9, 5.15e9][:nm]),
+                           kappa=TP * rng.uniform(1e6, 10e6, nm),
+                           g_re=TP * rng.uniform(5e6, 80e6, nm), g_im=np.zeros(nm),
+                           m0=W.tilted_state(1, n, n, n, 1.0, 0.7 * i),
+                           a0=(rng.normal(size=nm) + 1j * rng.normal(size=nm)) * 1e-3, T=1e-6)
+        out.append(f32_state(p))
+    return out
+
+
+@pytest.mark.parametrize("team", [8, 16])
+def test_batch_medium_spheres_large_teams_replay_against_oracle(team):
+    """Teams of 8 and 16 blocks (several segments per block, as in the benchmark's sweep) on
+    24^3 .. 48^3 spheres: every instance's accepted steps replayed by the oracle, its error
+    norms and step sizes checked attempt by attempt."""
+    probs = medium_batch()
+    b = cmx.BatchSimulation(probs, log_cap=420, team=team)
+    assert b.info()["team_size"] == team
+    b.run(max_attempts=400)
+    for i, p in enumerate(probs):
+        log = b.get_log(i)
+        dts = log["dt"][log["accepted"]]
+        assert len(dts) >= 300
+        it = O.Integrator(O.OracleProblem(p))
+        rc, olog = it.replay(dts)
+        assert rc == 0
+        st = it.state()
+        m_orc = st["m"].reshape(1, 3, p.nz, p.ny, p.nx)
+        dm = np.abs(masked(p, b.get_m(i)) - masked(p, m_orc)).max()
+        da = np.abs(b.get_a(i) - st["a"]).max() / np.abs(olog.view()["a"]).max()
+        assert dm <= TOL_M and da <= TOL_A, (i, dm, da)
+        check_step_log(p, log, olog.view())
     b.close()
 
 

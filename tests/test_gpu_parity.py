@@ -130,18 +130,35 @@ def test_replay_afm_complex_coupling_1000_steps():
 # full-size workloads in the measured configuration (sampled)
 # ---------------------------------------------------------------------------------------------
 
-def test_full_size_multimode_sphere_rhs_and_steps():
+def test_full_size_multimode_sphere_rhs():
     p = W.multimode_sphere()
     r = rhs_compare(p)
     assert r["err_m"] < 2e-6 and r["err_mm"] < 1e-7 and r["err_da"] < 1e-6, r
-    dm, da, info = replay_compare(p, 20)
-    assert dm <= TOL_M and da <= TOL_A, (dm, da)
+
+
+def test_full_size_multimode_sphere_1000_steps():
+    """The 128x128x64 sphere (137,376 cells, four profiled modes) in the benchmark's launch
+    configuration (window picked by the autotuner, every resident block, several segments per
+    block): 1000 adaptive device attempts replayed by the oracle, with the error norms and the
+    step-size sequence checked attempt by attempt."""
+    dm, da, info = replay_compare(W.multimode_sphere(), 1000, autotune=5)
+    assert info["stats"]["accepted"] >= 900
+    assert info["tiling"]["blocks"] > 100, info["tiling"]
+    assert dm <= TOL_M and da <= TOL_A, (dm, da, info["derr"], info["tiling"])
 
 
 def test_full_size_afm_film_rhs():
     p = W.afm_film()
     r = rhs_compare(p.replace(m0=W.random_state(2, p.nx, p.ny, p.nz, 7, 0.1, afm=True)))
     assert r["err_m"] < 2e-6 and r["err_mm"] < 1e-7 and r["err_da"] < 1e-6, r
+
+
+def test_full_size_afm_film_200_steps():
+    """The 256x256x16 two-sublattice film (complex coupling of mode 2) in the benchmark's launch
+    configuration: 200 adaptive device attempts replayed by the oracle."""
+    dm, da, info = replay_compare(W.afm_film(), 200, autotune=3)
+    assert info["stats"]["accepted"] >= 150
+    assert dm <= TOL_M and da <= TOL_A, (dm, da, info["derr"], info["tiling"])
 
 
 # ---------------------------------------------------------------------------------------------
