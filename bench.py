@@ -86,7 +86,7 @@ def bytes_per_cell_attempt(p):
 
 # Sources that define the single-problem integrator launch (kernel, engine, stage code, the
 # host code that lays out the cells and partitions the blocks).
-KERNEL_SOURCES = ("cmx_internal.cuh", "cmx_stage.cuh", "cmx_engine.cuh", "cmx_quad.cuh",
+KERNEL_SOURCES = ("cmx_internal.cuh", "cmx_stage.cuh", "cmx_engine.cuh",
                   "cmx_single.cu", "cmx_kernels.h", "cmx_api.cu", "cmx_layout.cu",
                   "cmx_layout.h", "cmx_problem.h")
 

@@ -97,23 +97,17 @@ typedef struct {
     int trace_cap;
 } cmx_solver;
 
-/* Launch shape.  Two window kinds march along z through columns of the grid:
- *  - one cell per thread (quad = 0 or 1, the default): bx, by = thread window in cells
- *    (compiled windows: 32x8, 32x16, 64x4, and 32x8, 32x16, 64x4 for two sublattices; bx = by =
- *    0 selects 32x8); a block computes the (bx-2) x (by-2) interior columns, the one-cell rim is
- *    the exchange halo;
- *  - four x-cells per thread (quad = 4, one sublattice only): a window of bx/4 x by threads
- *    (bx a multiple of 4, (bx/4) * by a multiple of 32 and at most 256, by <= 16; bx = by = 0
- *    selects 64x16) computes (bx-8) x (by-2) interior cells with 16-byte operands; cells are
- *    stored with rows aligned to 4 cells.  On B300 it runs one block per SM and is slower than
- *    the default on the measured workloads.
- * The columns' planes are split into contiguous per-block segments with balanced plane counts;
- * bz: the fewest planes per block (0 = 4); fewer blocks are used when the grid is small.
- * blocks_per_sm caps the resident blocks per SM (0 = as many as fit). */
+/* Launch shape.  A block of bx x by threads computes a tile of bx x by cells of a column of the
+ * grid (one cell per thread, one warp per x-row) and loads the tile's one-cell rim as well; it
+ * marches along z through its columns' planes.  Compiled tiles: 32x4, 32x8, 32x16, for one and
+ * two sublattices; bx = by = 0 selects 32x8.  The columns' planes are split into contiguous
+ * per-block segments with balanced plane counts; bz: the fewest planes per block (0 = 4); fewer
+ * blocks are used when the grid is small.  blocks_per_sm caps the resident blocks per SM (0 =
+ * as many as fit).  quad: 0 or 1 (other values are rejected; kept for layout compatibility). */
 typedef struct {
     int bx, by, bz;
     int blocks_per_sm;   /* 0 = as many as fit */
-    int quad;            /* 0 or 1 = one cell per thread, 4 = four cells per thread */
+    int quad;            /* 0 or 1 */
 } cmx_tiling;
 
 typedef struct {
@@ -219,14 +213,38 @@ int cmx_set_backward_coupling(cmx_problem *h, const double *gb_re, const double 
 int cmx_set_kerr(cmx_problem *h, const double *kerr);
 
 /* Autotuner: time `attempts` Dormand-Prince attempts (after a one-attempt warm-up) from the
- * current state with each compiled one-cell window (32x8, 32x16, 64x4; blocks_per_sm and bz of
- * the current tiling), restore the state after each trial (m, FSAL slope, control block; the
- * step log and trace counters roll back too) and keep the fastest window.  *chosen (may be
- * NULL) receives it; us_per_attempt (may be NULL, 3 entries) the measured times in that order.
- * Quad windows are left as they are (nothing is tuned). */
+ * current state with each compiled tile (32x4, 32x8, 32x16; blocks_per_sm and bz of the
+ * current tiling) and, for a grid small enough, with the single-block integrator, restore the
+ * state after each trial (m, FSAL slope, control block; the step log and trace counters roll
+ * back too) and keep the fastest.  *chosen (may be NULL) receives it (bx = by = 0: the
+ * single-block integrator); us_per_attempt (may be NULL, 4 entries) the measured times in that
+ * order (NaN where a candidate does not apply). */
 int cmx_autotune(cmx_problem *h, int attempts, cmx_tiling *chosen, double *us_per_attempt);
 
-/* Launch shape actually used: bx, by, bz, grid blocks, tiles. */
+/* Full magnetostatic demag (mode 1) instead of the diagonal factors Ndemag of cmx_material
+ * (mode 0, the default).  The field of the magnetic cells is the convolution
+ * B_d(r_i) = -mu0 Ms sum_j N(r_i - r_j) m_j with the cell-pair tensor of Newell, Williams and
+ * Dunlop (1993), evaluated on the device in every stage by zero-padded FFTs; for two
+ * sublattices it acts on the total moment m1 + m2.  The paper notes that diagonal factors hold
+ * only for the uniform mode of an ellipsoid (Sec. II C, Eq. (9)); the full field is what
+ * non-uniform modes (Sec. II D, Eq. (11)) and non-ellipsoidal samples need.  Grids up to
+ * CMX_DEMAG_MAX_FFT / 2 cells per axis.  With mode 1 the single-block integrator is not used,
+ * and the adjoint (cmx_adjoint_record) is rejected; the batched form has no full demag.
+ * Returns CMX_EINVAL for a larger grid, a recording adjoint or another mode. */
+#define CMX_DEMAG_MAX_FFT 256
+int cmx_set_demag(cmx_problem *h, int mode);
+
+/* Planning query, host only (no device work, callable without a GPU): the row-compacted layout
+ * and the partition that `blocks` blocks of bx x by tiles would use for this grid and mask
+ * (mask: host, nx*ny*nz, x fastest).  *n_segments (may be NULL) receives the number of column
+ * segments, *n_stored (may be NULL) the number of stored cells (rows padded to 8 cells).
+ * Returns CMX_EINVAL if the tile is not compiled, the mask is empty, or the tile columns cannot
+ * be spread over `blocks` blocks of at most 64 segments each (cmx_create and cmx_batch_create
+ * reject such a problem with the same code instead of leaving cells out). */
+int cmx_plan_tiling(const cmx_grid *grid, const uint8_t *mask, int bx, int by, int blocks,
+                    long long *n_segments, long long *n_stored);
+
+/* Launch shape actually used: bx, by, bz, grid blocks, segments; *quad = 1. */
 int cmx_get_tiling(const cmx_problem *h, int *bx, int *by, int *bz, int *blocks, int *tiles,
                    int *quad);
 

@@ -68,6 +68,9 @@ typedef struct {
     /* 1: the cavity amplitudes are held fixed (da/dt = 0, no drive): the magnet-only
        sub-integration of the operator-split scheme (orc_run_split) */
     int cavity_frozen;
+    /* full magnetostatic demag (NEXT-3 of the scope; Sec. II C-D, Eq. (9), (11)): the cell-pair
+       demag tensor of every displacement (orc_demag_tensor); NULL: the diagonal factors Nd */
+    const double *demag;
 } orc_problem;
 
 typedef struct {
@@ -137,6 +140,128 @@ static long count_cells(const orc_problem *P)
     return n;
 }
 
+/* ------------------------------------------------------------------------------------------- */
+/* Full magnetostatic demag.  The field of a uniformly magnetised cuboid cell j averaged over   */
+/* cuboid cell i is -N(r_i - r_j) M_j with the cell-pair tensor of Newell, Williams & Dunlop    */
+/* (1993): with D_h q(X) = 2 q(X) - q(X - h) - q(X + h) the negative second difference,          */
+/*   N_xx(X, Y, Z) = D_dx D_dy D_dz f(X, Y, Z) / (4 pi dx dy dz),                                 */
+/*   N_xy(X, Y, Z) = D_dx D_dy D_dz g(X, Y, Z) / (4 pi dx dy dz),                                 */
+/* and the other components by permuting the axes.  B_d(r_i) = -mu0 Ms sum_j N(r_i - r_j) m_j,  */
+/* summed over the magnetic cells directly (O(N_c^2), no FFT); for two sublattices m_j is the   */
+/* total moment m1 + m2, as for the diagonal factors.                                           */
+/* ------------------------------------------------------------------------------------------- */
+
+/* Newell's f, even in every argument */
+static double newell_f(double x, double y, double z)
+{
+    x = fabs(x);
+    y = fabs(y);
+    z = fabs(z);
+    const double x2 = x * x, y2 = y * y, z2 = z * z, R = sqrt(x2 + y2 + z2);
+    double t = (2.0 * x2 - y2 - z2) * R / 6.0;
+    if (y > 0.0 && x2 + z2 > 0.0) t += 0.5 * y * (z2 - x2) * asinh(y / sqrt(x2 + z2));
+    if (z > 0.0 && x2 + y2 > 0.0) t += 0.5 * z * (y2 - x2) * asinh(z / sqrt(x2 + y2));
+    if (x > 0.0 && y > 0.0 && z > 0.0) t -= x * y * z * atan(y * z / (x * R));
+    return t;
+}
+
+/* Newell's g, odd in x and in y, even in z */
+static double newell_g(double x, double y, double z)
+{
+    const double sgn = (x < 0.0 ? -1.0 : 1.0) * (y < 0.0 ? -1.0 : 1.0);
+    x = fabs(x);
+    y = fabs(y);
+    z = fabs(z);
+    const double x2 = x * x, y2 = y * y, z2 = z * z, R = sqrt(x2 + y2 + z2);
+    double t = -x * y * R / 3.0;
+    if (z > 0.0 && x2 + y2 > 0.0) t += x * y * z * asinh(z / sqrt(x2 + y2));
+    if (x > 0.0 && y2 + z2 > 0.0) t += y / 6.0 * (3.0 * z2 - y2) * asinh(x / sqrt(y2 + z2));
+    if (y > 0.0 && x2 + z2 > 0.0) t += x / 6.0 * (3.0 * z2 - x2) * asinh(y / sqrt(x2 + z2));
+    if (x > 0.0 && y > 0.0 && z > 0.0) {
+        t -= z2 * z / 6.0 * atan(x * y / (z * R));
+        t -= 0.5 * z * y2 * atan(x * z / (y * R));
+        t -= 0.5 * z * x2 * atan(y * z / (x * R));
+    }
+    return sgn * t;
+}
+
+/* D_dx D_dy D_dz q(X, Y, Z) / (4 pi dx dy dz) for q = f (which = 0) or g (which = 1) */
+static double newell_diff(int which, double X, double Y, double Z, double dx, double dy,
+                          double dz)
+{
+    static const double w[3] = {-1.0, 2.0, -1.0};
+    double s = 0.0;
+    for (int i = 0; i < 3; i++)
+        for (int j = 0; j < 3; j++)
+            for (int k = 0; k < 3; k++) {
+                const double x = X + (i - 1) * dx, y = Y + (j - 1) * dy, z = Z + (k - 1) * dz;
+                s += w[i] * w[j] * w[k] * (which ? newell_g(x, y, z) : newell_f(x, y, z));
+            }
+    return s / (4.0 * 3.14159265358979323846 * dx * dy * dz);
+}
+
+/* The cell-pair tensor of every displacement (X, Y, Z) = (i cx, j cy, k cz), |i| < nx,
+   |j| < ny, |k| < nz: out[c * ND + ((k + nz - 1) * (2 ny - 1) + j + ny - 1) * (2 nx - 1) +
+   i + nx - 1] with ND = (2nx-1)(2ny-1)(2nz-1) and components c = xx, yy, zz, xy, xz, yz. */
+void orc_demag_tensor(int nx, int ny, int nz, double cx, double cy, double cz, double *out)
+{
+    const long Lx = 2L * nx - 1, Ly = 2L * ny - 1, Lz = 2L * nz - 1, ND = Lx * Ly * Lz;
+#pragma omp parallel for schedule(dynamic)
+    for (long k = 0; k < Lz; k++)
+        for (long j = 0; j < Ly; j++)
+            for (long i = 0; i < Lx; i++) {
+                const double X = (double)(i - (nx - 1)) * cx, Y = (double)(j - (ny - 1)) * cy,
+                             Z = (double)(k - (nz - 1)) * cz;
+                const long o = (k * Ly + j) * Lx + i;
+                out[0 * ND + o] = newell_diff(0, X, Y, Z, cx, cy, cz);
+                out[1 * ND + o] = newell_diff(0, Y, X, Z, cy, cx, cz);
+                out[2 * ND + o] = newell_diff(0, Z, Y, X, cz, cy, cx);
+                out[3 * ND + o] = newell_diff(1, X, Y, Z, cx, cy, cz);
+                out[4 * ND + o] = newell_diff(1, X, Z, Y, cx, cz, cy);
+                out[5 * ND + o] = newell_diff(1, Y, Z, X, cy, cz, cx);
+            }
+}
+
+/* Demag field of the total moment at every magnetic cell (dense box, 3 * nbox, zero outside
+   the mask), by the direct sum over the magnetic cells. */
+static void demag_field(const orc_problem *P, const double *m, double *bd)
+{
+    const int nx = P->nx, ny = P->ny, nz = P->nz, ns = P->nsub;
+    const long nbox = (long)nx * ny * nz;
+    const long Lx = 2L * nx - 1, Ly = 2L * ny - 1, ND = Lx * Ly * (2L * nz - 1);
+    const double dmg = ORC_MU0 * P->Ms;
+#pragma omp parallel for schedule(dynamic)
+    for (long ci = 0; ci < nbox; ci++) {
+        bd[ci] = bd[nbox + ci] = bd[2 * nbox + ci] = 0.0;
+        if (!P->mask[ci]) continue;
+        const long xi = ci % nx, yi = (ci / nx) % ny, zi = ci / ((long)nx * ny);
+        double h[3] = {0.0, 0.0, 0.0};
+        for (long cj = 0; cj < nbox; cj++) {
+            if (!P->mask[cj]) continue;
+            const long xj = cj % nx, yj = (cj / nx) % ny, zj = cj / ((long)nx * ny);
+            const long o = ((zi - zj + nz - 1) * Ly + (yi - yj + ny - 1)) * Lx + (xi - xj + nx - 1);
+            double mj[3] = {0.0, 0.0, 0.0};
+            for (int s = 0; s < ns; s++)
+                for (int k = 0; k < 3; k++) mj[k] += m[(s * 3 + k) * nbox + cj];
+            const double xx = P->demag[o], yy = P->demag[ND + o], zz = P->demag[2 * ND + o];
+            const double xy = P->demag[3 * ND + o], xz = P->demag[4 * ND + o],
+                         yz = P->demag[5 * ND + o];
+            h[0] += xx * mj[0] + xy * mj[1] + xz * mj[2];
+            h[1] += xy * mj[0] + yy * mj[1] + yz * mj[2];
+            h[2] += xz * mj[0] + yz * mj[1] + zz * mj[2];
+        }
+        for (int k = 0; k < 3; k++) bd[k * nbox + ci] = -dmg * h[k];
+    }
+}
+
+/* Exported for the tests: the full demag field (T) of the state m (dense box). */
+int orc_demag_field(const orc_problem *P, const double *m, double *bd)
+{
+    if (!P->demag) return ORC_EINVAL;
+    demag_field(P, m, bd);
+    return ORC_OK;
+}
+
 /* Backward (feedback) coupling of mode n: gb~ if given, else the forward g~. */
 static double gback_re(const orc_problem *P, int n) { return P->gb_re ? P->gb_re[n] : P->g_re[n]; }
 static double gback_im(const orc_problem *P, int n) { return P->gb_im ? P->gb_im[n] : P->g_im[n]; }
@@ -196,6 +321,12 @@ int orc_rhs(const orc_problem *P, const double *m, const double *a, double *dm, 
         double re_ga = gback_re(P, n) * a[2 * n] - gback_im(P, n) * a[2 * n + 1];
         hrf[n] = 2.0 / P->gamma * re_ga;
     }
+    double *bd = NULL;   /* full demag field of the total moment */
+    if (P->demag) {
+        bd = malloc(3 * nbox * sizeof(double));
+        if (!bd) return ORC_ENOMEM;
+        demag_field(P, m, bd);
+    }
 
 #pragma omp parallel for schedule(static)
     for (int z = 0; z < nz; z++) {
@@ -228,8 +359,9 @@ int orc_rhs(const orc_problem *P, const double *m, const double *a, double *dm, 
                     /* uniaxial anisotropy (2 K_u / M_s)(m . k) k */
                     double mk = mi[0] * P->ku[0] + mi[1] * P->ku[1] + mi[2] * P->ku[2];
                     for (int k = 0; k < 3; k++) B[k] += anis * mk * P->ku[k];
-                    /* Zeeman and diagonal demag of the total moment */
-                    for (int k = 0; k < 3; k++) B[k] += P->B0[k] - dmg * P->Nd[k] * mtot[k];
+                    /* Zeeman and demag of the total moment (diagonal factors or full) */
+                    for (int k = 0; k < 3; k++)
+                        B[k] += P->B0[k] + (bd ? bd[k * nbox + c] : -dmg * P->Nd[k] * mtot[k]);
                     /* inter-sublattice exchange field */
                     if (ns == 2) {
                         const double *mo = m + (long)(1 - s) * 3 * nbox;
@@ -249,6 +381,7 @@ int orc_rhs(const orc_problem *P, const double *m, const double *a, double *dm, 
         }
     }
 
+    free(bd);
     orc_overlap(P, m, mm);
     for (int n = 0; n < N; n++) {
         double ar = a[2 * n], ai = a[2 * n + 1];
@@ -569,6 +702,7 @@ int orc_rhs_vjp(const orc_problem *P, const double *m, const double *a, const do
     const double anis = 2.0 * P->Ku / P->Ms;
     const double dmg = ORC_MU0 * P->Ms;
     if (N > 64 || ns < 1 || ns > 2) return ORC_EINVAL;
+    if (P->demag) return ORC_EINVAL;   /* the adjoint covers the diagonal demag factors only */
     const int want_u = P->u && G && G->u;
     double hrf[64], hbar[64], mm[128];
     for (int n = 0; n < N; n++) {

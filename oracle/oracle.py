@@ -56,7 +56,8 @@ class _Problem(C.Structure):
                 ("drive_re", C.POINTER(C.c_double)), ("drive_im", C.POINTER(C.c_double)),
                 ("drive_t0", C.c_double), ("drive_sigma", C.c_double),
                 ("gb_re", C.POINTER(C.c_double)), ("gb_im", C.POINTER(C.c_double)),
-                ("kerr", C.POINTER(C.c_double)), ("cavity_frozen", C.c_int)]
+                ("kerr", C.POINTER(C.c_double)), ("cavity_frozen", C.c_int),
+                ("demag", C.POINTER(C.c_double))]
 
 
 class _Solver(C.Structure):
@@ -106,6 +107,10 @@ def lib():
                                        C.c_long, C.POINTER(_Log)]
         _lib.orc_run_split.restype = C.c_int
         _lib.orc_tableau.argtypes = [dp, dp, dp]
+        _lib.orc_demag_tensor.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double, C.c_double,
+                                          C.c_double, dp]
+        _lib.orc_demag_field.argtypes = [P, dp, dp]
+        _lib.orc_demag_field.restype = C.c_int
         G = C.POINTER(_Grads)
         _lib.orc_rhs_vjp.argtypes = [P, dp, dp, dp, dp, dp, dp, G]
         _lib.orc_rhs_vjp.restype = C.c_int
@@ -168,6 +173,11 @@ class OracleProblem:
             s.kerr = _dptr(self.kerr)
         else:
             s.kerr = C.POINTER(C.c_double)()
+        if getattr(p, "full_demag", False):
+            self.demag = demag_tensor(p.nx, p.ny, p.nz, p.cx, p.cy, p.cz)
+            s.demag = _dptr(self.demag)
+        else:
+            s.demag = C.POINTER(C.c_double)()
         self.s = s
         self.solver = _Solver(p.rtol, p.a_ref, p.dt_min, p.dt_max)
 
@@ -180,6 +190,27 @@ class OracleProblem:
 
     def a0(self) -> np.ndarray:
         return pack_a(self.p.a0)
+
+
+def demag_tensor(nx, ny, nz, cx, cy, cz) -> np.ndarray:
+    """Cell-pair demag tensor (Newell, Williams & Dunlop 1993) of every displacement of an
+    nx x ny x nz grid of cx x cy x cz cells: array (6, 2nz-1, 2ny-1, 2nx-1), components
+    xx, yy, zz, xy, xz, yz, index [c, k + nz-1, j + ny-1, i + nx-1] for displacement
+    (i cx, j cy, k cz)."""
+    out = np.empty(6 * (2 * nx - 1) * (2 * ny - 1) * (2 * nz - 1))
+    lib().orc_demag_tensor(int(nx), int(ny), int(nz), float(cx), float(cy), float(cz),
+                           _dptr(out))
+    return out.reshape(6, 2 * nz - 1, 2 * ny - 1, 2 * nx - 1)
+
+
+def demag_field(op: OracleProblem, m: np.ndarray) -> np.ndarray:
+    """Full demag field (T) of state m (flat FP64, nsub*3*nbox) at every cell: (3, nbox)."""
+    m = np.ascontiguousarray(m, np.float64).reshape(-1)
+    out = np.empty(3 * op.nbox)
+    rc = lib().orc_demag_field(op.ref, _dptr(m), _dptr(out))
+    if rc:
+        raise RuntimeError("orc_demag_field: the problem has no full demag")
+    return out.reshape(3, op.nbox)
 
 
 def pack_a(a) -> np.ndarray:

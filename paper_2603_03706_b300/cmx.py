@@ -112,6 +112,9 @@ SIGNATURES = {
     "cmx_debug_skip_arrival": (C.c_int, [_P, C.c_int]),
     "cmx_get_tiling": (C.c_int, [_P, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int),
                                    C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+    "cmx_set_demag": (C.c_int, [_P, C.c_int]),
+    "cmx_plan_tiling": (C.c_int, [C.POINTER(Grid), C.c_void_p, C.c_int, C.c_int, C.c_int,
+                                  C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]),
     "cmx_last_error": (C.c_char_p, [_P]),
     "cmx_status_string": (C.c_char_p, [C.c_int]),
     "cmx_batch_create": (C.c_int, [C.POINTER(Instance), C.c_int, C.POINTER(Solver),
@@ -262,6 +265,8 @@ class Simulation:
             sim.set_backward_coupling(p.g_back)
         if getattr(p, "kerr", None) is not None:
             sim.set_kerr(p.kerr)
+        if getattr(p, "full_demag", False):
+            sim.set_demag(True)
         return sim
 
     # -- lifetime ----------------------------------------------------------------------------
@@ -488,6 +493,10 @@ class Simulation:
         """cmx_set_split: operator-split scheme with interval ds (0: the coupled scheme)."""
         self._check(load().cmx_set_split(self.h, float(ds)), "set_split")
 
+    def set_demag(self, full: bool):
+        """cmx_set_demag: full magnetostatic demag (True) or the diagonal factors (False)."""
+        self._check(load().cmx_set_demag(self.h, 1 if full else 0), "set_demag")
+
     def set_backward_coupling(self, gb=None):
         """cmx_set_backward_coupling: complex backward coefficients gb~_n of the feedback field
         (nonreciprocal coupling); None restores reciprocal coupling."""
@@ -525,13 +534,14 @@ class Simulation:
                                          float(sigma)), "set_drive")
 
     def autotune(self, attempts: int = 20) -> dict:
-        """cmx_autotune: time the compiled windows from the current state, keep the fastest."""
+        """cmx_autotune: time the compiled tiles (and, for a small grid, the single-block
+        integrator) from the current state, keep the fastest (bx = by = 0: single block)."""
         t = Tiling()
-        us = np.zeros(3)
+        us = np.zeros(4)
         self._check(load().cmx_autotune(self.h, int(attempts), C.byref(t), us.ctypes.data),
                     "autotune")
         return dict(bx=t.bx, by=t.by, bz=t.bz, us_per_attempt=dict(
-            zip(("32x8", "32x16", "64x4"), [float(v) for v in us])))
+            zip(("32x4", "32x8", "32x16", "single_block"), [float(v) for v in us])))
 
     def get_tiling(self) -> dict:
         v = [C.c_int() for _ in range(6)]
@@ -724,6 +734,19 @@ class BatchSimulation:
         v = [C.c_int(), C.c_int(), C.c_int(), C.c_longlong(), C.c_int()]
         self._check(load().cmx_batch_info(self.h, *[C.byref(x) for x in v]), "batch_info")
         return dict(zip(("teams", "team_size", "blocks", "cells", "graph"), [x.value for x in v]))
+
+
+def plan_tiling(p, bx: int, by: int, blocks: int) -> dict:
+    """cmx_plan_tiling (host only): segments and stored cells of the partition of workloads
+    Problem p into `blocks` blocks of bx x by tiles; raises CmxError when it does not fit."""
+    g = Grid(p.nx, p.ny, p.nz, p.cx, p.cy, p.cz, p.nsub)
+    mask = np.ascontiguousarray(np.asarray(p.mask, np.uint8).reshape(-1))
+    nseg, nst = C.c_longlong(), C.c_longlong()
+    rc = load().cmx_plan_tiling(C.byref(g), mask.ctypes.data, int(bx), int(by), int(blocks),
+                                C.byref(nseg), C.byref(nst))
+    if rc != OK:
+        raise CmxError(rc, "cmx_plan_tiling: " + load().cmx_status_string(rc).decode())
+    return dict(segments=nseg.value, stored=nst.value)
 
 
 def eval_rhs_noalloc(p, m_dev, dm_dev, a=None, stream=None, u_dev=None):

@@ -140,7 +140,8 @@ int ensure_reverse(cmx_problem *h)
     // reverse partition: 32 x 8 windows, as many resident blocks as the kernel allows
     const int occ = reverse_blocks_per_sm(h->grid.nsub, h->u != nullptr);
     if (occ <= 0) return fail(h, CMX_ECUDA, "reverse kernel occupancy query failed");
-    const std::vector<Column> cols = build_columns(h->lay, REV_WX, REV_WY);
+    // (a window of REV_WX x REV_WY threads computes its interior, rim excluded)
+    const std::vector<Column> cols = build_columns(h->lay, REV_WX - 2, REV_WY - 2);
     long long P = 0;
     for (const Column &c : cols) P += c.zhi - c.zlo;
     const int bz = std::max(1, h->bz);
@@ -148,7 +149,9 @@ int ensure_reverse(cmx_problem *h)
         1, std::min<long long>((long long)occ * h->nsm, (P + bz - 1) / bz));
     std::vector<int4> segs;
     std::vector<int> begin;
-    build_segments(cols, blocks, segs, begin);
+    if (!build_segments(cols, blocks, segs, begin))
+        return fail(h, CMX_EINVAL, "reverse partition: %zu columns do not fit %d blocks",
+                    cols.size(), blocks);
     if (segs.empty()) return fail(h, CMX_EINVAL, "no tiles");
     CU(dalloc(&s->tiles, segs.size()));
     CU(dalloc(&s->seg_begin, begin.size()));
@@ -196,6 +199,8 @@ int cmx_adjoint_record(cmx_problem *h, int every, long long max_steps)
         return fail(h, CMX_EINVAL, "cmx_adjoint_record must follow cmx_set_state directly");
     if (h->base.split_dt > 0.0)
         return fail(h, CMX_EINVAL, "the adjoint differentiates the coupled scheme, not the split one");
+    if (h->base.fd)
+        return fail(h, CMX_EINVAL, "the adjoint covers the diagonal demag factors only");
     if (!h->adj) h->adj = new AdjState();
     AdjState *s = h->adj;
     const int nq = 3 * h->grid.nsub, N = std::max(1, h->N);

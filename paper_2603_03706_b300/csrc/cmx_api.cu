@@ -109,33 +109,6 @@ int setup_tiling(cmx_problem *h, const cmx_tiling *t)
 {
     int bx = 32, by = 8, bz = 0, bps = 0;
     h->bps_cap = t ? t->blocks_per_sm : 0;
-    if (h->quad) {
-        int wq = 0, wy = 0;
-        if (t) {
-            bz = t->bz;
-            bps = t->blocks_per_sm;
-        }
-        if (bz <= 0) bz = 4;
-        wq = 16;   // default quad window: 64 x 16 cells
-        wy = 16;
-        if (t && (t->bx || t->by)) {
-            if (t->bx % 4 || !quad_shape_supported(t->bx / 4, t->by))
-                return fail(h, CMX_EINVAL,
-                            "quad window %dx%d: bx must be a multiple of 4 with (bx/4)*by a "
-                            "multiple of 32, at most 256 threads, by <= 16", t->bx, t->by);
-            wq = t->bx / 4;
-            wy = t->by;
-        }
-        int occ = quad_blocks_per_sm(wq, wy, h->u ? h->N : 0);
-        if (occ <= 0) return fail(h, CMX_ECUDA, "occupancy query failed for quad %dx%d", wq, wy);
-        if (bps > 0) occ = std::min(occ, bps);
-        const std::vector<Column> cols = build_columns(h->lay, 4 * (wq - 2) + 2, wy);
-        long long P = 0;
-        for (const Column &c : cols) P += c.zhi - c.zlo;
-        const long long cap = (long long)occ * h->nsm;
-        const int blocks = (int)std::max<long long>(1, std::min<long long>(cap, (P + bz - 1) / bz));
-        return install_tiling(h, cols, blocks, 4 * wq, wy, bz, occ);
-    }
     if (t && (t->bx || t->by)) {
         bx = t->bx;
         by = t->by;
@@ -146,8 +119,8 @@ int setup_tiling(cmx_problem *h, const cmx_tiling *t)
     }
     if (!tile_shape_supported(h->grid.nsub, bx, by))
         return fail(h, CMX_EINVAL,
-                    "block window %dx%d is not compiled for nsub=%d (32x8, 32x16, 64x4; two "
-                    "sublattices: 32x8, 64x4)", bx, by, h->grid.nsub);
+                    "tile %dx%d is not compiled for nsub=%d (32x4, 32x8, 32x16)", bx, by,
+                    h->grid.nsub);
     int occ = single_blocks_per_sm(h->grid.nsub, bx, by, h->N > 0 && h->u != nullptr);
     if (occ <= 0) return fail(h, CMX_ECUDA, "occupancy query failed for %dx%d", bx, by);
     if (bps > 0) occ = std::min(occ, bps);
@@ -167,7 +140,10 @@ int install_tiling(cmx_problem *h, const std::vector<Column> &cols, int blocks, 
 {
     std::vector<int4> segs;
     std::vector<int> begin;
-    build_segments(cols, blocks, segs, begin);
+    if (!build_segments(cols, blocks, segs, begin))
+        return fail(h, CMX_EINVAL,
+                    "%zu tile columns do not fit %d blocks of at most %d segments each "
+                    "(use a larger tile)", cols.size(), blocks, MAX_BLOCK_SEGMENTS);
     if (segs.empty()) return fail(h, CMX_EINVAL, "no tiles");
     if (h->tiles) cudaFree(h->tiles);
     if (h->seg_begin) cudaFree(h->seg_begin);
@@ -187,6 +163,47 @@ int install_tiling(cmx_problem *h, const std::vector<Column> &cols, int blocks, 
     return CMX_OK;
 }
 
+// Single-block integrator: eligible when the magnetic cells' state, slopes, profiles and
+// neighbour table fit one block's shared memory (at most SMALL_SMEM bytes); used unless the caller
+// asked for a tile shape.  Builds the magnetic cells' stored indices and neighbour table.
+constexpr size_t SMALL_SMEM = 200 * 1024;
+
+int setup_small(cmx_problem *h, const cmx_tiling *t)
+{
+    const int nm = h->ncell_mag;
+    const bool has_u = h->N > 0 && h->u != nullptr;
+    int optin = 0;
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->dev);
+    const size_t need = small_smem_bytes(nm, h->grid.nsub, h->N, has_u);
+    h->small_ok = need <= SMALL_SMEM && need + 8192 <= (size_t)optin;
+    h->use_small = h->small_ok && !(t && (t->bx || t->by));
+    h->small_default = h->use_small;
+    if (!h->small_ok) return CMX_OK;
+    const Layout &L = h->lay;
+    const int nx = L.nx, ny = L.ny, nz = L.nz;
+    std::vector<int> small_of_box((size_t)nx * ny * nz, -1), sidx(nm), snb(6 * (size_t)nm, -1);
+    std::vector<int> box(nm);
+    int k = 0;
+    for (int i = 0; i < L.ncell; i++)
+        if (L.active[i]) {
+            sidx[k] = i;
+            box[k] = L.box_of_cell[i];
+            small_of_box[L.box_of_cell[i]] = k++;
+        }
+    for (int i = 0; i < nm; i++) {
+        const int b = box[i], x = b % nx, y = (b / nx) % ny, z = b / (nx * ny);
+        const int nbx[6] = {x > 0 ? b - 1 : -1, x + 1 < nx ? b + 1 : -1,
+                            y > 0 ? b - nx : -1, y + 1 < ny ? b + nx : -1,
+                            z > 0 ? b - nx * ny : -1, z + 1 < nz ? b + nx * ny : -1};
+        for (int d = 0; d < 6; d++) snb[(size_t)d * nm + i] = nbx[d] >= 0 ? small_of_box[nbx[d]] : -1;
+    }
+    if (dalloc(&h->small_idx, nm) != cudaSuccess || dalloc(&h->small_nb, 6 * (size_t)nm) != cudaSuccess)
+        return fail(h, CMX_ENOMEM, "small-grid tables");
+    cudaMemcpy(h->small_idx, sidx.data(), nm * sizeof(int), cudaMemcpyHostToDevice);
+    cudaMemcpy(h->small_nb, snb.data(), snb.size() * sizeof(int), cudaMemcpyHostToDevice);
+    return CMX_OK;
+}
+
 }  // namespace
 
 Ctx cmx_host::make_ctx(const cmx_problem *h)
@@ -202,12 +219,20 @@ Ctx cmx_host::make_ctx(const cmx_problem *h)
 
 namespace {
 
+// The single-block integrator runs plain integrations of small grids; a run that records for
+// the adjoint (checkpoints or stage values) takes the tiled kernel, which writes those stores.
+bool small_run(const cmx_problem *h, const Ctx &c)
+{
+    return h->use_small && !c.traj_m && !c.rec_m && !c.stage_only;
+}
+
 int launch(cmx_problem *h, const PrepArgs &pa, const Ctx &c)
 {
     prep_kernel<<<1, 1, 0, h->stream>>>(c.ctl, pa);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return fail(h, CMX_ECUDA, "prep launch: %s", cudaGetErrorString(e));
-    e = launch_single(c, h->bx, h->by, h->blocks, h->stream);
+    e = small_run(h, c) ? launch_small(c, h->small_idx, h->small_nb, h->ncell_mag, h->stream)
+                        : launch_single(c, h->bx, h->by, h->blocks, h->stream);
     if (e != cudaSuccess) return fail(h, CMX_ECUDA, "integrator launch: %s", cudaGetErrorString(e));
     h->launches++;
     return CMX_OK;
@@ -296,7 +321,8 @@ int drive(cmx_problem *h, double T, long long max_attempts, int set_replay, long
 void free_all(cmx_problem *h)
 {
     void *ptrs[] = {h->rows, h->active, h->box_of_cell, h->tiles, h->seg_begin, h->u,
-                    h->mbuf[0], h->mbuf[1],
+                    h->mbuf[0], h->mbuf[1], h->msv[0], h->msv[1], h->esbuf, h->small_idx,
+                    h->small_nb,
                     h->ctl, h->log, h->log_a, h->log_mm, h->tr_t, h->tr_a,
                     h->tr_mm, h->replay_dts, h->dense, h->ev_m, h->ev_k, h->ev_ctl};
     for (void *p : ptrs)
@@ -304,6 +330,7 @@ void free_all(cmx_problem *h)
     for (float *p : h->kbuf)
         if (p) cudaFree(p);
     adj_free(h);
+    demag_release(h);
 }
 
 int reset_ctl(cmx_problem *h, const double *a, double t)
@@ -397,12 +424,10 @@ int cmx_create(const cmx_grid *grid, const uint8_t *mask, const cmx_material *ma
     cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, h->dev);
     if (!coop) return bail(CMX_ECUDA);
 
-    // window kind: one cell per thread unless quad windows are asked for
+    // one cell per thread (the only kind of tile)
     const int tq = tiling ? tiling->quad : 0;
-    if (tq != 0 && tq != 1 && tq != 4) return bail(CMX_EINVAL);
-    if (tq == 4 && grid->nsub != 1) return bail(CMX_EINVAL);
-    h->quad = tq == 4;
-    build_layout(h->lay, grid->nx, grid->ny, grid->nz, mask, h->quad ? 4 : 1);
+    if (tq != 0 && tq != 1) return bail(CMX_EINVAL);
+    build_layout(h->lay, grid->nx, grid->ny, grid->nz, mask);
     h->ncell = h->lay.ncell;
     h->ncell_mag = h->lay.ncell_mag;
     h->holes = h->lay.holes;
@@ -416,15 +441,19 @@ int cmx_create(const cmx_grid *grid, const uint8_t *mask, const cmx_material *ma
         return bail(CMX_ENOMEM);
     for (int j = 0; j < 7; j++)
         if (dalloc(&h->kbuf[j], nq * nc)) return bail(CMX_ENOMEM);
+    if (dalloc(&h->msv[0], nq * nc) || dalloc(&h->msv[1], nq * nc) || dalloc(&h->esbuf, nq * nc))
+        return bail(CMX_ENOMEM);
     cudaMemcpy(h->rows, h->lay.rows.data(), h->lay.rows.size() * sizeof(int2),
                cudaMemcpyHostToDevice);
     cudaMemcpy(h->box_of_cell, h->lay.box_of_cell.data(), nc * sizeof(int), cudaMemcpyHostToDevice);
-    if (h->holes) {
+    if (h->lay.padded) {   // gather / scatter skip inactive stored cells
         const std::vector<uint32_t> bits = active_bits(h->lay);
         if (dalloc(&h->active, bits.size())) return bail(CMX_ENOMEM);
         cudaMemcpy(h->active, bits.data(), bits.size() * sizeof(uint32_t), cudaMemcpyHostToDevice);
     }
     for (int j = 0; j < 7; j++) cudaMemset(h->kbuf[j], 0, nq * nc * sizeof(float));
+    for (int j = 0; j < 2; j++) cudaMemset(h->msv[j], 0, nq * nc * sizeof(float));
+    cudaMemset(h->esbuf, 0, nq * nc * sizeof(float));
     cudaMemset(h->mbuf[1], 0, nq * nc * sizeof(float));
     // mode profiles, compacted (umax bounds the overlap sums; device profiles: |u| <= 256)
     double umax = 1.0;
@@ -465,11 +494,14 @@ int cmx_create(const cmx_grid *grid, const uint8_t *mask, const cmx_material *ma
     c.ncell = h->ncell;
     c.ncell_mag = h->ncell_mag;
     c.rows = h->rows;
-    c.active = h->active;
+    c.active = h->holes ? h->active : nullptr;   // the row spans exclude the padding
     c.u = h->u;
     c.m[0] = h->mbuf[0];
     c.m[1] = h->mbuf[1];
     for (int j = 0; j < 7; j++) c.k[j] = h->kbuf[j];
+    c.msv[0] = h->msv[0];
+    c.msv[1] = h->msv[1];
+    c.es = h->esbuf;
     const double exch = 2.0 * mat->Aex / mat->Ms;
     c.wx = (float)(exch / (grid->cx * grid->cx));
     c.wy = (float)(exch / (grid->cy * grid->cy));
@@ -510,9 +542,10 @@ int cmx_create(const cmx_grid *grid, const uint8_t *mask, const cmx_material *ma
     c.tr_a = h->tr_a;
     c.tr_mm = h->tr_mm;
     c.tr_cap = solver->trace_cap;
-    c.quad = h->quad;
 
     int rc = setup_tiling(h, tiling);
+    if (rc) return bail(rc);
+    rc = setup_small(h, tiling);
     if (rc) return bail(rc);
 
     // initial state: +z (sublattice 2: -z), a = 0
@@ -815,10 +848,6 @@ int cmx_set_drive(cmx_problem *h, const double *eta_re, const double *eta_im, do
 int cmx_autotune(cmx_problem *h, int attempts, cmx_tiling *chosen, double *us_per_attempt)
 {
     if (!h || attempts <= 0) return fail(h, CMX_EINVAL, "bad argument");
-    if (h->quad) {
-        if (chosen) *chosen = cmx_tiling{h->bx, h->by, h->bz, 0, 4};
-        return CMX_OK;
-    }
     Ctl saved;
     int rc = read_ctl(h, &saved);
     if (rc) return rc;
@@ -840,17 +869,21 @@ int cmx_autotune(cmx_problem *h, int attempts, cmx_tiling *chosen, double *us_pe
         cudaMemcpyAsync(h->ctl, &saved, sizeof saved, cudaMemcpyHostToDevice, st);
         return cudaStreamSynchronize(st);
     };
-    static const int cand[3][2] = {{32, 8}, {32, 16}, {64, 4}};
+    // candidates 0..2: the compiled tiles; 3: the single-block integrator (small grids only)
+    static const int cand[3][2] = {{32, 4}, {32, 8}, {32, 16}};
     const int bz = h->bz, bps = h->bps_cap;
-    double best = 1e300;
+    double best = 1e300, tus[4];
     int bi = 0;
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    for (int ci = 0; ci < 3; ci++) {
+    for (int ci = 0; ci < 4; ci++) {
         double us = NAN;
-        cmx_tiling t{cand[ci][0], cand[ci][1], bz, bps, 1};
-        if (tile_shape_supported(h->grid.nsub, t.bx, t.by) && setup_tiling(h, &t) == CMX_OK) {
+        const bool small = ci == 3;
+        cmx_tiling t{small ? 0 : cand[ci][0], small ? 0 : cand[ci][1], bz, bps, 1};
+        h->use_small = small;
+        if (small ? (h->small_ok && !h->base.fd)
+                  : (tile_shape_supported(h->grid.nsub, t.bx, t.by) && setup_tiling(h, &t) == CMX_OK)) {
             PrepArgs pa{};
             pa.T = INFINITY;
             pa.set_replay = -1;
@@ -869,6 +902,7 @@ int cmx_autotune(cmx_problem *h, int attempts, cmx_tiling *chosen, double *us_pe
                 us = 1e3 * ms / (double)(after.attempts - saved.attempts - 1);
             }
         }
+        tus[ci] = us;
         if (us_per_attempt) us_per_attempt[ci] = us;
         if (us == us && us < best) {
             best = us;
@@ -881,10 +915,41 @@ int cmx_autotune(cmx_problem *h, int attempts, cmx_tiling *chosen, double *us_pe
     cudaFree(m_save);
     cudaFree(k_save);
     if (!(best < 1e300)) return fail(h, CMX_ECUDA, "autotune: no window could be timed");
-    cmx_tiling t{cand[bi][0], cand[bi][1], bz, bps, 1};
+    // the tiled partition stays installed in every case (the adjoint's recorded runs use it)
+    int tb = bi == 3 ? 1 : bi;
+    if (bi == 3) {   // the single-block integrator won: keep the best tile for recorded runs
+        double bt = 1e300;
+        for (int ci = 0; ci < 3; ci++)
+            if (tus[ci] == tus[ci] && tus[ci] < bt) {
+                bt = tus[ci];
+                tb = ci;
+            }
+    }
+    cmx_tiling t{cand[tb][0], cand[tb][1], bz, bps, 1};
     rc = setup_tiling(h, &t);
     if (rc) return rc;
-    if (chosen) *chosen = t;
+    h->use_small = bi == 3;
+    h->small_default = h->use_small;
+    if (chosen) *chosen = bi == 3 ? cmx_tiling{0, 0, bz, bps, 1} : t;
+    return CMX_OK;
+}
+
+int cmx_plan_tiling(const cmx_grid *grid, const uint8_t *mask, int bx, int by, int blocks,
+                    long long *n_segments, long long *n_stored)
+{
+    if (!grid || !mask || blocks <= 0 || grid->nx <= 0 || grid->ny <= 0 || grid->nz <= 0 ||
+        grid->nx > 65532 || (grid->nsub != 1 && grid->nsub != 2))
+        return CMX_EINVAL;
+    if ((long long)grid->nx * grid->ny * grid->nz > (1LL << 31) - 1) return CMX_EINVAL;
+    if (!tile_shape_supported(grid->nsub, bx, by)) return CMX_EINVAL;
+    Layout lay;
+    build_layout(lay, grid->nx, grid->ny, grid->nz, mask);
+    if (n_stored) *n_stored = lay.ncell;
+    if (lay.ncell_mag == 0) return CMX_EINVAL;
+    std::vector<int4> segs;
+    std::vector<int> begin;
+    if (!build_segments(build_columns(lay, bx, by), blocks, segs, begin)) return CMX_EINVAL;
+    if (n_segments) *n_segments = (long long)segs.size();
     return CMX_OK;
 }
 
@@ -892,12 +957,12 @@ int cmx_get_tiling(const cmx_problem *h, int *bx, int *by, int *bz, int *blocks,
                    int *quad)
 {
     if (!h) return CMX_EINVAL;
-    if (quad) *quad = h->quad ? 4 : 1;
-    if (bx) *bx = h->bx;
-    if (by) *by = h->by;
+    if (quad) *quad = 1;
+    if (bx) *bx = h->use_small ? 0 : h->bx;
+    if (by) *by = h->use_small ? 0 : h->by;
     if (bz) *bz = h->bz;
-    if (blocks) *blocks = h->blocks;
-    if (tiles) *tiles = h->ntiles;
+    if (blocks) *blocks = h->use_small ? 1 : h->blocks;
+    if (tiles) *tiles = h->use_small ? 0 : h->ntiles;
     return CMX_OK;
 }
 

@@ -8,7 +8,8 @@
 namespace cmx {
 
 template <int NS, int WX, int WY>
-__global__ void __launch_bounds__(WX *WY, (WX * WY <= 256 ? 2 : 1)) batch_kernel(BatchArgs B)
+__global__ void __launch_bounds__(WX *WY, (WX * WY <= 128 ? 4 : (WX * WY <= 256 ? 2 : 1)))
+    batch_kernel(BatchArgs B)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     auto &sm = *reinterpret_cast<StageSmem<NS, WX, WY, false> *>(smem_raw);
@@ -88,7 +89,7 @@ static int batch_occupancy_variant()
     return nb;
 }
 
-#define CMX_BATCH_VARIANTS(X) X(1, 32, 8) X(1, 32, 16) X(1, 64, 4) X(2, 32, 8) X(2, 64, 4)
+#define CMX_BATCH_VARIANTS(X) X(1, 32, 4) X(1, 32, 8) X(1, 32, 16) X(2, 32, 4) X(2, 32, 8)
 
 cudaError_t launch_batch(const BatchArgs &b, int nsub, int bx, int by, int blocks, cudaStream_t s)
 {

@@ -29,9 +29,9 @@ struct Inst {
     std::vector<int4> segs;
     std::vector<int> begin;
     // offsets into the device pools
-    size_t o_m[2] = {0, 0}, o_k[7] = {}, o_rows = 0, o_box = 0, o_act = 0, o_seg = 0,
-           o_begin = 0, o_log = 0, o_loga = 0, o_tr = 0, o_tra = 0;
-    bool has_act = false;
+    size_t o_m[2] = {0, 0}, o_k[7] = {}, o_msv[2] = {0, 0}, o_es = 0, o_rows = 0, o_box = 0,
+           o_act = 0, o_seg = 0, o_begin = 0, o_log = 0, o_loga = 0, o_tr = 0, o_tra = 0;
+    bool has_act = false;        // active bitmask stored (padding or holes)
 };
 
 size_t up64(size_t n) { return (n + 63) & ~(size_t)63; }
@@ -263,7 +263,9 @@ int cmx_batch_create(const cmx_instance *in, int n, const cmx_solver *solver,
     b->teams = G / K;
     b->blocks = b->teams * K;
     // partitions and queues (longest first onto the least loaded team)
-    for (Inst &I : b->inst) build_segments(build_columns(I.lay, b->bx, b->by), K, I.segs, I.begin);
+    for (Inst &I : b->inst)
+        if (!build_segments(build_columns(I.lay, b->bx, b->by), K, I.segs, I.begin))
+            return bail(CMX_EINVAL);   // too many tile columns for a team of K blocks
     std::vector<int> order(n);
     std::iota(order.begin(), order.end(), 0);
     std::stable_sort(order.begin(), order.end(), [&](int a, int c) {
@@ -295,10 +297,12 @@ int cmx_batch_create(const cmx_instance *in, int n, const cmx_solver *solver,
         const size_t nc = up64((size_t)I.lay.ncell);
         for (int s = 0; s < 2; s++) I.o_m[s] = nf, nf += nq * nc;
         for (int j = 0; j < 7; j++) I.o_k[j] = nf, nf += nq * nc;
+        for (int j = 0; j < 2; j++) I.o_msv[j] = nf, nf += nq * nc;
+        I.o_es = nf, nf += nq * nc;
         I.o_rows = nrows, nrows += I.lay.rows.size();
         I.o_box = nint, nint += I.lay.ncell;
         I.o_begin = nint, nint += I.begin.size();
-        I.has_act = I.lay.holes;
+        I.has_act = I.lay.padded;
         if (I.has_act) I.o_act = nact, nact += ((size_t)I.lay.ncell + 31) / 32;
         I.o_seg = nseg, nseg += I.segs.size();
         const int Q = 2 * std::max(1, I.N);
@@ -379,7 +383,7 @@ int cmx_batch_create(const cmx_instance *in, int n, const cmx_solver *solver,
         c.ncell = I.lay.ncell;
         c.ncell_mag = I.lay.ncell_mag;
         c.rows = b->rows + I.o_rows;
-        c.active = I.has_act ? b->act + I.o_act : nullptr;
+        c.active = I.lay.holes ? b->act + I.o_act : nullptr;   // the row spans exclude padding
         c.tiles = b->segs + I.o_seg;
         c.seg_begin = b->ipool + I.o_begin;
         c.ntiles = (int)I.segs.size();
@@ -389,6 +393,8 @@ int cmx_batch_create(const cmx_instance *in, int n, const cmx_solver *solver,
         c.m[0] = b->fpool + I.o_m[0];
         c.m[1] = b->fpool + I.o_m[1];
         for (int j = 0; j < 7; j++) c.k[j] = b->fpool + I.o_k[j];
+        for (int j = 0; j < 2; j++) c.msv[j] = b->fpool + I.o_msv[j];
+        c.es = b->fpool + I.o_es;
         const double exch = 2.0 * I.mat.Aex / I.mat.Ms;
         c.wx = (float)(exch / (I.grid.cx * I.grid.cx));
         c.wy = (float)(exch / (I.grid.cy * I.grid.cy));
@@ -587,7 +593,7 @@ int cmx_batch_autotune(const cmx_instance *inst, int n, const cmx_solver *solver
     std::vector<cmx_instance> sub;
     for (int i = 0; i < n; i += k) sub.push_back(inst[i]);
     const int nsub = inst[0].grid.nsub;
-    const int win[2][2] = {{32, 8}, {nsub == 1 ? 32 : 64, nsub == 1 ? 16 : 4}};
+    const int win[2][2] = {{32, 8}, {32, nsub == 1 ? 16 : 4}};
     const int teams[6] = {0, 1, 2, 4, 8, 16};
     cmx_solver sv = *solver;
     sv.log_cap = 0;

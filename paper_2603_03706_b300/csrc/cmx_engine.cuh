@@ -582,6 +582,12 @@ __device__ bool grid_barrier(const Ctx &c, const Team &tm, Local &L, int where)
     return s_ok > 0;
 }
 
+}  // namespace cmx
+
+#include "cmx_demag.cuh"
+
+namespace cmx {
+
 // Physical buffer of logical slope j (select rather than index the kernel-parameter array,
 // which keeps it out of local memory).
 __device__ __forceinline__ const float *slope_buffer(const Ctx &c, int kj)
@@ -608,16 +614,22 @@ __device__ bool run_stage(const Ctx &c, const Team &tm, SM &sm, Local &L, Coef &
     const int tid = threadIdx.x, N = c.nmodes;
     const float *mn = L.mcur ? c.m[1] : c.m[0];
     float *mnew = L.mcur ? c.m[0] : c.m[1];
+    // with full demag the stage's copies start after its demag passes (they use the pool)
+    begun = begun && !c.fd;
     if (!begun) {
         if (tid < 7) sm.kp[tid] = slope_buffer(c, L.kphys[tid]);
         __syncthreads();
-        stage_begin<S>(c, sm, mn, pp);
+        if (!c.fd) stage_begin<S>(c, sm, mn, pp);
     }
     if (S <= 2) {
         if (tid < 32) cavity_stage_value<S>(L, cf, tid, tid < 2 * N);
         if (S == 2 && tid >= 32 && tid < 32 + 36) attempt_coefficients(cf, L, L.h, tid - 32);
         if (S == 2 && tid == 96) cf.h = (float)L.h;
         __syncthreads();
+    }
+    if (c.fd) {
+        if (!demag_field<S>(c, tm, sm, L, cf, mn)) return false;
+        stage_begin<S>(c, sm, mn, pp);
     }
     Acc acc;
 #pragma unroll
@@ -647,7 +659,7 @@ __device__ bool run_stage(const Ctx &c, const Team &tm, SM &sm, Local &L, Coef &
             else w->remax[clr] = 0u;
         }
     }
-    if (S >= 2 && S < 7 && !c.stage_only) stage_begin<(S < 7 ? S + 1 : 7)>(c, sm, mn, pp);
+    if (S >= 2 && S < 7 && !c.stage_only && !c.fd) stage_begin<(S < 7 ? S + 1 : 7)>(c, sm, mn, pp);
     controller<S>(c, tm, L, cf, sq, emax);
     __syncthreads();
     return true;
@@ -685,11 +697,10 @@ __device__ bool integrate(const Ctx &c, const Team &tm, SM &sm, Local &L, Coef &
     stage_cache_rows(c, sm);
     if (threadIdx.x == 0) {
         // fixed-point scale of this block's overlap partials: a thread computes at most P cells
-        // per stage (interior planes of the block's segments, four cells each in quad windows),
-        // each contributing at most |u| |m| <= 2 umax
+        // per stage (interior planes of the block's segments), each contributing at most
+        // |u| |m| <= 2 umax
         int P = 0;
         for (int t = 0; t < sm.nseg; t++) P += sm.seg[t].w - sm.seg[t].z;
-        P *= c.quad > 1 ? c.quad : 1;
         const float bound = 2.f * (float)(P > 1 ? P : 1) * fmaxf(c.umax, 1.f);
         const int k = 24 - (int)ceilf(log2f(bound));
         L.tscale = ldexpf(1.f, k);

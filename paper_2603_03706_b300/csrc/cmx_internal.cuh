@@ -16,6 +16,11 @@ constexpr int MAXN = CMX_MAX_MODES;
 // self-Kerr coefficient K.
 constexpr int MC = 7;
 
+// Row storage alignment in cells: every row's stored span starts at a multiple of ROW_ALIGN
+// cells of x and of the compact index (see cmx_layout.h), so that a tile row (x0 a multiple of
+// 32) starts on a 32-byte sector.
+constexpr int ROW_ALIGN = 8;
+
 // Longest segment (planes including its two halo planes) and most segments per block.
 constexpr int MAX_TILE_PLANES = 66;
 constexpr int MAX_BLOCK_SEGMENTS = 64;
@@ -118,6 +123,19 @@ struct Ctx {
     const float *u;                  // [nmodes][ncell] or NULL
     float *m[2];                     // [nsub*3][ncell]
     float *k[7];                     // [nsub*3][ncell]
+    // stored stage values: stage S (2..6) writes m_{S+1} into msv[(S+1) & 1], stage S+1 reads
+    // its tile and halo from there; es: the error partial sum_{j<=6} E_j k_j of stage 6
+    float *msv[2];                   // [nsub*3][ncell]
+    float *es;                       // [nsub*3][ncell]
+    // full magnetostatic demag (fd = 1; dmg is then 0): tensor spectrum [6][Lz][Ly][Lx] (real,
+    // scaled), FFT work array [3][nz][Ly][Lx], the field of the stage value bd [3][ncell] and
+    // the twiddles of the three axes (see cmx_demag.cuh)
+    int fd;
+    const float *dk;
+    float2 *dwork;
+    float *bd;
+    const float2 *dtw[3];
+    int Lx, Ly, Lz, lgx, lgy, lgz;
     // material (float, tesla units)
     float wx, wy, wz;                // (2 Aex / Ms) / c_d^2
     float anis, ku[3], B0[3], dmg[3], BE;
@@ -146,7 +164,6 @@ struct Ctx {
     int tr_cap;
     long long timeout_ns;
     int stage_only;                  // 1: evaluate stage 1 once (cmx_eval_rhs) and stop
-    int quad;                        // 1: quad windows (four x-cells per thread, align-4 rows)
     double split_dt;                 // > 0: operator-split scheme with this interval
     // Checkpoint store of the adjoint (NULL = off): slot k holds the state after
     // k * traj_every accepted steps counted from traj_base (slot 0: the initial state):

@@ -5,13 +5,15 @@
 
 namespace cmx {
 
-// persistent single-problem integrator (cmx_single.cu)
+// persistent single-problem integrator (cmx_single.cu); tiles of bx x by cells, one thread each
 bool tile_shape_supported(int nsub, int bx, int by);
-// quad windows (Ctx::quad): wq x wy threads of four x-cells, launched with bx = 4 wq, by = wy
-bool quad_shape_supported(int wq, int wy);
-int quad_blocks_per_sm(int wq, int wy, int nu);
 cudaError_t launch_single(const Ctx &c, int bx, int by, int blocks, cudaStream_t s);
 int single_blocks_per_sm(int nsub, int bx, int by, bool has_u);
+
+// single-block integrator for small grids (cmx_small.cu): sidx = stored index of each of the nm
+// magnetic cells, snb = their neighbour table [-x, +x, -y, +y, -z, +z][nm] (-1: none)
+size_t small_smem_bytes(int nm, int nsub, int nmodes, bool has_u);
+cudaError_t launch_small(const Ctx &c, const int *sidx, const int *snb, int nm, cudaStream_t s);
 
 // batched integrator (cmx_batch.cu)
 struct BatchArgs {

@@ -6,15 +6,16 @@
 
 namespace cmx {
 
-void build_layout(Layout &L, int nx, int ny, int nz, const uint8_t *mask, int align)
+void build_layout(Layout &L, int nx, int ny, int nz, const uint8_t *mask)
 {
-    if (align < 1) align = 1;
+    constexpr int align = ROW_ALIGN;
     L.nx = nx;
     L.ny = ny;
     L.nz = nz;
     L.rows.assign((size_t)ny * nz, make_int2(0, 0));
     L.box_of_cell.clear();
     L.active.clear();
+    L.holes = false;
     int off = 0, nmag = 0;
     for (int z = 0; z < nz; z++)
         for (int y = 0; y < ny; y++) {
@@ -31,20 +32,22 @@ void build_layout(Layout &L, int nx, int ny, int nz, const uint8_t *mask, int al
             }
             // the stored span starts and ends on multiples of `align` (cells beyond the box are
             // inactive padding), so that aligned groups of `align` cells are aligned in memory
-            xs -= xs % align;
-            xe = (xe + align - 1) / align * align;
+            const int xa = xs - xs % align;
+            const int xb = (xe + align - 1) / align * align;
             L.rows[(size_t)z * ny + y] = make_int2(off, xs | (xe << 16));
-            for (int x = xs; x < xe; x++) {
-                const bool on = x < nx && mask[rb + x];
+            for (int x = xa; x < xb; x++) {
+                const bool in = x >= xs && x < xe;
+                const bool on = in && mask[rb + x];
+                if (in && !on) L.holes = true;
                 L.box_of_cell.push_back((int)(rb + std::min(x, nx - 1)));
                 L.active.push_back(on ? 1 : 0);
                 nmag += on ? 1 : 0;
             }
-            off += xe - xs;
+            off += xb - xa;
         }
     L.ncell = off;
     L.ncell_mag = nmag;
-    L.holes = nmag != off;
+    L.padded = nmag != off;
 }
 
 std::vector<uint32_t> active_bits(const Layout &L)
@@ -58,17 +61,18 @@ std::vector<uint32_t> active_bits(const Layout &L)
 // Columns of (wx-2) x (wy-2) interior cells (a wx x wy thread window with its one-cell rim):
 // the range of planes [zlo, zhi) that hold magnetic cells of the column, and per plane a work
 // weight (1: a plane iteration is latency-bound and costs about the same whatever its cells).
-std::vector<Column> build_columns(const Layout &L, int wx, int wy)
+std::vector<Column> build_columns(const Layout &L, int ix, int iy)
 {
     const int nx = L.nx, ny = L.ny, nz = L.nz;
-    const int bx = wx - 2, by = wy - 2;
+    const int bx = ix, by = iy;
     auto count = [&](int x0, int x1, int y0, int y1, int z) {
         int n = 0;
         if (z < 0 || z >= nz) return 0;
         for (int y = std::max(0, y0); y < std::min(ny, y1); y++) {
             const int2 r = L.rows[(size_t)z * ny + y];
             const int xs = r.y & 0xffff, xe = (int)((unsigned)r.y >> 16);
-            for (int x = std::max(xs, x0); x < std::min(xe, x1); x++) n += L.active[r.x + x - xs];
+            const int base = r.x - (xs - xs % ROW_ALIGN);
+            for (int x = std::max(xs, x0); x < std::min(xe, x1); x++) n += L.active[base + x];
         }
         return n;
     };
@@ -132,17 +136,22 @@ static int fill_blocks(const std::vector<Column> &cols, double cap, int max_bloc
 }
 
 // Smallest per-block capacity (binary search) whose greedy fill needs at most `blocks`
-// blocks; the partition then has no block above that capacity.
-void build_segments(const std::vector<Column> &cols, int blocks, std::vector<int4> &segs,
+// blocks; the partition then has no block above that capacity.  False if even the largest
+// capacity cannot place every plane (too many columns for MAX_BLOCK_SEGMENTS per block).
+bool build_segments(const std::vector<Column> &cols, int blocks, std::vector<int4> &segs,
                     std::vector<int> &begin)
 {
     double total = 0.0, wmax = 0.0;
-    for (const Column &c : cols)
+    long long planes = 0;
+    for (const Column &c : cols) {
         for (float v : c.w) {
             total += v;
             wmax = std::max(wmax, (double)v);
         }
+        planes += c.zhi - c.zlo;
+    }
     double lo = std::max(total / blocks, 2.0 + wmax), hi = total + 2.0 * (total + cols.size());
+    if (fill_blocks(cols, hi, blocks, segs, begin) > blocks) return false;
     for (int it = 0; it < 60 && hi - lo > 0.5; it++) {
         const double mid = 0.5 * (lo + hi);
         if (fill_blocks(cols, mid, blocks, segs, begin) <= blocks)
@@ -150,8 +159,14 @@ void build_segments(const std::vector<Column> &cols, int blocks, std::vector<int
         else
             lo = mid;
     }
-    fill_blocks(cols, hi, blocks, segs, begin);
+    if (fill_blocks(cols, hi, blocks, segs, begin) > blocks) return false;
     while ((int)begin.size() < blocks + 1) begin.push_back((int)segs.size());
+    // every plane of every column is in exactly one segment
+    long long covered = 0;
+    for (const int4 &t : segs) covered += t.w - t.z;
+    for (size_t b = 0; b + 1 < begin.size(); b++)
+        if (begin[b + 1] - begin[b] > MAX_BLOCK_SEGMENTS) return false;
+    return covered == planes;
 }
 
 

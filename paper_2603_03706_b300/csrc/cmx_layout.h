@@ -9,35 +9,39 @@
 
 namespace cmx {
 
-// Cells are stored per (y, z) row between the first and the last magnetic x of the row, the
-// span widened to multiples of `align` cells; cells in it that are not magnetic are holes
-// (inactive).  rows[z*ny + y] = (offset, xs | xe<<16).  With align = 4 every row starts at a
-// multiple of 4 stored cells and ncell is a multiple of 4 (16-byte aligned groups of four).
+// Cells are stored per (y, z) row: the span from the row's first magnetic x (xs) rounded down
+// to a multiple of ROW_ALIGN to its last magnetic x + 1 (xe) rounded up, at a storage offset
+// that is a multiple of ROW_ALIGN as well.  rows[z*ny + y] = (offset of the stored span, xs | xe<<16);
+// box cell x of the row is stored at offset + x - (xs rounded down).  Stored cells outside
+// [xs, xe) are padding; non-magnetic cells inside it are holes.  Both are inactive.
 struct Layout {
     int nx = 0, ny = 0, nz = 0;
     int ncell = 0, ncell_mag = 0;
-    bool holes = false;
+    bool holes = false;             // some row has a non-magnetic cell inside [xs, xe)
+    bool padded = false;            // some stored cell is inactive (holes or padding)
     std::vector<int2> rows;
     std::vector<int> box_of_cell;   // box index of each stored cell
     std::vector<uint8_t> active;    // 1 = magnetic (stored cells)
 };
 
-void build_layout(Layout &L, int nx, int ny, int nz, const uint8_t *mask, int align = 1);
+void build_layout(Layout &L, int nx, int ny, int nz, const uint8_t *mask);
 
 // 32-bit words of the active-cell bitmask (bit i of word i/32 = stored cell i is magnetic).
 std::vector<uint32_t> active_bits(const Layout &L);
 
-// Columns of (wx-2) x (wy-2) interior cells of a wx x wy block window, with the planes that
-// hold magnetic cells and a work weight per plane.
+// Columns of ix x iy cells (x0 a multiple of ix, y0 of iy) with the planes that hold magnetic
+// cells and a work weight per plane.
 struct Column {
     int x0, y0, zlo, zhi;
     std::vector<float> w;
 };
-std::vector<Column> build_columns(const Layout &L, int wx, int wy);
+std::vector<Column> build_columns(const Layout &L, int ix, int iy);
 
 // Split the columns into segments (x0, y0, z0, z1) and give `blocks` blocks contiguous runs of
-// them with balanced work; begin[b] .. begin[b+1] are block b's segments.
-void build_segments(const std::vector<Column> &cols, int blocks, std::vector<int4> &segs,
+// them with balanced work; begin[b] .. begin[b+1] are block b's segments.  Returns false if the
+// partition cannot cover every plane of every column within `blocks` blocks of at most
+// MAX_BLOCK_SEGMENTS segments each (the caller must reject the problem or the launch shape).
+bool build_segments(const std::vector<Column> &cols, int blocks, std::vector<int4> &segs,
                     std::vector<int> &begin);
 
 }  // namespace cmx

@@ -134,7 +134,7 @@ extern "C" int cmx_eval_rhs_noalloc(const cmx_grid *grid, const uint8_t *mask,
     const int blocks = (int)std::max<long long>(1, std::min<long long>((long long)occ * nsm, (P + 3) / 4));
     std::vector<int4> segs;
     std::vector<int> begin;
-    build_segments(cols, blocks, segs, begin);
+    if (!build_segments(cols, blocks, segs, begin)) return CMX_EINVAL;   // too many tile columns
 
     // carve the scratch; reject problems that do not fit
     void *base = nullptr;
@@ -143,7 +143,7 @@ extern "C" int cmx_eval_rhs_noalloc(const cmx_grid *grid, const uint8_t *mask,
     const size_t nc = (size_t)lay.ncell;
     int2 *rows = cv.take<int2>(lay.rows.size());
     int *box = cv.take<int>(nc);
-    uint32_t *act = lay.holes ? cv.take<uint32_t>((nc + 31) / 32) : nullptr;
+    uint32_t *act = lay.padded ? cv.take<uint32_t>((nc + 31) / 32) : nullptr;
     int4 *tiles = cv.take<int4>(segs.size());
     int *sbeg = cv.take<int>(begin.size());
     float *uc = has_u ? cv.take<float>((size_t)N * nc) : nullptr;
@@ -151,12 +151,12 @@ extern "C" int cmx_eval_rhs_noalloc(const cmx_grid *grid, const uint8_t *mask,
     float *kc = cv.take<float>((size_t)nq * nc);
     Ctl *ctl = cv.take<Ctl>(1);
     float *udense = has_u && !modes->u_on_device ? cv.take<float>((size_t)N * nbox) : nullptr;
-    if (!rows || !box || (lay.holes && !act) || !tiles || !sbeg || (has_u && !uc) || !mc ||
+    if (!rows || !box || (lay.padded && !act) || !tiles || !sbeg || (has_u && !uc) || !mc ||
         !kc || !ctl || (has_u && !modes->u_on_device && !udense))
         return CMX_ESCRATCH;   // larger than CMX_NOALLOC_SCRATCH_BYTES
 
     // tables and inputs into the scratch (every field the kernel reads is written here)
-    const std::vector<uint32_t> bits = lay.holes ? active_bits(lay) : std::vector<uint32_t>();
+    const std::vector<uint32_t> bits = lay.padded ? active_bits(lay) : std::vector<uint32_t>();
     Ctl c0;
     memset(&c0, 0, sizeof c0);
     for (int q = 0; q < 2 * N; q++) c0.a[q] = a ? a[q] : 0.0;
@@ -198,7 +198,7 @@ extern "C" int cmx_eval_rhs_noalloc(const cmx_grid *grid, const uint8_t *mask,
     c.ncell = (int)nc;
     c.ncell_mag = lay.ncell_mag;
     c.rows = rows;
-    c.active = act;
+    c.active = lay.holes ? act : nullptr;   // the row spans exclude the padding
     c.tiles = tiles;
     c.seg_begin = sbeg;
     c.ntiles = (int)segs.size();

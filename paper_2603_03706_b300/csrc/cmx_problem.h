@@ -25,7 +25,7 @@ struct cmx_problem {
     double omega[MAXN]{}, kappa[MAXN]{}, gre[MAXN]{}, gim[MAXN]{};
     long long nbox = 0;
     int ncell = 0, ncell_mag = 0;
-    bool holes = false;
+    bool holes = false;   // holes inside a row's magnetic span (stage kernels test them)
     Layout lay;
     // device buffers
     int2 *rows = nullptr;
@@ -37,6 +37,8 @@ struct cmx_problem {
     float *u = nullptr;
     float *mbuf[2] = {nullptr, nullptr};
     float *kbuf[7] = {};
+    float *msv[2] = {nullptr, nullptr};   // stored stage values
+    float *esbuf = nullptr;               // error partial of stage 6
     Ctl *ctl = nullptr;
     cmx_step *log = nullptr;
     double *log_a = nullptr, *log_mm = nullptr;
@@ -49,8 +51,16 @@ struct cmx_problem {
     Ctl *ev_ctl = nullptr;
     // launch shape
     int bx = 32, by = 8, bz = 16, blocks = 0, bps = 0, nsm = 0;
-    int quad = 0;                     // quad windows (four x-cells per thread)
     int bps_cap = 0;                  // blocks_per_sm requested (0 = as many as fit)
+    // single-block integrator (small grids): magnetic cells' stored indices and neighbour table
+    int *small_idx = nullptr, *small_nb = nullptr;
+    bool small_ok = false;            // the grid fits one block's shared memory
+    bool use_small = false;           // runs (not the adjoint's recorded ones) use it
+    bool small_default = false;       // use_small as chosen at creation / by the autotuner
+    // full demag (cmx_demag_api.cu)
+    float *dm_k = nullptr;
+    float2 *dm_work = nullptr, *dm_tw = nullptr;
+    float *dm_bd = nullptr;
     long long launch_attempts = 4096;
     long long timeout_ns = 2000000000LL;
     int skip_block = -1;
@@ -94,5 +104,6 @@ Ctx make_ctx(const cmx_problem *h);
 int read_ctl(cmx_problem *h, Ctl *out);
 int device_status(cmx_problem *h, const Ctl &c);
 void adj_free(cmx_problem *h);
+void demag_release(cmx_problem *h);
 
 }  // namespace cmx_host

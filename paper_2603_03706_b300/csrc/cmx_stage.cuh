@@ -1,20 +1,27 @@
 // Device code of one Dormand-Prince stage over the tiles of a masked grid (sm_103a).
 //
-// One stage S computes, for every magnetic cell,
-//   m_S  = m_n + h sum_{j<S} a_Sj k_j                      (stage combination, FP32)
+// Stage S computes, for every magnetic cell, the field at the stage value m_S,
 //   B    = exchange(m_S) + anisotropy + Zeeman + demag + inter-sublattice + B_rf(a_S)
 //   k_S  = -gamma/(1+alpha^2) [ m_S x B + alpha m_S x (m_S x B) ]      (LLG, Sec. II A)
-// and the block partial sums of the overlaps u_n (m_x - i m_y) (Eq. (18)).  Stage 7 also
-// writes the renormalised 5th-order point and the block maximum of |e_m|,
-// e_m = h sum_j E_j k_j.
+// and the block partial sums of the overlaps u_n (m_x - i m_y) (Eq. (18)); then, with k_S still
+// in registers, it combines the cell's NEXT stage value and stores it:
+//   m_{S+1} = m_n + h sum_{j<=S} a_{S+1,j} k_j                      (S = 2..6; S = 6 gives the
+//                                                                     5th-order point Y_7)
+// Stage S+1 reads these stored values for its tile and its one-cell halo, so a halo cell's
+// stage value is read (12 bytes per sublattice, mostly from L2: the neighbouring tiles wrote it
+// during the previous stage) instead of being recombined from m_n and all earlier slopes of that
+// cell.  The step size of an attempt is fixed only by the previous attempt's decision, so stage 2
+// forms m_2 = m_n + h a_21 k_1 itself for every tile position; stage 1 reads m_n.  Stage 6 also
+// stores the error partial sum_{j<=6} E_j k_j, and stage 7 adds E_7 k_7 to it:
+// e_m = h sum_j E_j k_j, and writes the renormalised 5th-order point.
 //
-// Tiles are columns of (WX-2) x (WY-2) cells, several planes deep; a block of WX x WY threads
-// covers a tile with its one-cell halo rim and marches through it plane by plane.  The raw
-// operands of the next planes arrive by asynchronous copies (cp.async) into shared memory while
-// the block combines the oldest plane into a ring of four planes of stage values and computes
-// the plane before it from planes p-1, p, p+1: one __syncthreads per plane, the 6-neighbour
-// stencil reads only shared memory.  Cells are stored compactly per (y, z) row between the first
-// and the last magnetic x of the row; the row table gives the offset.
+// A tile is WX x WY cells (one warp per x-row, every thread computes a cell) with a one-cell rim
+// that the first threads of the block load as well; blocks march through their columns plane by
+// plane.  Stage values of the tile and rim and the thread's own operands of the next combine
+// arrive by asynchronous copies (cp.async) several planes ahead; one __syncthreads per plane
+// publishes a plane's tile, and the 6-neighbour stencil reads only shared memory.  Cells are
+// stored compactly per (y, z) row between the first and the last magnetic x of the row; the row
+// table gives the offset.
 #pragma once
 
 #include "cmx_internal.cuh"
@@ -71,33 +78,48 @@ __device__ __forceinline__ void mode_constants(const Ctx &c, int n, double *out)
     for (int q = 0; q < MC; q++) out[q] = v[q];
 }
 
-// Slopes read by stage S (1-based): those with a nonzero coupling, and at stage 7 also those
-// with a nonzero error weight.  Array 0 of a stage is m_n, arrays 1.. are these slopes.
-__host__ __device__ constexpr bool slope_used(int S, int j)
+// Operand arrays of the combine that ends stage S (1-based), read for the thread's own cell:
+// stages 2..6 read m_n (array 0) and the earlier slopes k_j, j < S, with a nonzero coupling
+// a_{S+1,j} (k_S itself is in registers); stage 7 reads the error partial stored by stage 6.
+__host__ __device__ constexpr int n_ops(int S)
 {
-    return j < S - 1 && (dp_a(S - 1, j) != 0.0 || (S == 7 && dp_e(j) != 0.0));
-}
-
-__host__ __device__ constexpr int n_arrays(int S)
-{
+    if (S <= 1) return 0;
+    if (S == 7) return 1;
     int n = 1;
-    for (int j = 0; j < 6; j++) n += slope_used(S, j) ? 1 : 0;
+    for (int j = 0; j < S - 1; j++) n += dp_a(S, j) != 0.0 ? 1 : 0;
     return n;
 }
 
-__host__ __device__ constexpr int array_slope(int S, int a)
+// Slope (0-based) held by operand array a >= 1 of stage S.
+__host__ __device__ constexpr int op_slope(int S, int a)
 {
     int n = 0;
-    for (int j = 0; j < 6; j++)
-        if (slope_used(S, j)) {
+    for (int j = 0; j < S - 1; j++)
+        if (dp_a(S, j) != 0.0) {
             n++;
             if (n == a) return j;
         }
     return -1;
 }
 
+// The error partial of stage 6 uses the same slopes as the 5th-order point (E_2 = a_72 = 0).
+__host__ __device__ constexpr bool error_slopes_match()
+{
+    for (int j = 0; j < 6; j++)
+        if ((dp_e(j) != 0.0) != (dp_a(6, j) != 0.0)) return false;
+    return true;
+}
+static_assert(error_slopes_match(), "stage 6 forms Y_7 and the error partial from one operand set");
+
+// Arrays per tile position: stage 2 loads m_n and k_1 and combines them; the other stages load
+// one stage value (m_n at stage 1, the stored m_S otherwise).
+__host__ __device__ constexpr int n_tile(int S)
+{
+    return S == 2 ? 2 : 1;
+}
+
 // Compensated FP32 pair ("double-float"): value = hi + lo, about 44 significant bits.  Used for
-// the overlap sums across threads and blocks; FP64 has a long dependent latency on this part.
+// the fixed-order sums of the adjoint's reverse sweep.
 struct F2 {
     float hi, lo;
 };
@@ -124,13 +146,6 @@ __device__ __forceinline__ void cp_async4(void *smem, const void *gmem)
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(s), "l"(gmem) : "memory");
 }
 
-// Asynchronous 16-byte global -> shared copy (both addresses 16-byte aligned).
-__device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
-{
-    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
-}
-
 __device__ __forceinline__ void cp_async_commit()
 {
     asm volatile("cp.async.commit_group;" ::: "memory");
@@ -145,36 +160,34 @@ __device__ __forceinline__ void cp_async_wait()
 // Row-table entries cached for the first planes of a block's stream.
 constexpr int ROWC = 16;
 
-// Shared memory of a block whose threads cover a WX x WY window: the interior
-// (WX-2) x (WY-2) cells are computed, the one-cell rim is the halo.  D planes of raw operands
-// (m_n and the slopes of the stage) are in flight as asynchronous copies while the block
-// combines the oldest one into the ring of stage values and computes the plane before it.
+// Shared memory of a block of WX x WY threads.  The tile of a plane holds PX x PY positions
+// (the WX x WY cells and their one-cell rim): stage values and presence, RING planes of them
+// (p-1, p, p+1 read by the stencil of plane p, later planes in flight).  The operand pool holds,
+// per plane in flight, the thread's own operands of the next combine ([array][q][thread]) and,
+// at stage 2, the slope k_1 of the tile positions ([q][position]).
 template <int NS, int WX, int WY, bool HU>
 struct StageSmem {
     static constexpr int W = WX * WY;
+    static constexpr int PX = WX + 2, PY = WY + 2, P = PX * PY;
+    static constexpr int NR = 2 * PX + 2 * WY;            // rim positions
     static constexpr int NQ = NS * 3;
-    static constexpr int RING = 4;
-    static constexpr int NAMAX = 6;             // m_n + at most five slopes per stage
-    static constexpr int POOL = (NS == 1 ? 2 : 1) * NAMAX * NQ * W;   // raw operand floats
-    static constexpr int DMAX = 4;
-    // Planes in flight at stage S: as many plane slots of n_arrays(S) x NQ x W floats as the
-    // pool holds (at most 4).
-    template <int S>
-    __host__ __device__ static constexpr int depth()
-    {
-        const int d = POOL / (n_arrays(S) * NQ * W);
-        return d < 1 ? 1 : (d > DMAX ? DMAX : d);
-    }
-    float raw[POOL];              // raw operands of planes in flight, [slot][array][q][W]
-    int ridx[DMAX][W];            // their compact indices (-1: absent)
-    float v[RING][NQ + 1][W];     // stage values and presence (last row) of four planes
-    float es[2][NQ][W];           // stage 7: sum_{j<7} E_j k_j of the interior cells
-    int cidx[2][W];               // compact index of the interior cells (-1: absent)
-    F2 red[32][2 * MAXN];         // per-warp partial overlaps
+    static constexpr int NAMAX = 5;                       // m_n + at most four slopes
+    static constexpr int D = 2;                           // planes in flight
+    static constexpr int RING = D + 2;                    // tile slots
+    static constexpr int OIX = D + 1;                     // own-index slots
+    static constexpr int OPSLOT = NAMAX * NQ * W;         // operand slot (D of them)
+    static_assert(2 * NQ * W + NQ * P <= OPSLOT, "stage-2 slot");
+    static_assert(NR <= W, "rim positions need one thread each");
+    static_assert(WX == 32, "one warp per tile row");
+    float pool[D * OPSLOT];
+    float v[RING][NQ + 1][P];     // stage values of the tile positions, presence in row NQ
+    int oidx[OIX][W];             // compact index of the thread's cell of a plane in flight
+                                  // (-1: absent or a halo plane)
+    F2 red[32][2 * MAXN];         // per-warp partial overlaps (integer digits)
     float redmax[32];
     const float *kp[7];           // physical slope buffers in logical order
-    int2 rows[8][WY];             // row-table entries of the window rows, by plane mod 8
-    int2 rowc[ROWC][WY];          // the same for the first ROWC planes of the stream (every
+    int2 rows[8][PY];             // row-table entries of the tile rows, by plane mod 8
+    int2 rowc[ROWC][PY];          // the same for the first ROWC planes of the stream (every
                                   // stage starts there), filled once per launch
     int4 seg[MAX_BLOCK_SEGMENTS]; // this block's segments (x0, y0, z0, z1)
     int nseg;
@@ -223,12 +236,15 @@ struct Coef {
     float hrf[MAXN];
 };
 
-// Compact index of box cell x in a row given its row-table entry, or -1.
+// Compact index of box cell x in a row given its row-table entry, or -1.  The entry holds the
+// storage offset of the row's first stored cell, which is x = xs rounded down to ROW_ALIGN, and
+// the magnetic span [xs, xe); cells inside the span that are not magnetic (holes) are marked in
+// the active bitmask (NULL: no holes).
 __device__ __forceinline__ int row_index(const Ctx &c, int2 r, int x)
 {
     const int xs = r.y & 0xffff, xe = (int)((unsigned)r.y >> 16);
     if (x < xs || x >= xe) return -1;
-    const int idx = r.x + (x - xs);
+    const int idx = r.x + (x - (xs & ~(ROW_ALIGN - 1)));
     if (c.active && !((__ldg(&c.active[idx >> 5]) >> (idx & 31)) & 1u)) return -1;
     return idx;
 }
@@ -239,108 +255,145 @@ __device__ __forceinline__ int2 row_entry(const Ctx &c, int y, int z)
     return __ldg(&c.rows[z * c.ny + y]);
 }
 
-// Issue the asynchronous copies of this thread's window position in stream plane g, then
-// commit one copy group (possibly empty).
+// Copy-pipeline state of one stage: cursors for row loading (cr) and copy issue (ci), the next
+// plane to issue, the stream length, and the thread's tile positions: its own cell (eo) and the
+// rim position it loads (er, -1: none) with the rim position's row and column (rr, rc).
+struct Pipe {
+    Cursor cr, ci;
+    int nq, gend;
+    int eo, er, rr, rc;
+};
+
+// Source of the tile values of stage S: m_n (S = 1, 2) or the stored stage value.
+template <int S>
+__device__ __forceinline__ const float *tile_source(const Ctx &c, const float *mn)
+{
+    return S <= 2 ? mn : c.msv[S & 1];
+}
+
+// Source of operand array a of stage S.
+template <class SM, int S>
+__device__ __forceinline__ const float *op_source(const Ctx &c, const SM &sm, const float *mn,
+                                                  int a)
+{
+    if (S == 7) return c.es;
+    if (a == 0) return mn;
+    return sm.kp[op_slope(S, a)];
+}
+
+// Copies of one tile position of stream plane g into ring slot rs (stage values, and at stage 2
+// the slope k_1 into the operand slot's side array), presence written directly.
+template <class SM, int S>
+__device__ __forceinline__ void load_position(const Ctx &c, SM &sm, const float *tsrc,
+                                              int rs, float *side, int e, int idx)
+{
+    constexpr int NQ = SM::NQ, P = SM::P;
+    if (idx >= 0) {
+#pragma unroll
+        for (int k = 0; k < NQ; k++) {
+            cp_async4(&sm.v[rs][k][e], tsrc + (size_t)k * c.ncell + idx);
+            if (S == 2) cp_async4(side + k * P + e, sm.kp[0] + (size_t)k * c.ncell + idx);
+        }
+        sm.v[rs][NQ][e] = 1.f;
+    } else {
+        // absent: value and presence 0 (the stencil sums absent neighbours as 0), and at stage 2
+        // the side slope 0 as well, so that the stage-2 combine leaves the position at 0
+#pragma unroll
+        for (int k = 0; k <= NQ; k++) sm.v[rs][k][e] = 0.f;
+        if (S == 2)
+#pragma unroll
+            for (int k = 0; k < NQ; k++) side[k * P + e] = 0.f;
+    }
+}
+
+// Copies of stream plane g, in two commit groups: first the tile (the position of the thread's
+// cell and, for the first NR threads, one rim position) with the presence flags and the own
+// compact index, later the thread's own operands of the stage's combine on planes interior to
+// their segment.  Both commit one group (possibly empty).
 template <int NS, int WX, int WY, bool HU, int S>
-__device__ __forceinline__ void issue_plane(const Ctx &c, StageSmem<NS, WX, WY, HU> &sm,
-                                            const float *mn, int g, int gend, const Cursor &cu,
-                                            int r, int col, bool corner, bool inner_pos)
+__device__ __forceinline__ void issue_tile(const Ctx &c, StageSmem<NS, WX, WY, HU> &sm,
+                                           const float *mn, int g, Pipe &pp)
 {
     using SM = StageSmem<NS, WX, WY, HU>;
-    constexpr int NQ = NS * 3, NA = n_arrays(S), D = SM::template depth<S>();
-    constexpr int W = SM::W;
+    constexpr int NQ = SM::NQ, W = SM::W;
     const int i = threadIdx.x;
-    if (g < gend) {
-        const int slot = g % D;
-        float *rp = sm.raw + (size_t)slot * NA * NQ * W;
-        const int idx = corner ? -1 : row_index(c, sm.rows[g & 7][r], cu.x0 - 1 + col);
-        sm.ridx[slot][i] = idx;
-        if (idx >= 0) {
+    if (g < pp.gend) {
+        cursor_seek(sm, pp.ci, g);
+        const Cursor &cu = pp.ci;
+        const int q = g - cu.off;
+        const bool inner = q >= 1 && q <= cu.np - 2;
+        const int rs = g % SM::RING;
+        float *side = sm.pool + (size_t)(g % SM::D) * SM::OPSLOT + n_ops(2) * NQ * W;
+        const float *tsrc = tile_source<S>(c, mn);
+        const int2 *rw = sm.rows[g & 7];
+        const int idx = row_index(c, rw[i / WX + 1], cu.x0 + i % WX);
+        load_position<SM, S>(c, sm, tsrc, rs, side, pp.eo, idx);
+        sm.oidx[g % SM::OIX][i] = inner ? idx : -1;
+        if (pp.er >= 0) {
+            const int ridx = row_index(c, rw[pp.rr], cu.x0 - 1 + pp.rc);
+            load_position<SM, S>(c, sm, tsrc, rs, side, pp.er, ridx);
+        }
+    }
+    cp_async_commit();
+}
+
+template <int NS, int WX, int WY, bool HU, int S>
+__device__ __forceinline__ void issue_ops(const Ctx &c, StageSmem<NS, WX, WY, HU> &sm,
+                                          const float *mn, int g, const Pipe &pp)
+{
+    using SM = StageSmem<NS, WX, WY, HU>;
+    constexpr int NQ = SM::NQ, W = SM::W, NO = n_ops(S);
+    const int i = threadIdx.x;
+    if (NO > 0 && g < pp.gend) {
+        const int oi = sm.oidx[g % SM::OIX][i];
+        float *slot = sm.pool + (size_t)(g % SM::D) * SM::OPSLOT;
+        if (oi >= 0) {
 #pragma unroll
-            for (int k = 0; k < NQ; k++) {
-                const size_t o = (size_t)k * c.ncell + idx;
-                cp_async4(rp + (0 * NQ + k) * W + i, mn + o);
+            for (int a = 0; a < NO; a++) {
+                const float *src = op_source<SM, S>(c, sm, mn, a);
 #pragma unroll
-                for (int a = 1; a < NA; a++)
-                    cp_async4(rp + (a * NQ + k) * W + i, sm.kp[array_slope(S, a)] + o);
+                for (int k = 0; k < NQ; k++)
+                    cp_async4(slot + (a * NQ + k) * W + i, src + (size_t)k * c.ncell + oi);
             }
         }
     }
     cp_async_commit();
 }
 
-// Combine the raw operands of stream plane g (copied by this thread) into the stage value
-// m_S = m_n + sum_j (h a_Sj) k_j, and at stage 7 the partial error sum of interior cells.
+// Stage 2: the tile values m_2 = m_n + h a_21 k_1 of the thread's positions of plane g (the
+// copies of plane g are complete; only this thread wrote these positions).
 template <int NS, int WX, int WY, bool HU, int S>
-__device__ __forceinline__ void combine_plane(const Ctx &c, StageSmem<NS, WX, WY, HU> &sm,
-                                              const Coef &cf, int g, bool inner_cell)
+__device__ __forceinline__ void tile_combine(StageSmem<NS, WX, WY, HU> &sm, const Coef &cf, int g,
+                                             const Pipe &pp)
 {
     using SM = StageSmem<NS, WX, WY, HU>;
-    constexpr int NQ = NS * 3, NA = n_arrays(S), D = SM::template depth<S>();
-    constexpr int R = SM::RING, W = SM::W;
-    const int i = threadIdx.x;
-    const int rs = g % D, vs = g % R;
-    const float *rp = sm.raw + (size_t)rs * NA * NQ * W;
-    const int idx = sm.ridx[rs][i];
-    const bool here = idx >= 0;
+    constexpr int NQ = SM::NQ, P = SM::P;
+    if (S != 2 || g >= pp.gend) return;
+    const int rs = g % SM::RING;
+    const float *side = sm.pool + (size_t)(g % SM::D) * SM::OPSLOT + n_ops(2) * NQ * SM::W;
+    const float c21 = cf.cf[1][0];
 #pragma unroll
     for (int k = 0; k < NQ; k++) {
-        float acc = 0.f, es = 0.f;
-        if (here) {
-            acc = rp[(0 * NQ + k) * W + i];
-#pragma unroll
-            for (int a = 1; a < NA; a++) {
-                const int j = array_slope(S, a);
-                const float kj = rp[(a * NQ + k) * W + i];
-                if (dp_a(S - 1, j) != 0.0) acc = fmaf(cf.cf[S - 1][j], kj, acc);
-                if (S == 7 && dp_e(j) != 0.0) es = fmaf(cf.e[j], kj, es);
-            }
-        }
-        sm.v[vs][k][i] = acc;
-        if (S == 7 && inner_cell) sm.es[g & 1][k][i] = es;
+        sm.v[rs][k][pp.eo] = fmaf(c21, side[k * P + pp.eo], sm.v[rs][k][pp.eo]);
+        if (pp.er >= 0) sm.v[rs][k][pp.er] = fmaf(c21, side[k * P + pp.er], sm.v[rs][k][pp.er]);
     }
-    sm.v[vs][NQ][i] = here ? 1.f : 0.f;
-    sm.cidx[g & 1][i] = (inner_cell && here) ? idx : -1;
 }
 
-// RHS of this thread's interior cell of plane p (ring slots: p-1, p, p+1).  Writes k_S (and at
-// stage 7 the renormalised new m) and accumulates the overlap sums and the error maximum.
-template <int NS, int WX, int WY, bool HU, int S>
-__device__ __forceinline__ void compute_cell(const Ctx &c, StageSmem<NS, WX, WY, HU> &sm,
-                                             float *kout, float *mnew, const Coef &cf, int p,
-                                             const float *ucell, int tslot, int rslot,
-                                             Acc &acc)
+// Slope of one cell from its stage value m and exchange field B (both sublattices): adds the
+// local fields (uniaxial anisotropy, Zeeman, diagonal demag of the total moment or the full
+// demag field bdem of the cell (zero unless Ctx::fd; dmg is zero then),
+// inter-sublattice -B_E m_other) and the cavity feedback field x sum_n u_n (2/gamma)
+// Re[g~_n a_n] (Eq. (5), (13)) to B, accumulates the overlap partial sums of the net moment
+// (m1 + m2)/2 with the same profile values (Eq. (18)), and returns the Landau-Lifshitz slope
+// k = -gamma/(1+alpha^2) [m x B + alpha m x (m x B)].
+template <int NS, bool HU>
+__device__ __forceinline__ void cell_slope(const Ctx &c, const Coef &cf, const float (&m)[NS][3],
+                                           float (&B)[NS][3], const float *ucell,
+                                           const float (&bdem)[3], Acc &acc, float (&kv)[NS][3])
 {
-    using SM = StageSmem<NS, WX, WY, HU>;
-    constexpr int NQ = SM::NQ, R = SM::RING;
-    const int i = threadIdx.x;
-    const int idx = sm.cidx[p & 1][i];
-    if (idx < 0) return;
-    const int sp = (p + R - 1) % R, sc = p % R, sn = (p + 1) % R;
-
-    const float nx_ = sm.v[sc][NQ][i - 1] + sm.v[sc][NQ][i + 1];
-    const float ny_ = sm.v[sc][NQ][i - WX] + sm.v[sc][NQ][i + WX];
-    const float nz_ = sm.v[sp][NQ][i] + sm.v[sn][NQ][i];
-
-    float m[NS][3], B[NS][3];
-#pragma unroll
-    for (int s = 0; s < NS; s++)
-#pragma unroll
-        for (int k = 0; k < 3; k++) {
-            const int q = s * 3 + k;
-            const float cen = sm.v[sc][q][i];
-            m[s][k] = cen;
-            // exchange: sum over present neighbours of (m_j - m_i) / c_d^2 (absent ones hold 0)
-            B[s][k] = c.wx * (sm.v[sc][q][i - 1] + sm.v[sc][q][i + 1] - nx_ * cen) +
-                      c.wy * (sm.v[sc][q][i - WX] + sm.v[sc][q][i + WX] - ny_ * cen) +
-                      c.wz * (sm.v[sp][q][i] + sm.v[sn][q][i] - nz_ * cen);
-        }
-
     float mt[3];
 #pragma unroll
     for (int k = 0; k < 3; k++) mt[k] = (NS == 2) ? (m[0][k] + m[1][k]) : m[0][k];
-    // feedback field sum_n u_n (2/gamma) Re[g~_n a_n] and the overlap partial sums of the net
-    // moment (m1 + m2)/2 with the same profile values
     const float hx = (NS == 2) ? 0.5f * mt[0] : mt[0];
     const float hy = (NS == 2) ? 0.5f * mt[1] : mt[1];
     float brf = 0.f;
@@ -353,19 +406,17 @@ __device__ __forceinline__ void compute_cell(const Ctx &c, StageSmem<NS, WX, WY,
             acc.im[n] = fmaf(-un, hy, acc.im[n]);
         }
     }
-
 #pragma unroll
     for (int s = 0; s < NS; s++) {
         const float mk = m[s][0] * c.ku[0] + m[s][1] * c.ku[1] + m[s][2] * c.ku[2];
 #pragma unroll
         for (int k = 0; k < 3; k++) {
-            float b = B[s][k] + c.anis * mk * c.ku[k] + c.B0[k] - c.dmg[k] * mt[k];
+            float b = B[s][k] + c.anis * mk * c.ku[k] + c.B0[k] - c.dmg[k] * mt[k] + bdem[k];
             if (NS == 2) b -= c.BE * m[1 - s][k];
             B[s][k] = b;
         }
         B[s][0] += brf;
     }
-
     // LLG torque, Landau-Lifshitz form
 #pragma unroll
     for (int s = 0; s < NS; s++) {
@@ -376,8 +427,60 @@ __device__ __forceinline__ void compute_cell(const Ctx &c, StageSmem<NS, WX, WY,
         const float t2x = mm[1] * t1z - mm[2] * t1y;
         const float t2y = mm[2] * t1x - mm[0] * t1z;
         const float t2z = mm[0] * t1y - mm[1] * t1x;
-        const float kv[3] = {c.pre * fmaf(c.alpha, t2x, t1x), c.pre * fmaf(c.alpha, t2y, t1y),
-                             c.pre * fmaf(c.alpha, t2z, t1z)};
+        kv[s][0] = c.pre * fmaf(c.alpha, t2x, t1x);
+        kv[s][1] = c.pre * fmaf(c.alpha, t2y, t1y);
+        kv[s][2] = c.pre * fmaf(c.alpha, t2z, t1z);
+    }
+}
+
+// RHS of this thread's cell of plane p (ring slots: p-1, p, p+1), then the combine of the next
+// stage value from k_S and the operands in flight (stages 2..6), the error partial (stage 6), or
+// the error estimate and the renormalised new state (stage 7).  Accumulates the overlap sums and
+// the error maximum.
+template <int NS, int WX, int WY, bool HU, int S>
+__device__ __forceinline__ void compute_cell(const Ctx &c, StageSmem<NS, WX, WY, HU> &sm,
+                                             float *kout, float *mnew, const Coef &cf, int p,
+                                             const float *ucell, int tslot, int rslot,
+                                             const Pipe &pp, Acc &acc)
+{
+    using SM = StageSmem<NS, WX, WY, HU>;
+    constexpr int NQ = SM::NQ, R = SM::RING, PX = SM::PX, W = SM::W, NO = n_ops(S);
+    const int i = threadIdx.x;
+    const int idx = sm.oidx[p % SM::OIX][i];
+    if (idx < 0) return;
+    const int sp = (p + R - 1) % R, sc = p % R, sn = (p + 1) % R;
+    const int e = pp.eo;
+    const float *op = sm.pool + (size_t)(p % SM::D) * SM::OPSLOT;
+
+    const float nx_ = sm.v[sc][NQ][e - 1] + sm.v[sc][NQ][e + 1];
+    const float ny_ = sm.v[sc][NQ][e - PX] + sm.v[sc][NQ][e + PX];
+    const float nz_ = sm.v[sp][NQ][e] + sm.v[sn][NQ][e];
+
+    float m[NS][3], B[NS][3];
+#pragma unroll
+    for (int s = 0; s < NS; s++)
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            const int q = s * 3 + k;
+            const float cen = sm.v[sc][q][e];
+            m[s][k] = cen;
+            // exchange: sum over present neighbours of (m_j - m_i) / c_d^2 (absent ones hold 0)
+            B[s][k] = c.wx * (sm.v[sc][q][e - 1] + sm.v[sc][q][e + 1] - nx_ * cen) +
+                      c.wy * (sm.v[sc][q][e - PX] + sm.v[sc][q][e + PX] - ny_ * cen) +
+                      c.wz * (sm.v[sp][q][e] + sm.v[sn][q][e] - nz_ * cen);
+        }
+
+    float bdem[3] = {0.f, 0.f, 0.f};
+    if (c.fd)
+#pragma unroll
+        for (int k = 0; k < 3; k++) bdem[k] = __ldcg(c.bd + (size_t)k * c.ncell + idx);
+    float kvs[NS][3];
+    cell_slope<NS, HU>(c, cf, m, B, ucell, bdem, acc, kvs);
+
+#pragma unroll
+    for (int s = 0; s < NS; s++) {
+        const float *mm = m[s];
+        const float *kv = kvs[s];
 #pragma unroll
         for (int k = 0; k < 3; k++) kout[(size_t)(s * 3 + k) * c.ncell + idx] = kv[k];
         if (S >= 2 && rslot >= 0) {
@@ -394,125 +497,145 @@ __device__ __forceinline__ void compute_cell(const Ctx &c, StageSmem<NS, WX, WY,
                 c.traj_k[o + (size_t)(s * 3 + k) * c.ncell + idx] = kv[k];
             }
         }
+        if (S >= 2 && S <= 6 && !c.stage_only) {
+            // next stage value m_{S+1} = m_n + sum_j (h a_{S+1,j}) k_j, k_S last
+            float *out = c.msv[(S + 1) & 1];
+#pragma unroll
+            for (int k = 0; k < 3; k++) {
+                const int q = s * 3 + k;
+                float a = op[(0 * NQ + q) * W + i];
+                float es = 0.f;
+#pragma unroll
+                for (int o = 1; o < NO; o++) {
+                    const int j = op_slope(S, o);
+                    const float kj = op[(o * NQ + q) * W + i];
+                    a = fmaf(cf.cf[S][j], kj, a);
+                    if (S == 6) es = fmaf(cf.e[j], kj, es);
+                }
+                a = fmaf(cf.cf[S][S - 1], kv[k], a);
+                out[(size_t)q * c.ncell + idx] = a;
+                if (S == 6) c.es[(size_t)q * c.ncell + idx] = fmaf(cf.e[5], kv[k], es);
+            }
+        }
         if (S == 7) {
             const float r = rsqrtf(mm[0] * mm[0] + mm[1] * mm[1] + mm[2] * mm[2]);
 #pragma unroll
             for (int k = 0; k < 3; k++) {
                 const int q = s * 3 + k;
                 mnew[(size_t)q * c.ncell + idx] = mm[k] * r;
-                const float e = cf.h * fmaf(cf.e[6], kv[k], sm.es[p & 1][q][i]);
-                acc.emax = nanmax(acc.emax, fabsf(e));
+                const float e7 = cf.h * fmaf(cf.e[6], kv[k], op[q * W + i]);
+                acc.emax = nanmax(acc.emax, fabsf(e7));
             }
         }
     }
 }
 
-// Copy-pipeline state of one stage: cursors for row loading (cr), copy issue (ci) and combine
-// (cc), the next plane to issue and the stream length.
-struct Pipe {
-    Cursor cr, ci, cc;
-    int nq, gend;
-    int fidx, fnib, finner;   // quad windows: the first plane, issued by stage_begin
-};
-
 // Start stage S's stream: row entries of the first planes and the first D planes of copies.
-// Needs only m_n and the slopes of earlier stages, so it can run before the cavity update of
-// the previous stage is known.  Planes of the block's segments: segment t covers interior x in
-// [x0, x0+WX-2), y in [y0, y0+WY-2), z in [z0, z1) and contributes planes z0-1 .. z1.
+// Needs only m_n, the slopes of earlier stages and the stage values stored by the previous stage,
+// so it can run before the cavity update of the previous stage is known.  Planes of the block's
+// segments: segment t covers x in [x0, x0+WX), y in [y0, y0+WY), z in [z0, z1) and contributes
+// planes z0-1 .. z1.
 template <int NS, int WX, int WY, bool HU, int S>
 __device__ void tiles_begin(const Ctx &c, StageSmem<NS, WX, WY, HU> &sm, const float *mn,
                             Pipe &pp)
 {
-    constexpr int D = StageSmem<NS, WX, WY, HU>::template depth<S>();
-    constexpr int AHEAD = D + 3;   // row entries are loaded this many planes ahead (ring of 8)
+    using SM = StageSmem<NS, WX, WY, HU>;
+    constexpr int D = SM::D, AHEAD = D + 1, PY = SM::PY, PX = SM::PX;
     pp.gend = 0;
     for (int t = 0; t < sm.nseg; t++) pp.gend += sm.seg[t].w - sm.seg[t].z + 2;
     pp.nq = 0;
     if (sm.nseg == 0) return;
-    const int r = threadIdx.x / WX, col = threadIdx.x - (threadIdx.x / WX) * WX;
-    const bool corner = (r == 0 || r == WY - 1) && (col == 0 || col == WX - 1);
-    const bool inner_pos = r >= 1 && r <= WY - 2 && col >= 1 && col <= WX - 2;
+    const int i = threadIdx.x;
+    pp.eo = (i / WX + 1) * PX + i % WX + 1;
+    pp.er = -1;
+    pp.rr = pp.rc = 0;
+    if (i < SM::NR) {
+        if (i < PX) {
+            pp.rr = 0;
+            pp.rc = i;
+        } else if (i < 2 * PX) {
+            pp.rr = PY - 1;
+            pp.rc = i - PX;
+        } else if (i < 2 * PX + WY) {
+            pp.rr = i - 2 * PX + 1;
+            pp.rc = 0;
+        } else {
+            pp.rr = i - 2 * PX - WY + 1;
+            pp.rc = PX - 1;
+        }
+        pp.er = pp.rr * PX + pp.rc;
+    }
     pp.cr = cursor_start(sm);
     pp.ci = pp.cr;
-    pp.cc = pp.cr;
     __syncthreads();   // the previous stage may still read the shared buffers
     for (int g = 0; g <= AHEAD; g++)
-        if (threadIdx.x < WY && g < pp.gend) {
+        if (i < PY && g < pp.gend) {
             cursor_seek(sm, pp.cr, g);
-            sm.rows[g & 7][threadIdx.x] =
-                g < ROWC ? sm.rowc[g][threadIdx.x]
-                         : row_entry(c, pp.cr.y0 - 1 + threadIdx.x, pp.cr.z0 - 1 + (g - pp.cr.off));
+            sm.rows[g & 7][i] = g < ROWC ? sm.rowc[g][i]
+                                         : row_entry(c, pp.cr.y0 - 1 + i, pp.cr.z0 - 1 + (g - pp.cr.off));
         }
     __syncthreads();
     for (; pp.nq < D; pp.nq++) {
-        cursor_seek(sm, pp.ci, pp.nq);
-        issue_plane<NS, WX, WY, HU, S>(c, sm, mn, pp.nq, pp.gend, pp.ci, r, col, corner,
-                                       inner_pos);
+        issue_tile<NS, WX, WY, HU, S>(c, sm, mn, pp.nq, pp);
+        issue_ops<NS, WX, WY, HU, S>(c, sm, mn, pp.nq, pp);
     }
 }
 
-// Run stage S's stream to its end: combine the oldest plane in flight, issue the next, compute
-// the plane before it.  Only planes interior to their segment are computed; the profiles of
-// the next computed cell are loaded one plane ahead.
+// Run stage S's stream to its end.  Commit groups come in the order tile(g), ops(g) for
+// g = 0, 1, ...; at the start of iteration p the groups of planes up to p+D-1 are committed.
+// Iteration p: wait for plane p+1's tile (and plane p's operands; stage 2: form plane p+1's tile
+// values), publish it with the block barrier, issue plane p+D's tile, compute plane p, issue
+// plane p+D's operands into the slot plane p has just released.  Only planes interior to their
+// segment are computed; the profiles of the next computed cell are loaded one plane ahead.
 template <int NS, int WX, int WY, bool HU, int S>
 __device__ void tiles_run(const Ctx &c, StageSmem<NS, WX, WY, HU> &sm, float *kout,
                           const float *mn, float *mnew, const Coef &cf, Pipe &pp, int tslot,
                           int rslot, Acc &acc)
 {
-    constexpr int D = StageSmem<NS, WX, WY, HU>::template depth<S>();
-    constexpr int AHEAD = D + 3;
+    using SM = StageSmem<NS, WX, WY, HU>;
+    constexpr int D = SM::D, AHEAD = D + 1, PY = SM::PY;
+    constexpr int PEND = 2 * D - 3;   // groups after tile(p+1): ops(p+1), then D-2 planes
+    static_assert(D >= 2, "two planes in flight at least");
     const int gend = pp.gend;
     if (sm.nseg == 0) return;
-    const int r = threadIdx.x / WX, col = threadIdx.x - (threadIdx.x / WX) * WX;
-    const bool corner = (r == 0 || r == WY - 1) && (col == 0 || col == WX - 1);
-    const bool inner_pos = r >= 1 && r <= WY - 2 && col >= 1 && col <= WX - 2;
+    const int i = threadIdx.x;
     auto load_rows = [&](int g) {   // rows of stream plane g into ring slot g mod 8
-        if (threadIdx.x < WY && g < gend) {
+        if (i < PY && g < gend) {
             cursor_seek(sm, pp.cr, g);
-            sm.rows[g & 7][threadIdx.x] =
-                g < ROWC ? sm.rowc[g][threadIdx.x]
-                         : row_entry(c, pp.cr.y0 - 1 + threadIdx.x, pp.cr.z0 - 1 + (g - pp.cr.off));
+            sm.rows[g & 7][i] = g < ROWC ? sm.rowc[g][i]
+                                         : row_entry(c, pp.cr.y0 - 1 + i, pp.cr.z0 - 1 + (g - pp.cr.off));
         }
-    };
-    auto inner_at = [&](const Cursor &cu, int g) {
-        const int q = g - cu.off;
-        return inner_pos && q >= 1 && q <= cu.np - 2;
     };
     float ucur[MAXN], unext[MAXN];
 #pragma unroll
     for (int n = 0; n < MAXN; n++) ucur[n] = unext[n] = 1.f;
     auto load_u = [&](int g, float *dst) {   // profiles of this thread's cell of plane g
         if (!HU) return;
-        const int idx = sm.cidx[g & 1][threadIdx.x];
+        const int idx = sm.oidx[g % SM::OIX][i];
 #pragma unroll
         for (int n = 0; n < MAXN; n++)
             if (n < c.nmodes && idx >= 0) dst[n] = __ldg(c.u + (size_t)n * c.ncell + idx);
     };
-    for (int g = 0; g < 2 && g < gend; g++) {
-        cp_async_wait<D - 1>();
-        cursor_seek(sm, pp.cc, g);
-        combine_plane<NS, WX, WY, HU, S>(c, sm, cf, g, inner_at(pp.cc, g));
-        cursor_seek(sm, pp.ci, pp.nq);
-        issue_plane<NS, WX, WY, HU, S>(c, sm, mn, pp.nq, gend, pp.ci, r, col, corner,
-                                       inner_pos);
-        pp.nq++;
-    }
+    // planes 0 and 1 (committed: 0 .. D-1; plane 0 is a halo plane: its operand slot is free)
+    cp_async_wait<PEND>();
+    tile_combine<NS, WX, WY, HU, S>(sm, cf, 0, pp);
+    tile_combine<NS, WX, WY, HU, S>(sm, cf, 1, pp);
+    issue_tile<NS, WX, WY, HU, S>(c, sm, mn, pp.nq, pp);
+    issue_ops<NS, WX, WY, HU, S>(c, sm, mn, pp.nq, pp);
+    pp.nq++;
     load_u(1, unext);
     for (int p = 1; p <= gend - 2; p++) {
         load_rows(p + AHEAD);
-        // plane p+1: its copies are the oldest in flight
-        cp_async_wait<D - 1>();
-        cursor_seek(sm, pp.cc, p + 1);
-        combine_plane<NS, WX, WY, HU, S>(c, sm, cf, p + 1, inner_at(pp.cc, p + 1));
-        cursor_seek(sm, pp.ci, pp.nq);
-        issue_plane<NS, WX, WY, HU, S>(c, sm, mn, pp.nq, gend, pp.ci, r, col, corner,
-                                       inner_pos);
-        pp.nq++;
+        cp_async_wait<PEND>();
+        tile_combine<NS, WX, WY, HU, S>(sm, cf, p + 1, pp);
+        __syncthreads();
+        issue_tile<NS, WX, WY, HU, S>(c, sm, mn, pp.nq, pp);
 #pragma unroll
         for (int n = 0; n < MAXN; n++) ucur[n] = unext[n];
         load_u(p + 1, unext);
-        __syncthreads();
-        compute_cell<NS, WX, WY, HU, S>(c, sm, kout, mnew, cf, p, ucur, tslot, rslot, acc);
+        compute_cell<NS, WX, WY, HU, S>(c, sm, kout, mnew, cf, p, ucur, tslot, rslot, pp, acc);
+        issue_ops<NS, WX, WY, HU, S>(c, sm, mn, pp.nq, pp);
+        pp.nq++;
     }
     cp_async_wait<0>();
 }
@@ -522,12 +645,13 @@ __device__ void tiles_run(const Ctx &c, StageSmem<NS, WX, WY, HU> &sm, float *ko
 template <int NS, int WX, int WY, bool HU>
 __device__ void stage_cache_rows(const Ctx &c, StageSmem<NS, WX, WY, HU> &sm)
 {
+    constexpr int PY = StageSmem<NS, WX, WY, HU>::PY;
     if (sm.nseg == 0) return;
     int gend = 0;
     for (int t = 0; t < sm.nseg; t++) gend += sm.seg[t].w - sm.seg[t].z + 2;
-    const int n = (gend < ROWC ? gend : ROWC) * WY;
+    const int n = (gend < ROWC ? gend : ROWC) * PY;
     for (int e = threadIdx.x; e < n; e += WX * WY) {
-        const int g = e / WY, r = e - g * WY;
+        const int g = e / PY, r = e - g * PY;
         Cursor cu = cursor_start(sm);
         cursor_seek(sm, cu, g);
         sm.rowc[g][r] = row_entry(c, cu.y0 - 1 + r, cu.z0 - 1 + (g - cu.off));

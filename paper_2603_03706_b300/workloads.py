@@ -76,6 +76,8 @@ class Problem:
     # None = reciprocal (the forward g~); self-Kerr coefficients K_n [rad/s per |a|^2] or None
     g_back: Optional[np.ndarray] = None
     kerr: Optional[np.ndarray] = None
+    # full magnetostatic demag (cell-pair tensor convolution) instead of the diagonal factors
+    full_demag: bool = False
 
     @property
     def nmodes(self) -> int:

@@ -4,6 +4,8 @@ import ctypes
 import os
 import re
 
+import pytest
+
 from paper_2603_03706_b300 import build, cmx
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -57,3 +59,28 @@ def test_create_rejects_bad_arguments_before_touching_the_device():
     assert lib.cmx_create(ctypes.byref(g), mask, ctypes.byref(m), ctypes.byref(md),
                           ctypes.byref(sv), None, None, ctypes.byref(h)) == cmx.EINVAL
     assert not h.value
+
+
+def test_partition_that_cannot_hold_every_column_is_rejected():
+    """A wide, thin grid has more tile columns than a few blocks of at most 64 segments can
+    take: the planning query (the same partition cmx_create uses) must refuse it instead of
+    leaving cells out, and accept it once there are enough blocks."""
+    from paper_2603_03706_b300 import workloads as W
+    p = W.make_problem(1024, 32, 1, 5e-9, W.full_mask(1024, 32, 1))   # 32 x 4 columns of 32x8
+    with pytest.raises(cmx.CmxError) as ei:
+        cmx.plan_tiling(p, 32, 8, 1)
+    assert ei.value.code == cmx.EINVAL
+    r = cmx.plan_tiling(p, 32, 8, 2)
+    assert r["segments"] == 128 and r["stored"] == 1024 * 32
+    with pytest.raises(cmx.CmxError):
+        cmx.plan_tiling(p, 64, 4, 8)                                  # tile not compiled
+
+
+def test_rows_are_stored_on_sector_boundaries():
+    """Every row's stored span starts at a multiple of 8 cells, so the stored count of a sphere is
+    a multiple of 8 and at least its magnetic count."""
+    from paper_2603_03706_b300 import workloads as W
+    for n in (8, 13, 24):
+        p = W.make_problem(n, n, n, 5e-9, W.sphere_mask(n, n, n))
+        r = cmx.plan_tiling(p, 32, 8, 4)
+        assert r["stored"] % 8 == 0 and r["stored"] >= p.ncells, (n, r)

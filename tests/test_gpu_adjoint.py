@@ -106,7 +106,7 @@ def compare(p, g, go):
 
 @pytest.mark.parametrize("case,every,tiling", [("sphere16", 40, None), ("afm", 16, None),
                                                ("plain", 25, None),
-                                               ("sphere16", 40, (64, 16, 0, 0, 4))])
+                                               ("sphere16", 40, (32, 4, 1))])
 def test_adjoint_matches_oracle(case, every, tiling):
     p = {"sphere16": sphere16, "afm": afm_small, "plain": ferro_plain}[case]()
     sim, dts, traj = forward(p, every, tiling=tiling)

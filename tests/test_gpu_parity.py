@@ -67,9 +67,10 @@ def rhs_compare(p, tiling=None):
 # one stage
 # ---------------------------------------------------------------------------------------------
 
-# one cell per thread (bx, by, bz) and quad windows (bx, by, bz, blocks_per_sm, 4)
-TILINGS = [None, (32, 8, 3), (64, 4, 5), (32, 16, 11), (32, 8, 1), (128, 8, 3, 0, 4),
-           (96, 8, 5, 0, 4), (64, 16, 2, 0, 4), (32, 16, 1, 0, 4), (64, 8, 7, 0, 4)]
+# tiles (bx, by, bz[, blocks_per_sm]): shapes, fewest planes per block (segments cut across
+# columns), one resident block per SM (many segments per block)
+TILINGS = [None, (32, 8, 3), (32, 4, 5), (32, 16, 11), (32, 8, 1), (32, 4, 1), (32, 16, 1),
+           (32, 8, 2, 1), (32, 4, 7, 1)]
 
 
 @pytest.mark.parametrize("tiling", TILINGS)
@@ -80,7 +81,7 @@ def test_rhs_ferromagnet_ragged(tiling):
     assert r["err_mm"] < 1e-7 and r["err_da"] < 1e-6, r
 
 
-@pytest.mark.parametrize("tiling", [(64, 4, 4), (64, 8, 4, 0, 4)])
+@pytest.mark.parametrize("tiling", [(32, 4, 4), (32, 16, 2)])
 def test_rhs_mask_with_holes_and_many_runs_per_row(tiling):
     r = rhs_compare(ragged_problem(holes=True, nmodes=8, seed=3), tiling)
     assert r["err_m"] < 2e-6 and r["outside"] == 0.0, r
@@ -110,7 +111,7 @@ def test_replay_single_sphere_1000_steps():
     assert dm <= TOL_M and da <= TOL_A, (dm, da)
 
 
-@pytest.mark.parametrize("tiling", [(64, 4, 4), (64, 16, 4, 0, 4)])
+@pytest.mark.parametrize("tiling", [(32, 4, 4), (32, 16, 2)])
 def test_replay_ragged_multimode_1000_steps(tiling):
     p = ragged_problem(nmodes=3, seed=11)
     p = p.replace(m0=W.tilted_state(1, p.nx, p.ny, p.nz, 5.0, 0.3), a0=np.array([1e-3, 0, 0j]))
@@ -124,6 +125,69 @@ def test_replay_afm_complex_coupling_1000_steps():
     p = p.replace(m0=m, a0=np.zeros(2, complex), u=None, T=1e-6)
     dm, da, info = replay_compare(p, 1000, tiling=(32, 8, 4))
     assert dm <= TOL_M and da <= TOL_A, (dm, da)
+
+
+# ---------------------------------------------------------------------------------------------
+# single-block integrator (small grids: the whole state in one block's shared memory)
+# ---------------------------------------------------------------------------------------------
+
+def small_afm():
+    nx, ny, nz = 10, 9, 4
+    p = W.make_problem(nx, ny, nz, 2e-9, W.full_mask(nx, ny, nz), nsub=2, Ms=4e5, Aex=5e-12,
+                       alpha=2e-3, Ku=5e4, B0=(0, 0, 1.0), Nd=(0, 0, 1), BE=50.0,
+                       omega=[W.afm_params()["w_minus"] - TP * 60e6] * 2,
+                       kappa=[TP * 2e6] * 2, g_re=[TP * 30e6] * 2, g_im=[0.0, TP * 30e6],
+                       m0=W.random_state(2, nx, ny, nz, 31, spread=0.05, afm=True), T=1e-6)
+    return p.replace(dt_max=W.stable_dt_max(p))
+
+
+def small_profiled():
+    nx, ny, nz = 11, 9, 7
+    rng = np.random.default_rng(41)
+    u = rng.uniform(-1, 1, (3, nz, ny, nx)).astype(np.float32)
+    p = W.make_problem(nx, ny, nz, 5e-9, W.random_mask(nx, ny, nz, 0.8, 41), Ku=-610.0,
+                       ku_axis=(0.6, 0.0, 0.8), B0=(0.01, 0, 0.187), Nd=(0.3, 0.3, 0.4),
+                       omega=TP * np.array([4.9e9, 5.0e9, 5.1e9]), kappa=TP * np.full(3, 2e6),
+                       g_re=TP * np.array([40e6, 60e6, 20e6]), g_im=TP * np.array([0, 10e6, 0]),
+                       u=u, m0=W.tilted_state(1, nx, ny, nz, 5.0, 0.3),
+                       a0=np.array([1e-3, 0, 2e-4j]), T=1e-6)
+    return p.replace(dt_max=W.stable_dt_max(p))
+
+
+@pytest.mark.parametrize("case", ["sphere", "afm", "profiles_holes"])
+def test_single_block_integrator_1000_steps(case):
+    """Grids that fit one block's shared memory run on the single-block integrator by default:
+    1000 adaptive attempts replayed by the oracle (error norms and step sizes checked)."""
+    p = {"sphere": W.single_sphere, "afm": small_afm, "profiles_holes": small_profiled}[case]()
+    dm, da, info = replay_compare(p, 1000)
+    assert info["tiling"]["blocks"] == 1 and info["tiling"]["bx"] == 0, info["tiling"]
+    assert dm <= TOL_M and da <= TOL_A, (dm, da, info["derr"])
+
+
+def test_single_block_and_tiled_kernels_agree():
+    """The same 8^3 sphere on the single-block integrator and on the tiled multi-block kernel
+    (tile forced): both replays match the oracle."""
+    p = W.single_sphere()
+    dm1, da1, i1 = replay_compare(p, 400)
+    dm2, da2, i2 = replay_compare(p, 400, tiling=(32, 4, 2))
+    assert i1["tiling"]["blocks"] == 1 and i2["tiling"]["blocks"] > 1
+    for dm, da in ((dm1, da1), (dm2, da2)):
+        assert dm <= TOL_M and da <= TOL_A, (dm, da)
+
+
+def test_single_block_split_scheme_matches_tiled():
+    """Operator-split mode on the single-block integrator against the tiled kernel."""
+    p = f32_state(W.single_sphere(T=0.2e-9).replace(a0=np.array([1e-2 + 0j])))
+    out = []
+    for tiling in (None, (32, 4, 2)):
+        sim = sim_for(p, log_cap=0, tiling=tiling)
+        sim.set_split(2e-12)
+        sim.run(p.T)
+        out.append((sim.get_m(), sim.get_a(), sim.get_tiling()["blocks"]))
+        sim.close()
+    assert out[0][2] == 1 and out[1][2] > 1
+    assert np.abs(out[0][0] - out[1][0]).max() < 1e-5
+    assert np.abs(out[0][1] - out[1][1]).max() < 1e-5 * np.abs(out[1][1]).max()
 
 
 # ---------------------------------------------------------------------------------------------
@@ -235,8 +299,10 @@ def test_autotune_restores_the_state_and_keeps_a_compiled_window():
     sim.run(p.T, max_attempts=5)
     m0, a0, st0 = sim.get_m(), sim.get_a(), sim.sync()
     t = sim.autotune(3)
-    assert (t["bx"], t["by"]) in ((32, 8), (32, 16), (64, 4))
-    assert all(v > 0 for v in t["us_per_attempt"].values()), t
+    assert (t["bx"], t["by"]) in ((32, 4), (32, 8), (32, 16))
+    us = t["us_per_attempt"]
+    assert all(us[k] > 0 for k in ("32x4", "32x8", "32x16")), t
+    assert us["single_block"] != us["single_block"], t   # NaN: the grid is too large for it
     st1 = sim.sync()
     assert np.array_equal(sim.get_m(), m0) and np.array_equal(sim.get_a(), a0)
     assert (st1["t"], st1["attempts"], st1["accepted"]) == (st0["t"], st0["attempts"],
