@@ -1,36 +1,10 @@
-// Batched integrator: one persistent cooperative launch advances many independent problems.
-// The blocks form teams of equal size; a team integrates the instances of its queue one after
-// the other with the same engine as the single-problem kernel, synchronising only its own
-// blocks through the instance's arrival counter.
+// Batched integrator: one persistent cooperative launch advances many independent problems
+// (kernel in cmx_batch_kernel.cuh, instantiated per tile shape in cmx_batch_t*.cu); the
+// per-launch bookkeeping kernels, the drive and the spectral map.
 #include "cmx_engine.cuh"
 #include "cmx_kernels.h"
 
 namespace cmx {
-
-template <int NS, int WX, int WY>
-__global__ void __launch_bounds__(WX *WY, (WX * WY <= 128 ? 4 : (WX * WY <= 256 ? 2 : 1)))
-    batch_kernel(BatchArgs B)
-{
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    auto &sm = *reinterpret_cast<StageSmem<NS, WX, WY, false> *>(smem_raw);
-    __shared__ Local L;
-    __shared__ Coef cf;
-    __shared__ int s_stop;
-    __shared__ __align__(16) Ctx sc;
-    const int team = blockIdx.x / B.team_size, rank = blockIdx.x % B.team_size;
-    const int qb = __ldg(&B.q_begin[team]), qe = __ldg(&B.q_begin[team + 1]);
-    for (int q = qb; q < qe; q++) {
-        const int inst = __ldg(&B.queue[q]);
-        // the instance's context into shared memory (word copy)
-        const int *src = reinterpret_cast<const int *>(B.ctx + inst);
-        int *dst = reinterpret_cast<int *>(&sc);
-        for (int w = threadIdx.x; w < (int)(sizeof(Ctx) / sizeof(int)); w += WX * WY)
-            dst[w] = __ldg(src + w);
-        __syncthreads();
-        const Team tm{rank, B.team_size, &sc.ctl->bar_count};
-        integrate(sc, tm, sm, L, cf, s_stop);
-    }
-}
 
 // Stream-ordered start of a batch launch: reset every instance's per-launch counters.
 __global__ void batch_prep_kernel(Ctl *const *ctls, int n, long long max_attempts)
@@ -62,38 +36,15 @@ __global__ void batch_pending_kernel(Ctl *const *ctls, int n, int *pending)
 }
 
 template <int NS, int WX, int WY>
-static cudaError_t batch_launch_variant(const BatchArgs &b, int blocks, cudaStream_t s)
-{
-    auto *fn = batch_kernel<NS, WX, WY>;
-    const size_t smem = sizeof(StageSmem<NS, WX, WY, false>);
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return e;
-    BatchArgs bb = b;
-    void *args[] = {&bb};
-    return cudaLaunchCooperativeKernel((const void *)fn, dim3(blocks), dim3(WX * WY), args, smem,
-                                       s);
-}
-
+cudaError_t batch_launch_tiles(const BatchArgs &b, int blocks, cudaStream_t s);
 template <int NS, int WX, int WY>
-static int batch_occupancy_variant()
-{
-    auto *fn = batch_kernel<NS, WX, WY>;
-    const size_t smem = sizeof(StageSmem<NS, WX, WY, false>);
-    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-        cudaSuccess)
-        return 0;
-    int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, WX * WY, smem) != cudaSuccess)
-        return 0;
-    return nb;
-}
+int batch_occupancy_tiles();
 
 #define CMX_BATCH_VARIANTS(X) X(1, 32, 4) X(1, 32, 8) X(1, 32, 16) X(2, 32, 4) X(2, 32, 8)
 
 cudaError_t launch_batch(const BatchArgs &b, int nsub, int bx, int by, int blocks, cudaStream_t s)
 {
-#define X(n, a, c) if (nsub == n && bx == a && by == c) return batch_launch_variant<n, a, c>(b, blocks, s);
+#define X(n, a, c) if (nsub == n && bx == a && by == c) return batch_launch_tiles<n, a, c>(b, blocks, s);
     CMX_BATCH_VARIANTS(X)
 #undef X
     return cudaErrorInvalidValue;
@@ -101,7 +52,7 @@ cudaError_t launch_batch(const BatchArgs &b, int nsub, int bx, int by, int block
 
 int batch_blocks_per_sm(int nsub, int bx, int by)
 {
-#define X(n, a, c) if (nsub == n && bx == a && by == c) return batch_occupancy_variant<n, a, c>();
+#define X(n, a, c) if (nsub == n && bx == a && by == c) return batch_occupancy_tiles<n, a, c>();
     CMX_BATCH_VARIANTS(X)
 #undef X
     return 0;

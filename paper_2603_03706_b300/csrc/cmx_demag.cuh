@@ -34,7 +34,7 @@ __device__ __forceinline__ int bit_reverse(int n, int lg)
 // In-place radix-2 transforms of nl lines of length L = 2^lg in shared memory (line l at
 // s + l * L), input in bit-reversed order, output in natural order; tw[k] = e^{-2 pi i k / L},
 // k < L/2; inv: conjugate twiddles (unscaled inverse).  Ends with a block barrier.
-__device__ void smem_fft(float2 *s, int L, int lg, int nl, const float2 *tw, bool inv)
+static __device__ void smem_fft(float2 *s, int L, int lg, int nl, const float2 *tw, bool inv)
 {
     const int half = L >> 1, nb = nl * half;
     for (int h = 1; h < L; h <<= 1) {

@@ -1,0 +1,74 @@
+// Persistent single-problem integrator kernel and its launch helpers, instantiated per tile
+// shape in the cmx_single_t*.cu files (one compilation unit each, so they build in parallel).
+#pragma once
+
+#include "cmx_engine.cuh"
+#include "cmx_kernels.h"
+
+namespace cmx {
+
+// Blocks of WX x WY threads (one cell each); registers held so that several blocks are resident
+// per SM: four of 128 threads, two of 256, one of 512.
+template <int NT>
+struct MinBlocks {
+    static constexpr int value = NT <= 128 ? 4 : (NT <= 256 ? 2 : 1);
+};
+
+template <int NS, int WX, int WY, bool HU>
+__global__ void __launch_bounds__(WX *WY, (MinBlocks<WX * WY>::value)) run_kernel(Ctx c)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    auto &sm = *reinterpret_cast<StageSmem<NS, WX, WY, HU> *>(smem_raw);
+    __shared__ Local L;
+    __shared__ Coef cf;
+    __shared__ int s_stop;
+    const Team tm{(int)blockIdx.x, (int)gridDim.x, &c.ctl->bar_count};
+    integrate(c, tm, sm, L, cf, s_stop);
+}
+
+template <int NS, int WX, int WY, bool HU>
+static cudaError_t launch_variant(const Ctx &c, int blocks, cudaStream_t s)
+{
+    auto *fn = run_kernel<NS, WX, WY, HU>;
+    const size_t smem = sizeof(StageSmem<NS, WX, WY, HU>);
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    Ctx cc = c;
+    void *args[] = {&cc};
+    return cudaLaunchCooperativeKernel((const void *)fn, dim3(blocks), dim3(WX * WY), args, smem,
+                                       s);
+}
+
+template <int NS, int WX, int WY, bool HU>
+static int occupancy_variant()
+{
+    auto *fn = run_kernel<NS, WX, WY, HU>;
+    const size_t smem = sizeof(StageSmem<NS, WX, WY, HU>);
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess)
+        return 0;
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, WX * WY, smem) != cudaSuccess)
+        return 0;
+    return nb;
+}
+
+template <int NS, int WX, int WY>
+cudaError_t launch_tiles(const Ctx &c, int blocks, cudaStream_t s)
+{
+    return c.u ? launch_variant<NS, WX, WY, true>(c, blocks, s)
+               : launch_variant<NS, WX, WY, false>(c, blocks, s);
+}
+
+template <int NS, int WX, int WY>
+int occupancy_tiles(bool has_u)
+{
+    return has_u ? occupancy_variant<NS, WX, WY, true>() : occupancy_variant<NS, WX, WY, false>();
+}
+
+#define CMX_INSTANTIATE_TILES(NS, WX, WY)                                                    \
+    template cudaError_t launch_tiles<NS, WX, WY>(const Ctx &, int, cudaStream_t);          \
+    template int occupancy_tiles<NS, WX, WY>(bool);
+
+}  // namespace cmx

@@ -1,0 +1,6 @@
+// Tile 8 rows x 32 cells, 2 sublattice(s): instantiation of the single-problem kernel.
+#include "cmx_single_kernel.cuh"
+
+namespace cmx {
+CMX_INSTANTIATE_TILES(2, 32, 8)
+}  // namespace cmx
