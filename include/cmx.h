@@ -218,7 +218,7 @@ int cmx_set_kerr(cmx_problem *h, const double *kerr);
  * state after each trial (m, FSAL slope, control block; the step log and trace counters roll
  * back too) and keep the fastest.  *chosen (may be NULL) receives it (bx = by = 0: the
  * single-block integrator); us_per_attempt (may be NULL, 4 entries) the measured times in that
- * order (NaN where a candidate does not apply). */
+ * order (NaN where a candidate does not apply; with full demag only 32x8 is timed). */
 int cmx_autotune(cmx_problem *h, int attempts, cmx_tiling *chosen, double *us_per_attempt);
 
 /* Full magnetostatic demag (mode 1) instead of the diagonal factors Ndemag of cmx_material
@@ -233,6 +233,19 @@ int cmx_autotune(cmx_problem *h, int attempts, cmx_tiling *chosen, double *us_pe
  * Returns CMX_EINVAL for a larger grid, a recording adjoint or another mode. */
 #define CMX_DEMAG_MAX_FFT 256
 int cmx_set_demag(cmx_problem *h, int mode);
+
+/* Checkpoint and resume (no counterpart in the paper): cmx_save_state writes into the host
+ * buffer `blob` (cap bytes) the integrator's state: the control block (time, step size, cavity
+ * amplitudes and slopes, counters, step-log and trace positions, controller flags) and the
+ * stored state m_n and FSAL slope of every cell; *size (may be NULL) receives the byte count
+ * (blob == NULL: size query only).  cmx_load_state puts such a blob into a handle created for
+ * the same grid, mask, sublattices and mode count (CMX_EINVAL otherwise) and configured the same
+ * way (solver, drive, couplings, split, demag: those are not in the blob); a run continued from
+ * it is bitwise the run continued from the saved handle.  The step log and trace buffers keep
+ * their contents; new entries continue at the saved positions.  A replay in progress is not
+ * resumed, and loading ends any checkpoint recording for the adjoint.  Both synchronise. */
+int cmx_save_state(cmx_problem *h, void *blob, size_t cap, size_t *size);
+int cmx_load_state(cmx_problem *h, const void *blob, size_t size);
 
 /* Planning query, host only (no device work, callable without a GPU): the row-compacted layout
  * and the partition that `blocks` blocks of bx x by tiles would use for this grid and mask
@@ -324,8 +337,8 @@ int cmx_batch_create(const cmx_instance *inst, int n, const cmx_solver *solver,
                      const cmx_batch_config *cfg, void *stream, cmx_batch **out);
 int cmx_batch_destroy(cmx_batch *b);
 
-/* Batch autotuner: for every candidate launch shape (window 32x8 or 32x16 (two sublattices:
- * 32x8, 64x4) times team size automatic, 1, 2, 4, 8, 16), build a trial batch over every k-th
+/* Batch autotuner: for every candidate launch shape (tile 32x8 or 32x16 (two sublattices:
+ * 32x4), times team size automatic, 1, 2, 4, 8, 16), build a trial batch over every k-th
  * instance (k = ceil(n / sample)), time one launch of `attempts` attempts per instance with CUDA
  * events after a one-attempt warm-up launch, and destroy it.  cfg is read for use_graph and
  * blocks_per_sm and receives the fastest bx, by, team.  us (may be NULL, 12 entries) gets the

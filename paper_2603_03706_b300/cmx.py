@@ -113,6 +113,8 @@ SIGNATURES = {
     "cmx_get_tiling": (C.c_int, [_P, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int),
                                    C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "cmx_set_demag": (C.c_int, [_P, C.c_int]),
+    "cmx_save_state": (C.c_int, [_P, C.c_void_p, C.c_size_t, C.POINTER(C.c_size_t)]),
+    "cmx_load_state": (C.c_int, [_P, C.c_void_p, C.c_size_t]),
     "cmx_plan_tiling": (C.c_int, [C.POINTER(Grid), C.c_void_p, C.c_int, C.c_int, C.c_int,
                                   C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]),
     "cmx_last_error": (C.c_char_p, [_P]),
@@ -492,6 +494,19 @@ class Simulation:
     def set_split(self, ds: float):
         """cmx_set_split: operator-split scheme with interval ds (0: the coupled scheme)."""
         self._check(load().cmx_set_split(self.h, float(ds)), "set_split")
+
+    def save_state(self) -> bytes:
+        """cmx_save_state: the integrator's state as a host blob."""
+        n = C.c_size_t()
+        self._check(load().cmx_save_state(self.h, None, 0, C.byref(n)), "save_state")
+        buf = (C.c_ubyte * n.value)()
+        self._check(load().cmx_save_state(self.h, buf, n.value, None), "save_state")
+        return bytes(buf)
+
+    def load_state(self, blob: bytes):
+        """cmx_load_state: resume from a blob of save_state (same problem and settings)."""
+        buf = (C.c_ubyte * len(blob)).from_buffer_copy(blob)
+        self._check(load().cmx_load_state(self.h, buf, len(blob)), "load_state")
 
     def set_demag(self, full: bool):
         """cmx_set_demag: full magnetostatic demag (True) or the diagonal factors (False)."""

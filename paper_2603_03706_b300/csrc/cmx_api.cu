@@ -206,6 +206,12 @@ int setup_small(cmx_problem *h, const cmx_tiling *t)
 
 }  // namespace
 
+int cmx_host::retile(cmx_problem *h, int bx, int by)
+{
+    const cmx_tiling t{bx, by, h->bz, h->bps_cap, 1};
+    return setup_tiling(h, &t);
+}
+
 Ctx cmx_host::make_ctx(const cmx_problem *h)
 {
     Ctx c = h->base;
@@ -757,6 +763,91 @@ int cmx_eval_rhs(cmx_problem *h, const float *m, const double *a, float *dm, dou
     return CMX_OK;
 }
 
+// Checkpoint blob: a header (magic, version, the sizes that must match), the control block and
+// the compact state m_n and FSAL slope k_1 of every stored cell.
+namespace {
+struct StateHeader {
+    unsigned magic, version;
+    int nx, ny, nz, nsub, nmodes, ncell, ncell_mag;
+    unsigned ctl_bytes;
+    long long nfloats;   // floats of m and of k1 each
+};
+constexpr unsigned STATE_MAGIC = 0x53584d43u;   // "CMXS"
+constexpr unsigned STATE_VERSION = 1;
+
+size_t state_bytes(const cmx_problem *h)
+{
+    return sizeof(StateHeader) + sizeof(Ctl) + 2 * (size_t)3 * h->grid.nsub * h->ncell * sizeof(float);
+}
+}  // namespace
+
+int cmx_save_state(cmx_problem *h, void *blob, size_t cap, size_t *size)
+{
+    if (!h) return CMX_EINVAL;
+    const size_t need = state_bytes(h);
+    if (size) *size = need;
+    if (!blob) return CMX_OK;   // size query
+    if (cap < need) return fail(h, CMX_EINVAL, "state blob needs %zu bytes", need);
+    Ctl hc;
+    int rc = read_ctl(h, &hc);
+    if (rc) return rc;
+    if (hc.status) return device_status(h, hc);
+    unsigned char *b = static_cast<unsigned char *>(blob);
+    StateHeader hd{STATE_MAGIC, STATE_VERSION, h->grid.nx, h->grid.ny, h->grid.nz, h->grid.nsub,
+                   h->N, h->ncell, h->ncell_mag, (unsigned)sizeof(Ctl),
+                   (long long)3 * h->grid.nsub * h->ncell};
+    memcpy(b, &hd, sizeof hd);
+    memcpy(b + sizeof hd, &hc, sizeof hc);
+    float *m = reinterpret_cast<float *>(b + sizeof hd + sizeof hc);
+    const size_t bytes = (size_t)hd.nfloats * sizeof(float);
+    CU(cudaMemcpyAsync(m, h->mbuf[hc.mcur], bytes, cudaMemcpyDeviceToHost, h->stream));
+    CU(cudaMemcpyAsync(m + hd.nfloats, h->kbuf[hc.kphys[0]], bytes, cudaMemcpyDeviceToHost,
+                       h->stream));
+    CU(cudaStreamSynchronize(h->stream));
+    return CMX_OK;
+}
+
+int cmx_load_state(cmx_problem *h, const void *blob, size_t size)
+{
+    if (!h || !blob) return fail(h, CMX_EINVAL, "null argument");
+    if (size < sizeof(StateHeader)) return fail(h, CMX_EINVAL, "state blob too short");
+    StateHeader hd;
+    memcpy(&hd, blob, sizeof hd);
+    if (hd.magic != STATE_MAGIC || hd.version != STATE_VERSION || hd.ctl_bytes != sizeof(Ctl))
+        return fail(h, CMX_EINVAL, "not a state blob of this library version");
+    if (hd.nx != h->grid.nx || hd.ny != h->grid.ny || hd.nz != h->grid.nz ||
+        hd.nsub != h->grid.nsub || hd.nmodes != h->N || hd.ncell != h->ncell ||
+        hd.ncell_mag != h->ncell_mag || size < state_bytes(h))
+        return fail(h, CMX_EINVAL, "state blob is for another problem");
+    const unsigned char *b = static_cast<const unsigned char *>(blob);
+    Ctl hc;
+    memcpy(&hc, b + sizeof hd, sizeof hc);
+    // per-launch and device-side fields start afresh; a replay in progress is not resumed
+    hc.done = 0;
+    hc.launch_attempts = 0;
+    hc.max_launch_attempts = 1;
+    hc.replay = 0;
+    hc.replay_dts = nullptr;
+    hc.replay_pos = hc.replay_n = 0;
+    hc.bar_count = hc.bar_gen = 0;
+    memset(hc.racc, 0, sizeof hc.racc);
+    memset(hc.remax, 0, sizeof hc.remax);
+    hc.range_error = 0;
+    hc.skip_block = -1;
+    hc.timeout_where = 0;
+    const float *m = reinterpret_cast<const float *>(b + sizeof hd + sizeof hc);
+    const size_t bytes = (size_t)hd.nfloats * sizeof(float);
+    CU(cudaMemcpyAsync(h->mbuf[hc.mcur], m, bytes, cudaMemcpyHostToDevice, h->stream));
+    CU(cudaMemcpyAsync(h->kbuf[hc.kphys[0]], m + hd.nfloats, bytes, cudaMemcpyHostToDevice,
+                       h->stream));
+    CU(cudaMemcpyAsync(h->ctl, &hc, sizeof hc, cudaMemcpyHostToDevice, h->stream));
+    CU(cudaStreamSynchronize(h->stream));
+    // a loaded state ends any checkpoint recording for the adjoint
+    h->base.traj_m = h->base.traj_k = nullptr;
+    h->base.traj_a = nullptr;
+    return CMX_OK;
+}
+
 int cmx_ncells(const cmx_problem *h, long long *n_magnetic, long long *n_stored)
 {
     if (!h) return CMX_EINVAL;
@@ -870,19 +961,23 @@ int cmx_autotune(cmx_problem *h, int attempts, cmx_tiling *chosen, double *us_pe
         return cudaStreamSynchronize(st);
     };
     // candidates 0..2: the compiled tiles; 3: the single-block integrator (small grids only)
-    static const int cand[3][2] = {{32, 4}, {32, 8}, {32, 16}};
+    constexpr int NC = 3, SB = NC;
+    static const int cand[NC][2] = {{32, 4}, {32, 8}, {32, 16}};
     const int bz = h->bz, bps = h->bps_cap;
-    double best = 1e300, tus[4];
+    double best = 1e300, tus[NC + 1];
     int bi = 0;
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    for (int ci = 0; ci < 4; ci++) {
+    for (int ci = 0; ci <= NC; ci++) {
         double us = NAN;
-        const bool small = ci == 3;
+        const bool small = ci == SB;
         cmx_tiling t{small ? 0 : cand[ci][0], small ? 0 : cand[ci][1], bz, bps, 1};
         h->use_small = small;
-        if (small ? (h->small_ok && !h->base.fd)
+        // full demag runs on the 32 x 8 tiles only
+        const bool allowed = !h->base.fd || (!small && t.bx == 32 && t.by == 8);
+        if (!allowed ? false
+            : small ? h->small_ok
                   : (tile_shape_supported(h->grid.nsub, t.bx, t.by) && setup_tiling(h, &t) == CMX_OK)) {
             PrepArgs pa{};
             pa.T = INFINITY;
@@ -916,10 +1011,10 @@ int cmx_autotune(cmx_problem *h, int attempts, cmx_tiling *chosen, double *us_pe
     cudaFree(k_save);
     if (!(best < 1e300)) return fail(h, CMX_ECUDA, "autotune: no window could be timed");
     // the tiled partition stays installed in every case (the adjoint's recorded runs use it)
-    int tb = bi == 3 ? 1 : bi;
-    if (bi == 3) {   // the single-block integrator won: keep the best tile for recorded runs
+    int tb = bi == SB ? 1 : bi;
+    if (bi == SB) {   // the single-block integrator won: keep the best tile for recorded runs
         double bt = 1e300;
-        for (int ci = 0; ci < 3; ci++)
+        for (int ci = 0; ci < NC; ci++)
             if (tus[ci] == tus[ci] && tus[ci] < bt) {
                 bt = tus[ci];
                 tb = ci;
@@ -928,9 +1023,9 @@ int cmx_autotune(cmx_problem *h, int attempts, cmx_tiling *chosen, double *us_pe
     cmx_tiling t{cand[tb][0], cand[tb][1], bz, bps, 1};
     rc = setup_tiling(h, &t);
     if (rc) return rc;
-    h->use_small = bi == 3;
+    h->use_small = bi == SB;
     h->small_default = h->use_small;
-    if (chosen) *chosen = bi == 3 ? cmx_tiling{0, 0, bz, bps, 1} : t;
+    if (chosen) *chosen = bi == SB ? cmx_tiling{0, 0, bz, bps, 1} : t;
     return CMX_OK;
 }
 

@@ -11,7 +11,7 @@
 namespace cmx {
 
 template <int NS, int WX, int WY>
-__global__ void __launch_bounds__(WX *WY, (WX * WY <= 128 ? 4 : (WX * WY <= 256 ? 2 : 1)))
+__global__ void __launch_bounds__(32 * WY, (WY <= 4 ? 4 : (WY <= 8 ? 2 : 1)))
     batch_kernel(BatchArgs B)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -27,11 +27,11 @@ __global__ void __launch_bounds__(WX *WY, (WX * WY <= 128 ? 4 : (WX * WY <= 256 
         // the instance's context into shared memory (word copy)
         const int *src = reinterpret_cast<const int *>(B.ctx + inst);
         int *dst = reinterpret_cast<int *>(&sc);
-        for (int w = threadIdx.x; w < (int)(sizeof(Ctx) / sizeof(int)); w += WX * WY)
+        for (int w = threadIdx.x; w < (int)(sizeof(Ctx) / sizeof(int)); w += 32 * WY)
             dst[w] = __ldg(src + w);
         __syncthreads();
         const Team tm{rank, B.team_size, &sc.ctl->bar_count};
-        integrate(sc, tm, sm, L, cf, s_stop);
+        integrate<false>(sc, tm, sm, L, cf, s_stop);
     }
 }
 
@@ -45,7 +45,7 @@ static cudaError_t batch_launch_variant(const BatchArgs &b, int blocks, cudaStre
     if (e != cudaSuccess) return e;
     BatchArgs bb = b;
     void *args[] = {&bb};
-    return cudaLaunchCooperativeKernel((const void *)fn, dim3(blocks), dim3(WX * WY), args, smem,
+    return cudaLaunchCooperativeKernel((const void *)fn, dim3(blocks), dim3(32 * WY), args, smem,
                                        s);
 }
 
@@ -58,7 +58,7 @@ static int batch_occupancy_variant()
         cudaSuccess)
         return 0;
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, WX * WY, smem) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, 32 * WY, smem) != cudaSuccess)
         return 0;
     return nb;
 }

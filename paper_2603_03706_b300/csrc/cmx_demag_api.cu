@@ -222,5 +222,5 @@ extern "C" int cmx_set_demag(cmx_problem *h, int mode)
     c.lgy = log2i(Ly);
     c.lgz = log2i(Lz);
     h->use_small = false;   // the single-block integrator has no demag passes
-    return CMX_OK;
+    return retile(h, 32, 8);   // the kernels with the demag passes use 32 x 8 tiles
 }

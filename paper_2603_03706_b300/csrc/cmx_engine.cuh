@@ -607,19 +607,21 @@ __device__ __forceinline__ const float *slope_buffer(const Ctx &c, int kj)
 // controller overlap the first copies, and warp 0 runs the controller.  The team's rank 0
 // clears the set that stage count + 2 will use: every block read it before arriving at this
 // barrier.
-template <int S, class SM>
+template <int S, bool FD, class SM>
 __device__ bool run_stage(const Ctx &c, const Team &tm, SM &sm, Local &L, Coef &cf, Pipe &pp,
                           bool begun)
 {
     const int tid = threadIdx.x, N = c.nmodes;
     const float *mn = L.mcur ? c.m[1] : c.m[0];
     float *mnew = L.mcur ? c.m[0] : c.m[1];
-    // with full demag the stage's copies start after its demag passes (they use the pool)
-    begun = begun && !c.fd;
+    // with full demag (kernels compiled with FD) the stage's copies start after its demag passes
+    // (they use the pool)
+    const bool fd = FD && c.fd;
+    begun = begun && !fd;
     if (!begun) {
         if (tid < 7) sm.kp[tid] = slope_buffer(c, L.kphys[tid]);
         __syncthreads();
-        if (!c.fd) stage_begin<S>(c, sm, mn, pp);
+        if (!fd) stage_begin<S>(c, sm, mn, pp);
     }
     if (S <= 2) {
         if (tid < 32) cavity_stage_value<S>(L, cf, tid, tid < 2 * N);
@@ -627,9 +629,11 @@ __device__ bool run_stage(const Ctx &c, const Team &tm, SM &sm, Local &L, Coef &
         if (S == 2 && tid == 96) cf.h = (float)L.h;
         __syncthreads();
     }
-    if (c.fd) {
-        if (!demag_field<S>(c, tm, sm, L, cf, mn)) return false;
-        stage_begin<S>(c, sm, mn, pp);
+    if constexpr (FD) {
+        if (fd) {
+            if (!demag_field<S>(c, tm, sm, L, cf, mn)) return false;
+            stage_begin<S>(c, sm, mn, pp);
+        }
     }
     Acc acc;
 #pragma unroll
@@ -659,7 +663,7 @@ __device__ bool run_stage(const Ctx &c, const Team &tm, SM &sm, Local &L, Coef &
             else w->remax[clr] = 0u;
         }
     }
-    if (S >= 2 && S < 7 && !c.stage_only && !c.fd) stage_begin<(S < 7 ? S + 1 : 7)>(c, sm, mn, pp);
+    if (S >= 2 && S < 7 && !c.stage_only && !fd) stage_begin<(S < 7 ? S + 1 : 7)>(c, sm, mn, pp);
     controller<S>(c, tm, L, cf, sq, emax);
     __syncthreads();
     return true;
@@ -669,7 +673,7 @@ __device__ bool run_stage(const Ctx &c, const Team &tm, SM &sm, Local &L, Coef &
 // this block's segments and the mode constants, then run Dormand-Prince attempts until the
 // problem is done (t >= T, replay end, attempt budget of the launch, or an error).  The team's
 // rank-0 block writes the state back.  Returns false if the run stopped on a device error.
-template <class SM>
+template <bool FD = false, class SM>
 __device__ bool integrate(const Ctx &c, const Team &tm, SM &sm, Local &L, Coef &cf, int &s_stop)
 {
     if (threadIdx.x == 0) {
@@ -701,6 +705,7 @@ __device__ bool integrate(const Ctx &c, const Team &tm, SM &sm, Local &L, Coef &
         // |u| |m| <= 2 umax
         int P = 0;
         for (int t = 0; t < sm.nseg; t++) P += sm.seg[t].w - sm.seg[t].z;
+        P *= cells_per_thread(&sm);
         const float bound = 2.f * (float)(P > 1 ? P : 1) * fmaxf(c.umax, 1.f);
         const int k = 24 - (int)ceilf(log2f(bound));
         L.tscale = ldexpf(1.f, k);
@@ -718,17 +723,17 @@ __device__ bool integrate(const Ctx &c, const Team &tm, SM &sm, Local &L, Coef &
         __syncthreads();
         if (s_stop) break;
         while (!L.k1_valid) {   // twice at an operator-split boundary (see controller<1>)
-            if (!(ok = run_stage<1>(c, tm, sm, L, cf, pp, false)))
+            if (!(ok = run_stage<1, FD>(c, tm, sm, L, cf, pp, false)))
                 break;
             if (c.stage_only) break;
         }
         if (!ok || c.stage_only) break;
-        if (!(ok = run_stage<2>(c, tm, sm, L, cf, pp, false))) break;
-        if (!(ok = run_stage<3>(c, tm, sm, L, cf, pp, true))) break;
-        if (!(ok = run_stage<4>(c, tm, sm, L, cf, pp, true))) break;
-        if (!(ok = run_stage<5>(c, tm, sm, L, cf, pp, true))) break;
-        if (!(ok = run_stage<6>(c, tm, sm, L, cf, pp, true))) break;
-        if (!(ok = run_stage<7>(c, tm, sm, L, cf, pp, true))) break;
+        if (!(ok = run_stage<2, FD>(c, tm, sm, L, cf, pp, false))) break;
+        if (!(ok = run_stage<3, FD>(c, tm, sm, L, cf, pp, true))) break;
+        if (!(ok = run_stage<4, FD>(c, tm, sm, L, cf, pp, true))) break;
+        if (!(ok = run_stage<5, FD>(c, tm, sm, L, cf, pp, true))) break;
+        if (!(ok = run_stage<6, FD>(c, tm, sm, L, cf, pp, true))) break;
+        if (!(ok = run_stage<7, FD>(c, tm, sm, L, cf, pp, true))) break;
     }
     if (ok && tm.rank == 0 && threadIdx.x == 0) store_local(c, L);
     __syncthreads();

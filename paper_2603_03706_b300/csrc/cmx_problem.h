@@ -105,5 +105,7 @@ int read_ctl(cmx_problem *h, Ctl *out);
 int device_status(cmx_problem *h, const Ctl &c);
 void adj_free(cmx_problem *h);
 void demag_release(cmx_problem *h);
+// install the bx x by tile partition (bz and blocks_per_sm as before)
+int retile(cmx_problem *h, int bx, int by);
 
 }  // namespace cmx_host

@@ -7,15 +7,17 @@
 
 namespace cmx {
 
-// Blocks of WX x WY threads (one cell each); registers held so that several blocks are resident
-// per SM: four of 128 threads, two of 256, one of 512.
+// Blocks of 32 x WY threads computing 32 x WY tiles (one cell per thread); registers held so
+// that several blocks are resident per SM: four of 128 threads, two of 256, one of 512.
 template <int NT>
 struct MinBlocks {
     static constexpr int value = NT <= 128 ? 4 : (NT <= 256 ? 2 : 1);
 };
 
-template <int NS, int WX, int WY, bool HU>
-__global__ void __launch_bounds__(WX *WY, (MinBlocks<WX * WY>::value)) run_kernel(Ctx c)
+// FD: compiled with the full-demag passes (only the 32 x 8 tiles; the plain kernels stay
+// free of that code)
+template <int NS, int WX, int WY, bool HU, bool FD>
+__global__ void __launch_bounds__(32 * WY, (MinBlocks<32 * WY>::value)) run_kernel(Ctx c)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     auto &sm = *reinterpret_cast<StageSmem<NS, WX, WY, HU> *>(smem_raw);
@@ -23,33 +25,33 @@ __global__ void __launch_bounds__(WX *WY, (MinBlocks<WX * WY>::value)) run_kerne
     __shared__ Coef cf;
     __shared__ int s_stop;
     const Team tm{(int)blockIdx.x, (int)gridDim.x, &c.ctl->bar_count};
-    integrate(c, tm, sm, L, cf, s_stop);
+    integrate<FD>(c, tm, sm, L, cf, s_stop);
 }
 
-template <int NS, int WX, int WY, bool HU>
+template <int NS, int WX, int WY, bool HU, bool FD>
 static cudaError_t launch_variant(const Ctx &c, int blocks, cudaStream_t s)
 {
-    auto *fn = run_kernel<NS, WX, WY, HU>;
+    auto *fn = run_kernel<NS, WX, WY, HU, FD>;
     const size_t smem = sizeof(StageSmem<NS, WX, WY, HU>);
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
     Ctx cc = c;
     void *args[] = {&cc};
-    return cudaLaunchCooperativeKernel((const void *)fn, dim3(blocks), dim3(WX * WY), args, smem,
+    return cudaLaunchCooperativeKernel((const void *)fn, dim3(blocks), dim3(32 * WY), args, smem,
                                        s);
 }
 
 template <int NS, int WX, int WY, bool HU>
 static int occupancy_variant()
 {
-    auto *fn = run_kernel<NS, WX, WY, HU>;
+    auto *fn = run_kernel<NS, WX, WY, HU, false>;
     const size_t smem = sizeof(StageSmem<NS, WX, WY, HU>);
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
         cudaSuccess)
         return 0;
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, WX * WY, smem) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, 32 * WY, smem) != cudaSuccess)
         return 0;
     return nb;
 }
@@ -57,8 +59,14 @@ static int occupancy_variant()
 template <int NS, int WX, int WY>
 cudaError_t launch_tiles(const Ctx &c, int blocks, cudaStream_t s)
 {
-    return c.u ? launch_variant<NS, WX, WY, true>(c, blocks, s)
-               : launch_variant<NS, WX, WY, false>(c, blocks, s);
+    if (c.fd) {
+        if constexpr (WX == 32 && WY == 8)
+            return c.u ? launch_variant<NS, WX, WY, true, true>(c, blocks, s)
+                       : launch_variant<NS, WX, WY, false, true>(c, blocks, s);
+        return cudaErrorInvalidValue;   // full demag runs on the 32 x 8 tiles
+    }
+    return c.u ? launch_variant<NS, WX, WY, true, false>(c, blocks, s)
+               : launch_variant<NS, WX, WY, false, false>(c, blocks, s);
 }
 
 template <int NS, int WX, int WY>

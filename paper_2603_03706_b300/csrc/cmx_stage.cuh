@@ -160,31 +160,41 @@ __device__ __forceinline__ void cp_async_wait()
 // Row-table entries cached for the first planes of a block's stream.
 constexpr int ROWC = 16;
 
-// Shared memory of a block of WX x WY threads.  The tile of a plane holds PX x PY positions
-// (the WX x WY cells and their one-cell rim): stage values and presence, RING planes of them
-// (p-1, p, p+1 read by the stencil of plane p, later planes in flight).  The operand pool holds,
-// per plane in flight, the thread's own operands of the next combine ([array][q][thread]) and,
-// at stage 2, the slope k_1 of the tile positions ([q][position]).
-template <int NS, int WX, int WY, bool HU>
+// Shared memory of a block of 32 x WY threads whose tile is CX x WY cells: every thread owns a
+// "unit" of CPT = CX / 32 consecutive x-cells of one tile row (CPT = 1 or 2).  The tile of a
+// plane holds PXS x PY positions: the tile's cells at columns OFF .. OFF+CX-1 of rows 1 .. WY,
+// the one-cell rim at rows 0 and PY-1 and at columns OFF-1 and OFF+CX (OFF = CPT keeps every unit
+// aligned to its size).  RING planes of stage values and presence (p-1, p, p+1 read by the
+// stencil of plane p, later planes in flight).  The operand pool holds, per plane in flight, the
+// thread's own operands of the next combine ([array][q][cell]) and, at stage 2, the slope k_1 of
+// the tile positions ([q][position]); with mode profiles their values of the thread's unit.
+template <int NS, int CX, int WY, bool HU>
 struct StageSmem {
-    static constexpr int W = WX * WY;
-    static constexpr int PX = WX + 2, PY = WY + 2, P = PX * PY;
-    static constexpr int NR = 2 * PX + 2 * WY;            // rim positions
+    static constexpr int CPT = CX / 32;                   // cells per thread
+    static constexpr int NT = 32 * WY;                    // threads
+    static constexpr int CW = CX * WY;                    // cells of a tile plane
+    static constexpr int OFF = CPT;
+    static constexpr int PXS = CX + 2 * OFF, PY = WY + 2, P = PXS * PY;
+    static constexpr int NRU = 64;                        // rim units: rows 0 and PY-1
+    static constexpr int NRS = 2 * PY;                    // rim singles: columns OFF-1, OFF+CX
     static constexpr int NQ = NS * 3;
     static constexpr int NAMAX = 5;                       // m_n + at most four slopes
     static constexpr int D = 2;                           // planes in flight
     static constexpr int RING = D + 2;                    // tile slots
     static constexpr int OIX = D + 1;                     // own-index slots
-    static constexpr int OPSLOT = NAMAX * NQ * W;         // operand slot (D of them)
-    static_assert(2 * NQ * W + NQ * P <= OPSLOT, "stage-2 slot");
-    static_assert(NR <= W, "rim positions need one thread each");
-    static_assert(WX == 32, "one warp per tile row");
-    float pool[D * OPSLOT];
-    float v[RING][NQ + 1][P];     // stage values of the tile positions, presence in row NQ
-    int oidx[OIX][W];             // compact index of the thread's cell of a plane in flight
-                                  // (-1: absent or a halo plane)
-    F2 red[32][2 * MAXN];         // per-warp partial overlaps (integer digits)
-    float redmax[32];
+    static constexpr int OPSLOT = NAMAX * NQ * CW;        // operand slot (D of them)
+    static constexpr int USLOT = HU ? MAXN * CW : 0;      // profile slot (D of them)
+    static_assert(CX == 32, "one cell per thread (64-wide two-cell tiles measured slower)");
+    static_assert(2 * NQ * CW + NQ * P <= OPSLOT, "stage-2 slot");
+    static_assert(NRU + NRS <= NT, "rim loads need one thread each");
+    static_assert(P % 2 == 0 && CW % 2 == 0 && OPSLOT % 4 == 0, "units stay 8-byte aligned");
+    alignas(16) float pool[D * OPSLOT];
+    alignas(16) float upool[D * USLOT + 4];
+    alignas(16) float v[RING][NQ + 1][P];   // stage values of the tile positions, presence in row NQ
+    int oidx[OIX][NT];            // compact index of the thread's first cell of a plane in flight
+                                  // (-1: no magnetic cell, or a halo plane)
+    F2 red[NT / 32][2 * MAXN];    // per-warp partial overlaps (integer digits)
+    float redmax[NT / 32];
     const float *kp[7];           // physical slope buffers in logical order
     int2 rows[8][PY];             // row-table entries of the tile rows, by plane mod 8
     int2 rowc[ROWC][PY];          // the same for the first ROWC planes of the stream (every
@@ -255,13 +265,51 @@ __device__ __forceinline__ int2 row_entry(const Ctx &c, int y, int z)
     return __ldg(&c.rows[z * c.ny + y]);
 }
 
+// Storage index of the unit of CPT cells that starts at box x (a multiple of CPT) in a row, or
+// -1 if the unit lies outside the row's stored span (whose ends are multiples of ROW_ALIGN, so
+// a unit is either inside or outside); pres[k] = 1 if cell x + k is magnetic.
+template <int CPT>
+__device__ __forceinline__ int unit_index(const Ctx &c, int2 r, int x, float (&pres)[CPT])
+{
+    const int xs = r.y & 0xffff, xe = (int)((unsigned)r.y >> 16);
+    const int xa = xs & ~(ROW_ALIGN - 1), xb = (xe + ROW_ALIGN - 1) & ~(ROW_ALIGN - 1);
+#pragma unroll
+    for (int k = 0; k < CPT; k++) pres[k] = 0.f;
+    if (x < xa || x >= xb) return -1;
+    const int idx = r.x + (x - xa);
+#pragma unroll
+    for (int k = 0; k < CPT; k++) {
+        bool on = x + k >= xs && x + k < xe;
+        if (on && c.active) on = (__ldg(&c.active[(idx + k) >> 5]) >> ((idx + k) & 31)) & 1u;
+        pres[k] = on ? 1.f : 0.f;
+    }
+    return idx;
+}
+
+// Asynchronous global -> shared copy of one unit (4 bytes per cell).
+template <int CPT>
+__device__ __forceinline__ void cp_async_unit(void *smem, const void *gmem)
+{
+    static_assert(CPT == 1, "one cell per unit");
+    cp_async4(smem, gmem);
+}
+
+// The CPT values of a unit in shared memory.
+template <int CPT>
+__device__ __forceinline__ void unit_load(const float *p, float (&o)[CPT])
+{
+#pragma unroll
+    for (int u = 0; u < CPT; u++) o[u] = p[u];
+}
+
 // Copy-pipeline state of one stage: cursors for row loading (cr) and copy issue (ci), the next
-// plane to issue, the stream length, and the thread's tile positions: its own cell (eo) and the
-// rim position it loads (er, -1: none) with the rim position's row and column (rr, rc).
+// plane to issue, the stream length, and the thread's tile positions: its own unit (eo) and the
+// rim element it loads (er, -1: none), a unit (rk = 1) or a single cell (rk = 2) at row rr and
+// column offset rc from the tile's x0 (rc in box cells).
 struct Pipe {
     Cursor cr, ci;
     int nq, gend;
-    int eo, er, rr, rc;
+    int eo, er, rr, rc, rk;
 };
 
 // Source of the tile values of stage S: m_n (S = 1, 2) or the stored stage value.
@@ -281,41 +329,44 @@ __device__ __forceinline__ const float *op_source(const Ctx &c, const SM &sm, co
     return sm.kp[op_slope(S, a)];
 }
 
-// Copies of one tile position of stream plane g into ring slot rs (stage values, and at stage 2
-// the slope k_1 into the operand slot's side array), presence written directly.
-template <class SM, int S>
-__device__ __forceinline__ void load_position(const Ctx &c, SM &sm, const float *tsrc,
-                                              int rs, float *side, int e, int idx)
+// Copies of U tile positions e .. e+U-1 (stored from compact index idx, or -1: outside the
+// row's stored span) of stream plane g into ring slot rs: stage values (and at stage 2 the slope
+// k_1 into the side array), presence written directly.  Inactive cells inside a stored span hold
+// 0 in every array, so a copied unit needs no masking; a position outside is zero-filled.
+template <class SM, int S, int U>
+__device__ __forceinline__ void load_positions(const Ctx &c, SM &sm, const float *tsrc, int rs,
+                                               float *side, int e, int idx, const float (&pres)[U])
 {
     constexpr int NQ = SM::NQ, P = SM::P;
     if (idx >= 0) {
 #pragma unroll
         for (int k = 0; k < NQ; k++) {
-            cp_async4(&sm.v[rs][k][e], tsrc + (size_t)k * c.ncell + idx);
-            if (S == 2) cp_async4(side + k * P + e, sm.kp[0] + (size_t)k * c.ncell + idx);
+            cp_async_unit<U>(&sm.v[rs][k][e], tsrc + (size_t)k * c.ncell + idx);
+            if (S == 2) cp_async_unit<U>(side + k * P + e, sm.kp[0] + (size_t)k * c.ncell + idx);
         }
-        sm.v[rs][NQ][e] = 1.f;
     } else {
-        // absent: value and presence 0 (the stencil sums absent neighbours as 0), and at stage 2
-        // the side slope 0 as well, so that the stage-2 combine leaves the position at 0
 #pragma unroll
-        for (int k = 0; k <= NQ; k++) sm.v[rs][k][e] = 0.f;
-        if (S == 2)
+        for (int k = 0; k < NQ; k++)
 #pragma unroll
-            for (int k = 0; k < NQ; k++) side[k * P + e] = 0.f;
+            for (int u = 0; u < U; u++) {
+                sm.v[rs][k][e + u] = 0.f;
+                if (S == 2) side[k * P + e + u] = 0.f;
+            }
     }
+#pragma unroll
+    for (int u = 0; u < U; u++) sm.v[rs][NQ][e + u] = pres[u];
 }
 
-// Copies of stream plane g, in two commit groups: first the tile (the position of the thread's
-// cell and, for the first NR threads, one rim position) with the presence flags and the own
-// compact index, later the thread's own operands of the stage's combine on planes interior to
-// their segment.  Both commit one group (possibly empty).
-template <int NS, int WX, int WY, bool HU, int S>
-__device__ __forceinline__ void issue_tile(const Ctx &c, StageSmem<NS, WX, WY, HU> &sm,
+// Copies of stream plane g, in two commit groups: first the tile (the thread's unit and, for the
+// first NRU + NRS threads, one rim unit or single) with the presence flags and the own compact
+// index, later the thread's own operands of the stage's combine (and profiles) on planes
+// interior to their segment.  Both commit one group (possibly empty).
+template <int NS, int CX, int WY, bool HU, int S>
+__device__ __forceinline__ void issue_tile(const Ctx &c, StageSmem<NS, CX, WY, HU> &sm,
                                            const float *mn, int g, Pipe &pp)
 {
-    using SM = StageSmem<NS, WX, WY, HU>;
-    constexpr int NQ = SM::NQ, W = SM::W;
+    using SM = StageSmem<NS, CX, WY, HU>;
+    constexpr int NQ = SM::NQ, CPT = SM::CPT;
     const int i = threadIdx.x;
     if (g < pp.gend) {
         cursor_seek(sm, pp.ci, g);
@@ -323,37 +374,55 @@ __device__ __forceinline__ void issue_tile(const Ctx &c, StageSmem<NS, WX, WY, H
         const int q = g - cu.off;
         const bool inner = q >= 1 && q <= cu.np - 2;
         const int rs = g % SM::RING;
-        float *side = sm.pool + (size_t)(g % SM::D) * SM::OPSLOT + n_ops(2) * NQ * W;
+        float *side = sm.pool + (size_t)(g % SM::D) * SM::OPSLOT + n_ops(2) * NQ * SM::CW;
         const float *tsrc = tile_source<S>(c, mn);
         const int2 *rw = sm.rows[g & 7];
-        const int idx = row_index(c, rw[i / WX + 1], cu.x0 + i % WX);
-        load_position<SM, S>(c, sm, tsrc, rs, side, pp.eo, idx);
-        sm.oidx[g % SM::OIX][i] = inner ? idx : -1;
-        if (pp.er >= 0) {
-            const int ridx = row_index(c, rw[pp.rr], cu.x0 - 1 + pp.rc);
-            load_position<SM, S>(c, sm, tsrc, rs, side, pp.er, ridx);
+        float pres[CPT];
+        const int idx = unit_index<CPT>(c, rw[i / 32 + 1], cu.x0 + CPT * (i % 32), pres);
+        load_positions<SM, S, CPT>(c, sm, tsrc, rs, side, pp.eo, idx, pres);
+        bool any = false;
+#pragma unroll
+        for (int u = 0; u < CPT; u++) any |= pres[u] != 0.f;
+        sm.oidx[g % SM::OIX][i] = (inner && any) ? idx : -1;
+        if (pp.rk == 1) {
+            float rp[CPT];
+            const int ridx = unit_index<CPT>(c, rw[pp.rr], cu.x0 + pp.rc, rp);
+            load_positions<SM, S, CPT>(c, sm, tsrc, rs, side, pp.er, ridx, rp);
+        } else if (pp.rk == 2) {
+            float rp[1];
+            const int ridx = row_index(c, rw[pp.rr], cu.x0 + pp.rc);
+            rp[0] = ridx >= 0 ? 1.f : 0.f;
+            load_positions<SM, S, 1>(c, sm, tsrc, rs, side, pp.er, ridx, rp);
         }
     }
     cp_async_commit();
 }
 
-template <int NS, int WX, int WY, bool HU, int S>
-__device__ __forceinline__ void issue_ops(const Ctx &c, StageSmem<NS, WX, WY, HU> &sm,
+template <int NS, int CX, int WY, bool HU, int S>
+__device__ __forceinline__ void issue_ops(const Ctx &c, StageSmem<NS, CX, WY, HU> &sm,
                                           const float *mn, int g, const Pipe &pp)
 {
-    using SM = StageSmem<NS, WX, WY, HU>;
-    constexpr int NQ = SM::NQ, W = SM::W, NO = n_ops(S);
+    using SM = StageSmem<NS, CX, WY, HU>;
+    constexpr int NQ = SM::NQ, CW = SM::CW, CPT = SM::CPT, NO = n_ops(S);
     const int i = threadIdx.x;
-    if (NO > 0 && g < pp.gend) {
+    if (g < pp.gend) {
         const int oi = sm.oidx[g % SM::OIX][i];
-        float *slot = sm.pool + (size_t)(g % SM::D) * SM::OPSLOT;
         if (oi >= 0) {
+            float *slot = sm.pool + (size_t)(g % SM::D) * SM::OPSLOT;
 #pragma unroll
             for (int a = 0; a < NO; a++) {
                 const float *src = op_source<SM, S>(c, sm, mn, a);
 #pragma unroll
                 for (int k = 0; k < NQ; k++)
-                    cp_async4(slot + (a * NQ + k) * W + i, src + (size_t)k * c.ncell + oi);
+                    cp_async_unit<CPT>(slot + (a * NQ + k) * CW + CPT * i,
+                                       src + (size_t)k * c.ncell + oi);
+            }
+            if (HU) {
+                float *us = sm.upool + (size_t)(g % SM::D) * SM::USLOT;
+#pragma unroll
+                for (int n = 0; n < MAXN; n++)
+                    if (n < c.nmodes)
+                        cp_async_unit<CPT>(us + n * CW + CPT * i, c.u + (size_t)n * c.ncell + oi);
             }
         }
     }
@@ -362,20 +431,28 @@ __device__ __forceinline__ void issue_ops(const Ctx &c, StageSmem<NS, WX, WY, HU
 
 // Stage 2: the tile values m_2 = m_n + h a_21 k_1 of the thread's positions of plane g (the
 // copies of plane g are complete; only this thread wrote these positions).
-template <int NS, int WX, int WY, bool HU, int S>
-__device__ __forceinline__ void tile_combine(StageSmem<NS, WX, WY, HU> &sm, const Coef &cf, int g,
+template <int NS, int CX, int WY, bool HU, int S>
+__device__ __forceinline__ void tile_combine(StageSmem<NS, CX, WY, HU> &sm, const Coef &cf, int g,
                                              const Pipe &pp)
 {
-    using SM = StageSmem<NS, WX, WY, HU>;
-    constexpr int NQ = SM::NQ, P = SM::P;
+    using SM = StageSmem<NS, CX, WY, HU>;
+    constexpr int NQ = SM::NQ, P = SM::P, CPT = SM::CPT;
     if (S != 2 || g >= pp.gend) return;
     const int rs = g % SM::RING;
-    const float *side = sm.pool + (size_t)(g % SM::D) * SM::OPSLOT + n_ops(2) * NQ * SM::W;
+    const float *side = sm.pool + (size_t)(g % SM::D) * SM::OPSLOT + n_ops(2) * NQ * SM::CW;
     const float c21 = cf.cf[1][0];
+    const int nr = pp.rk == 1 ? CPT : (pp.rk == 2 ? 1 : 0);
 #pragma unroll
     for (int k = 0; k < NQ; k++) {
-        sm.v[rs][k][pp.eo] = fmaf(c21, side[k * P + pp.eo], sm.v[rs][k][pp.eo]);
-        if (pp.er >= 0) sm.v[rs][k][pp.er] = fmaf(c21, side[k * P + pp.er], sm.v[rs][k][pp.er]);
+#pragma unroll
+        for (int u = 0; u < CPT; u++) {
+            const int e = pp.eo + u;
+            sm.v[rs][k][e] = fmaf(c21, side[k * P + e], sm.v[rs][k][e]);
+        }
+        for (int u = 0; u < nr; u++) {
+            const int e = pp.er + u;
+            sm.v[rs][k][e] = fmaf(c21, side[k * P + e], sm.v[rs][k][e]);
+        }
     }
 }
 
@@ -433,98 +510,191 @@ __device__ __forceinline__ void cell_slope(const Ctx &c, const Coef &cf, const f
     }
 }
 
-// RHS of this thread's cell of plane p (ring slots: p-1, p, p+1), then the combine of the next
+// RHS of this thread's unit of plane p (ring slots: p-1, p, p+1), then the combine of the next
 // stage value from k_S and the operands in flight (stages 2..6), the error partial (stage 6), or
 // the error estimate and the renormalised new state (stage 7).  Accumulates the overlap sums and
-// the error maximum.
-template <int NS, int WX, int WY, bool HU, int S>
-__device__ __forceinline__ void compute_cell(const Ctx &c, StageSmem<NS, WX, WY, HU> &sm,
+// the error maximum over the unit's magnetic cells; a non-magnetic cell of the unit gets 0 in
+// every output (inactive cells hold 0 in every array).
+template <int NS, int CX, int WY, bool HU, int S>
+__device__ __forceinline__ void compute_cell(const Ctx &c, StageSmem<NS, CX, WY, HU> &sm,
                                              float *kout, float *mnew, const Coef &cf, int p,
-                                             const float *ucell, int tslot, int rslot,
-                                             const Pipe &pp, Acc &acc)
+                                             int tslot, int rslot, const Pipe &pp, Acc &acc)
 {
-    using SM = StageSmem<NS, WX, WY, HU>;
-    constexpr int NQ = SM::NQ, R = SM::RING, PX = SM::PX, W = SM::W, NO = n_ops(S);
+    using SM = StageSmem<NS, CX, WY, HU>;
+    constexpr int NQ = SM::NQ, R = SM::RING, PXS = SM::PXS, CW = SM::CW, CPT = SM::CPT;
+    constexpr int NO = n_ops(S);
     const int i = threadIdx.x;
     const int idx = sm.oidx[p % SM::OIX][i];
     if (idx < 0) return;
     const int sp = (p + R - 1) % R, sc = p % R, sn = (p + 1) % R;
     const int e = pp.eo;
     const float *op = sm.pool + (size_t)(p % SM::D) * SM::OPSLOT;
+    const int oc = CPT * i;   // the unit's first cell in the operand slot
+    const float *pr = sm.v[sc][NQ];
 
-    const float nx_ = sm.v[sc][NQ][e - 1] + sm.v[sc][NQ][e + 1];
-    const float ny_ = sm.v[sc][NQ][e - PX] + sm.v[sc][NQ][e + PX];
-    const float nz_ = sm.v[sp][NQ][e] + sm.v[sn][NQ][e];
+    // presence of the unit's cells and their neighbour counts per axis
+    float here[CPT], nx_[CPT], ny_[CPT], nz_[CPT];
+    {
+        float a[CPT], b[CPT], z0[CPT], z1[CPT];
+        unit_load<CPT>(pr + e, here);
+        unit_load<CPT>(pr + e - PXS, a);
+        unit_load<CPT>(pr + e + PXS, b);
+        unit_load<CPT>(sm.v[sp][NQ] + e, z0);
+        unit_load<CPT>(sm.v[sn][NQ] + e, z1);
+#pragma unroll
+        for (int u = 0; u < CPT; u++) {
+            ny_[u] = a[u] + b[u];
+            nz_[u] = z0[u] + z1[u];
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < CPT; u++)
+        nx_[u] = (u == 0 ? pr[e - 1] : here[u - 1]) + (u == CPT - 1 ? pr[e + CPT] : here[u + 1]);
 
-    float m[NS][3], B[NS][3];
+    // stage values and exchange fields of the unit's cells
+    float m[CPT][NS][3], B[CPT][NS][3];
 #pragma unroll
     for (int s = 0; s < NS; s++)
 #pragma unroll
         for (int k = 0; k < 3; k++) {
             const int q = s * 3 + k;
-            const float cen = sm.v[sc][q][e];
-            m[s][k] = cen;
-            // exchange: sum over present neighbours of (m_j - m_i) / c_d^2 (absent ones hold 0)
-            B[s][k] = c.wx * (sm.v[sc][q][e - 1] + sm.v[sc][q][e + 1] - nx_ * cen) +
-                      c.wy * (sm.v[sc][q][e - PX] + sm.v[sc][q][e + PX] - ny_ * cen) +
-                      c.wz * (sm.v[sp][q][e] + sm.v[sn][q][e] - nz_ * cen);
-        }
-
-    float bdem[3] = {0.f, 0.f, 0.f};
-    if (c.fd)
+            const float *vc = sm.v[sc][q], *vp = sm.v[sp][q], *vn = sm.v[sn][q];
+            float cen[CPT], ya[CPT], yb[CPT], za[CPT], zb[CPT];
+            unit_load<CPT>(vc + e, cen);
+            unit_load<CPT>(vc + e - PXS, ya);
+            unit_load<CPT>(vc + e + PXS, yb);
+            unit_load<CPT>(vp + e, za);
+            unit_load<CPT>(vn + e, zb);
+            const float left = vc[e - 1], right = vc[e + CPT];
 #pragma unroll
-        for (int k = 0; k < 3; k++) bdem[k] = __ldcg(c.bd + (size_t)k * c.ncell + idx);
-    float kvs[NS][3];
-    cell_slope<NS, HU>(c, cf, m, B, ucell, bdem, acc, kvs);
-
-#pragma unroll
-    for (int s = 0; s < NS; s++) {
-        const float *mm = m[s];
-        const float *kv = kvs[s];
-#pragma unroll
-        for (int k = 0; k < 3; k++) kout[(size_t)(s * 3 + k) * c.ncell + idx] = kv[k];
-        if (S >= 2 && rslot >= 0) {
-            const size_t o = ((size_t)rslot * 6 + (S >= 2 ? S - 2 : 0)) * NQ * c.ncell;
-#pragma unroll
-            for (int k = 0; k < 3; k++) c.rec_m[o + (size_t)(s * 3 + k) * c.ncell + idx] = mm[k];
-        }
-        if ((S == 1 || S == 7) && tslot >= 0) {
-            const size_t o = (size_t)tslot * NQ * c.ncell;
-            const float r = S == 7 ? rsqrtf(mm[0] * mm[0] + mm[1] * mm[1] + mm[2] * mm[2]) : 1.f;
-#pragma unroll
-            for (int k = 0; k < 3; k++) {
-                c.traj_m[o + (size_t)(s * 3 + k) * c.ncell + idx] = mm[k] * r;
-                c.traj_k[o + (size_t)(s * 3 + k) * c.ncell + idx] = kv[k];
+            for (int u = 0; u < CPT; u++) {
+                const float xl = u == 0 ? left : cen[u - 1], xr = u == CPT - 1 ? right : cen[u + 1];
+                m[u][s][k] = cen[u];
+                // exchange: sum over present neighbours of (m_j - m_i) / c_d^2 (absent ones hold 0)
+                B[u][s][k] = c.wx * (xl + xr - nx_[u] * cen[u]) +
+                             c.wy * (ya[u] + yb[u] - ny_[u] * cen[u]) +
+                             c.wz * (za[u] + zb[u] - nz_[u] * cen[u]);
             }
         }
-        if (S >= 2 && S <= 6 && !c.stage_only) {
-            // next stage value m_{S+1} = m_n + sum_j (h a_{S+1,j}) k_j, k_S last
-            float *out = c.msv[(S + 1) & 1];
+
+    float kv[CPT][NS][3];
+#pragma unroll
+    for (int u = 0; u < CPT; u++) {
+        float ucell[MAXN];
+#pragma unroll
+        for (int n = 0; n < MAXN; n++)
+            ucell[n] = (HU && n < c.nmodes)
+                           ? sm.upool[(size_t)(p % SM::D) * SM::USLOT + n * CW + oc + u] : 1.f;
+        float bdem[3] = {0.f, 0.f, 0.f};
+        if (c.fd && here[u] != 0.f)
+#pragma unroll
+            for (int k = 0; k < 3; k++) bdem[k] = __ldcg(c.bd + (size_t)k * c.ncell + idx + u);
+        // a non-magnetic cell of the unit holds m = 0, so its overlap terms are exactly 0
+        cell_slope<NS, HU>(c, cf, m[u], B[u], ucell, bdem, acc, kv[u]);
+        if (here[u] == 0.f)
+#pragma unroll
+            for (int s = 0; s < NS; s++)
+#pragma unroll
+                for (int k = 0; k < 3; k++) kv[u][s][k] = 0.f;
+    }
+
+    // stores of the unit: one store per cell and component
+    auto put = [&](float *base, int q, const float (&val)[CPT]) {
+        float *dst = base + (size_t)q * c.ncell + idx;
+#pragma unroll
+        for (int u = 0; u < CPT; u++) dst[u] = val[u];
+    };
+#pragma unroll
+    for (int s = 0; s < NS; s++)
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            const int q = s * 3 + k;
+            float o[CPT];
+#pragma unroll
+            for (int u = 0; u < CPT; u++) o[u] = kv[u][s][k];
+            put(kout, q, o);
+            if (S >= 2 && rslot >= 0) {
+#pragma unroll
+                for (int u = 0; u < CPT; u++) o[u] = m[u][s][k];
+                put(c.rec_m + ((size_t)rslot * 6 + (S >= 2 ? S - 2 : 0)) * NQ * c.ncell, q, o);
+            }
+        }
+    if ((S == 1 || S == 7) && tslot >= 0) {
+#pragma unroll
+        for (int s = 0; s < NS; s++) {
+            float r[CPT];
+#pragma unroll
+            for (int u = 0; u < CPT; u++) {
+                const float *mm = m[u][s];
+                r[u] = (S == 7 && here[u] != 0.f)
+                           ? rsqrtf(mm[0] * mm[0] + mm[1] * mm[1] + mm[2] * mm[2]) : 1.f;
+            }
+#pragma unroll
+            for (int k = 0; k < 3; k++) {
+                float om[CPT], ok[CPT];
+#pragma unroll
+                for (int u = 0; u < CPT; u++) {
+                    om[u] = m[u][s][k] * r[u];
+                    ok[u] = kv[u][s][k];
+                }
+                put(c.traj_m + (size_t)tslot * NQ * c.ncell, s * 3 + k, om);
+                put(c.traj_k + (size_t)tslot * NQ * c.ncell, s * 3 + k, ok);
+            }
+        }
+    }
+    if (S >= 2 && S <= 6 && !c.stage_only) {
+        // next stage value m_{S+1} = m_n + sum_j (h a_{S+1,j}) k_j, k_S last; error partial
+#pragma unroll
+        for (int s = 0; s < NS; s++)
 #pragma unroll
             for (int k = 0; k < 3; k++) {
                 const int q = s * 3 + k;
-                float a = op[(0 * NQ + q) * W + i];
-                float es = 0.f;
+                float a[CPT], es[CPT];
+                unit_load<CPT>(op + (0 * NQ + q) * CW + oc, a);
+#pragma unroll
+                for (int u = 0; u < CPT; u++) es[u] = 0.f;
 #pragma unroll
                 for (int o = 1; o < NO; o++) {
                     const int j = op_slope(S, o);
-                    const float kj = op[(o * NQ + q) * W + i];
-                    a = fmaf(cf.cf[S][j], kj, a);
-                    if (S == 6) es = fmaf(cf.e[j], kj, es);
+                    float kj[CPT];
+                    unit_load<CPT>(op + (o * NQ + q) * CW + oc, kj);
+#pragma unroll
+                    for (int u = 0; u < CPT; u++) {
+                        a[u] = fmaf(cf.cf[S][j], kj[u], a[u]);
+                        if (S == 6) es[u] = fmaf(cf.e[j], kj[u], es[u]);
+                    }
                 }
-                a = fmaf(cf.cf[S][S - 1], kv[k], a);
-                out[(size_t)q * c.ncell + idx] = a;
-                if (S == 6) c.es[(size_t)q * c.ncell + idx] = fmaf(cf.e[5], kv[k], es);
+#pragma unroll
+                for (int u = 0; u < CPT; u++) {
+                    a[u] = here[u] != 0.f ? fmaf(cf.cf[S][S - 1], kv[u][s][k], a[u]) : 0.f;
+                    es[u] = here[u] != 0.f ? fmaf(cf.e[5], kv[u][s][k], es[u]) : 0.f;
+                }
+                put(c.msv[(S + 1) & 1], q, a);
+                if (S == 6) put(c.es, q, es);
             }
-        }
-        if (S == 7) {
-            const float r = rsqrtf(mm[0] * mm[0] + mm[1] * mm[1] + mm[2] * mm[2]);
+    }
+    if (S == 7) {
+#pragma unroll
+        for (int s = 0; s < NS; s++) {
+            float r[CPT];
+#pragma unroll
+            for (int u = 0; u < CPT; u++) {
+                const float *mm = m[u][s];
+                r[u] = here[u] != 0.f ? rsqrtf(mm[0] * mm[0] + mm[1] * mm[1] + mm[2] * mm[2]) : 0.f;
+            }
 #pragma unroll
             for (int k = 0; k < 3; k++) {
                 const int q = s * 3 + k;
-                mnew[(size_t)q * c.ncell + idx] = mm[k] * r;
-                const float e7 = cf.h * fmaf(cf.e[6], kv[k], op[q * W + i]);
-                acc.emax = nanmax(acc.emax, fabsf(e7));
+                float o[CPT];
+#pragma unroll
+                for (int u = 0; u < CPT; u++) {
+                    o[u] = m[u][s][k] * r[u];
+                    if (here[u] != 0.f) {
+                        const float e7 = cf.h * fmaf(cf.e[6], kv[u][s][k], op[q * CW + oc + u]);
+                        acc.emax = nanmax(acc.emax, fabsf(e7));
+                    }
+                }
+                put(mnew, q, o);
             }
         }
     }
@@ -533,37 +703,37 @@ __device__ __forceinline__ void compute_cell(const Ctx &c, StageSmem<NS, WX, WY,
 // Start stage S's stream: row entries of the first planes and the first D planes of copies.
 // Needs only m_n, the slopes of earlier stages and the stage values stored by the previous stage,
 // so it can run before the cavity update of the previous stage is known.  Planes of the block's
-// segments: segment t covers x in [x0, x0+WX), y in [y0, y0+WY), z in [z0, z1) and contributes
+// segments: segment t covers x in [x0, x0+CX), y in [y0, y0+WY), z in [z0, z1) and contributes
 // planes z0-1 .. z1.
-template <int NS, int WX, int WY, bool HU, int S>
-__device__ void tiles_begin(const Ctx &c, StageSmem<NS, WX, WY, HU> &sm, const float *mn,
+template <int NS, int CX, int WY, bool HU, int S>
+__device__ void tiles_begin(const Ctx &c, StageSmem<NS, CX, WY, HU> &sm, const float *mn,
                             Pipe &pp)
 {
-    using SM = StageSmem<NS, WX, WY, HU>;
-    constexpr int D = SM::D, AHEAD = D + 1, PY = SM::PY, PX = SM::PX;
+    using SM = StageSmem<NS, CX, WY, HU>;
+    constexpr int D = SM::D, AHEAD = D + 1, PY = SM::PY, PXS = SM::PXS, CPT = SM::CPT;
+    constexpr int OFF = SM::OFF;
     pp.gend = 0;
     for (int t = 0; t < sm.nseg; t++) pp.gend += sm.seg[t].w - sm.seg[t].z + 2;
     pp.nq = 0;
     if (sm.nseg == 0) return;
     const int i = threadIdx.x;
-    pp.eo = (i / WX + 1) * PX + i % WX + 1;
+    pp.eo = (i / 32 + 1) * PXS + OFF + CPT * (i % 32);
     pp.er = -1;
-    pp.rr = pp.rc = 0;
-    if (i < SM::NR) {
-        if (i < PX) {
-            pp.rr = 0;
-            pp.rc = i;
-        } else if (i < 2 * PX) {
-            pp.rr = PY - 1;
-            pp.rc = i - PX;
-        } else if (i < 2 * PX + WY) {
-            pp.rr = i - 2 * PX + 1;
-            pp.rc = 0;
-        } else {
-            pp.rr = i - 2 * PX - WY + 1;
-            pp.rc = PX - 1;
-        }
-        pp.er = pp.rr * PX + pp.rc;
+    pp.rr = pp.rc = pp.rk = 0;
+    // rim: threads 0..63 the units of rows 0 and PY-1, the next 2 PY the single cells of columns
+    // OFF-1 and OFF+CX (the rim loads stay in as few warps as possible: a warp pays for its rim
+    // loads whenever one of its lanes has one)
+    if (i < SM::NRU) {
+        pp.rk = 1;
+        pp.rr = i < 32 ? 0 : PY - 1;
+        pp.rc = CPT * (i % 32);
+        pp.er = pp.rr * PXS + OFF + pp.rc;
+    } else if (i < SM::NRU + SM::NRS) {
+        const int j = i - SM::NRU;
+        pp.rk = 2;
+        pp.rr = j % PY;
+        pp.rc = j < PY ? -1 : CX;
+        pp.er = pp.rr * PXS + OFF + pp.rc;
     }
     pp.cr = cursor_start(sm);
     pp.ci = pp.cr;
@@ -576,8 +746,8 @@ __device__ void tiles_begin(const Ctx &c, StageSmem<NS, WX, WY, HU> &sm, const f
         }
     __syncthreads();
     for (; pp.nq < D; pp.nq++) {
-        issue_tile<NS, WX, WY, HU, S>(c, sm, mn, pp.nq, pp);
-        issue_ops<NS, WX, WY, HU, S>(c, sm, mn, pp.nq, pp);
+        issue_tile<NS, CX, WY, HU, S>(c, sm, mn, pp.nq, pp);
+        issue_ops<NS, CX, WY, HU, S>(c, sm, mn, pp.nq, pp);
     }
 }
 
@@ -586,13 +756,13 @@ __device__ void tiles_begin(const Ctx &c, StageSmem<NS, WX, WY, HU> &sm, const f
 // Iteration p: wait for plane p+1's tile (and plane p's operands; stage 2: form plane p+1's tile
 // values), publish it with the block barrier, issue plane p+D's tile, compute plane p, issue
 // plane p+D's operands into the slot plane p has just released.  Only planes interior to their
-// segment are computed; the profiles of the next computed cell are loaded one plane ahead.
-template <int NS, int WX, int WY, bool HU, int S>
-__device__ void tiles_run(const Ctx &c, StageSmem<NS, WX, WY, HU> &sm, float *kout,
+// segment are computed.
+template <int NS, int CX, int WY, bool HU, int S>
+__device__ void tiles_run(const Ctx &c, StageSmem<NS, CX, WY, HU> &sm, float *kout,
                           const float *mn, float *mnew, const Coef &cf, Pipe &pp, int tslot,
                           int rslot, Acc &acc)
 {
-    using SM = StageSmem<NS, WX, WY, HU>;
+    using SM = StageSmem<NS, CX, WY, HU>;
     constexpr int D = SM::D, AHEAD = D + 1, PY = SM::PY;
     constexpr int PEND = 2 * D - 3;   // groups after tile(p+1): ops(p+1), then D-2 planes
     static_assert(D >= 2, "two planes in flight at least");
@@ -606,35 +776,21 @@ __device__ void tiles_run(const Ctx &c, StageSmem<NS, WX, WY, HU> &sm, float *ko
                                          : row_entry(c, pp.cr.y0 - 1 + i, pp.cr.z0 - 1 + (g - pp.cr.off));
         }
     };
-    float ucur[MAXN], unext[MAXN];
-#pragma unroll
-    for (int n = 0; n < MAXN; n++) ucur[n] = unext[n] = 1.f;
-    auto load_u = [&](int g, float *dst) {   // profiles of this thread's cell of plane g
-        if (!HU) return;
-        const int idx = sm.oidx[g % SM::OIX][i];
-#pragma unroll
-        for (int n = 0; n < MAXN; n++)
-            if (n < c.nmodes && idx >= 0) dst[n] = __ldg(c.u + (size_t)n * c.ncell + idx);
-    };
     // planes 0 and 1 (committed: 0 .. D-1; plane 0 is a halo plane: its operand slot is free)
     cp_async_wait<PEND>();
-    tile_combine<NS, WX, WY, HU, S>(sm, cf, 0, pp);
-    tile_combine<NS, WX, WY, HU, S>(sm, cf, 1, pp);
-    issue_tile<NS, WX, WY, HU, S>(c, sm, mn, pp.nq, pp);
-    issue_ops<NS, WX, WY, HU, S>(c, sm, mn, pp.nq, pp);
+    tile_combine<NS, CX, WY, HU, S>(sm, cf, 0, pp);
+    tile_combine<NS, CX, WY, HU, S>(sm, cf, 1, pp);
+    issue_tile<NS, CX, WY, HU, S>(c, sm, mn, pp.nq, pp);
+    issue_ops<NS, CX, WY, HU, S>(c, sm, mn, pp.nq, pp);
     pp.nq++;
-    load_u(1, unext);
     for (int p = 1; p <= gend - 2; p++) {
         load_rows(p + AHEAD);
         cp_async_wait<PEND>();
-        tile_combine<NS, WX, WY, HU, S>(sm, cf, p + 1, pp);
+        tile_combine<NS, CX, WY, HU, S>(sm, cf, p + 1, pp);
         __syncthreads();
-        issue_tile<NS, WX, WY, HU, S>(c, sm, mn, pp.nq, pp);
-#pragma unroll
-        for (int n = 0; n < MAXN; n++) ucur[n] = unext[n];
-        load_u(p + 1, unext);
-        compute_cell<NS, WX, WY, HU, S>(c, sm, kout, mnew, cf, p, ucur, tslot, rslot, pp, acc);
-        issue_ops<NS, WX, WY, HU, S>(c, sm, mn, pp.nq, pp);
+        issue_tile<NS, CX, WY, HU, S>(c, sm, mn, pp.nq, pp);
+        compute_cell<NS, CX, WY, HU, S>(c, sm, kout, mnew, cf, p, tslot, rslot, pp, acc);
+        issue_ops<NS, CX, WY, HU, S>(c, sm, mn, pp.nq, pp);
         pp.nq++;
     }
     cp_async_wait<0>();
@@ -642,15 +798,16 @@ __device__ void tiles_run(const Ctx &c, StageSmem<NS, WX, WY, HU> &sm, float *ko
 
 // Row-table entries of the first ROWC planes of the block's stream into the cache (once per
 // launch, after the block's segments are known).
-template <int NS, int WX, int WY, bool HU>
-__device__ void stage_cache_rows(const Ctx &c, StageSmem<NS, WX, WY, HU> &sm)
+template <int NS, int CX, int WY, bool HU>
+__device__ void stage_cache_rows(const Ctx &c, StageSmem<NS, CX, WY, HU> &sm)
 {
-    constexpr int PY = StageSmem<NS, WX, WY, HU>::PY;
+    using SM = StageSmem<NS, CX, WY, HU>;
+    constexpr int PY = SM::PY;
     if (sm.nseg == 0) return;
     int gend = 0;
     for (int t = 0; t < sm.nseg; t++) gend += sm.seg[t].w - sm.seg[t].z + 2;
     const int n = (gend < ROWC ? gend : ROWC) * PY;
-    for (int e = threadIdx.x; e < n; e += WX * WY) {
+    for (int e = threadIdx.x; e < n; e += SM::NT) {
         const int g = e / PY, r = e - g * PY;
         Cursor cu = cursor_start(sm);
         cursor_seek(sm, cu, g);
@@ -658,21 +815,28 @@ __device__ void stage_cache_rows(const Ctx &c, StageSmem<NS, WX, WY, HU> &sm)
     }
 }
 
-// Engine-facing names of the stage code of this window type (overloaded by smem type).
-template <int S, int NS, int WX, int WY, bool HU>
-__device__ __forceinline__ void stage_begin(const Ctx &c, StageSmem<NS, WX, WY, HU> &sm,
+// Engine-facing names of the stage code of this tile type (overloaded by smem type).
+template <int S, int NS, int CX, int WY, bool HU>
+__device__ __forceinline__ void stage_begin(const Ctx &c, StageSmem<NS, CX, WY, HU> &sm,
                                             const float *mn, Pipe &pp)
 {
-    tiles_begin<NS, WX, WY, HU, S>(c, sm, mn, pp);
+    tiles_begin<NS, CX, WY, HU, S>(c, sm, mn, pp);
 }
 
-template <int S, int NS, int WX, int WY, bool HU>
-__device__ __forceinline__ void stage_run(const Ctx &c, StageSmem<NS, WX, WY, HU> &sm,
+template <int S, int NS, int CX, int WY, bool HU>
+__device__ __forceinline__ void stage_run(const Ctx &c, StageSmem<NS, CX, WY, HU> &sm,
                                           float *kout, const float *mn, float *mnew,
                                           const Coef &cf, Pipe &pp, int tslot, int rslot,
                                           Acc &acc)
 {
-    tiles_run<NS, WX, WY, HU, S>(c, sm, kout, mn, mnew, cf, pp, tslot, rslot, acc);
+    tiles_run<NS, CX, WY, HU, S>(c, sm, kout, mn, mnew, cf, pp, tslot, rslot, acc);
+}
+
+// Magnetic cells a thread of this tile type computes per plane (the overlap sums' bound).
+template <int NS, int CX, int WY, bool HU>
+__host__ __device__ constexpr int cells_per_thread(const StageSmem<NS, CX, WY, HU> *)
+{
+    return CX / 32;
 }
 
 }  // namespace cmx

@@ -88,8 +88,9 @@ def test_rhs_mask_with_holes_and_many_runs_per_row(tiling):
     assert r["err_mm"] < 1e-7 and r["err_da"] < 1e-6, r
 
 
-def test_rhs_antiferromagnet_two_sublattices():
-    r = rhs_compare(ragged_problem(nsub=2, nmodes=2, seed=5), (32, 8, 4))
+@pytest.mark.parametrize("tiling", [(32, 8, 4), (32, 4, 2)])
+def test_rhs_antiferromagnet_two_sublattices(tiling):
+    r = rhs_compare(ragged_problem(nsub=2, nmodes=2, seed=5), tiling)
     assert r["err_m"] < 2e-6, r
     assert r["err_mm"] < 1e-7 and r["err_da"] < 1e-6, r
 
@@ -123,8 +124,9 @@ def test_replay_afm_complex_coupling_1000_steps():
     p = ragged_problem(nsub=2, nmodes=2, seed=13)
     m = W.tilted_state(2, p.nx, p.ny, p.nz, 1.0, 0.0, afm=True)
     p = p.replace(m0=m, a0=np.zeros(2, complex), u=None, T=1e-6)
-    dm, da, info = replay_compare(p, 1000, tiling=(32, 8, 4))
-    assert dm <= TOL_M and da <= TOL_A, (dm, da)
+    for tiling in ((32, 8, 4), (32, 4, 1)):
+        dm, da, info = replay_compare(p, 1000, tiling=tiling)
+        assert dm <= TOL_M and da <= TOL_A, (tiling, dm, da)
 
 
 # ---------------------------------------------------------------------------------------------
@@ -310,3 +312,47 @@ def test_autotune_restores_the_state_and_keeps_a_compiled_window():
     sim.run(p.T, max_attempts=5)
     assert sim.sync()["attempts"] == st0["attempts"] + 5
     sim.close()
+
+
+@pytest.mark.parametrize("case", ["ragged", "single_block", "afm"])
+def test_save_and_load_state_resume_bitwise(case):
+    """A run saved after some attempts and resumed in a fresh handle continues bitwise like the
+    uninterrupted run: state, cavity amplitudes, step sizes and the step log."""
+    if case == "ragged":
+        p = f32_state(ragged_problem(seed=17).replace(T=1e-6))
+    elif case == "afm":
+        p = f32_state(ragged_problem(nsub=2, seed=19).replace(T=1e-6))
+    else:
+        p = f32_state(W.single_sphere())
+    sim = sim_for(p, log_cap=400)
+    sim.run(p.T, max_attempts=120)
+    blob = sim.save_state()
+    sim.run(p.T, max_attempts=150)
+    ref = (sim.get_m(), sim.get_a(), sim.sync(), sim.get_log())
+    sim.close()
+    sim = sim_for(p, log_cap=400)
+    sim.load_state(blob)
+    sim.run(p.T, max_attempts=150)
+    got = (sim.get_m(), sim.get_a(), sim.sync(), sim.get_log())
+    sim.close()
+    assert np.array_equal(ref[0], got[0]) and np.array_equal(ref[1], got[1])
+    assert (ref[2]["t"], ref[2]["attempts"], ref[2]["accepted"]) == \
+        (got[2]["t"], got[2]["attempts"], got[2]["accepted"])
+    n = ref[3]["n"]
+    assert got[3]["n"] == n
+    assert np.array_equal(ref[3]["dt"][120:n], got[3]["dt"][120:n])
+
+
+def test_load_state_rejects_another_problem():
+    p = ragged_problem(seed=23)
+    sim = sim_for(p, log_cap=0)
+    blob = sim.save_state()
+    sim.close()
+    q = W.single_sphere()
+    other = sim_for(q, log_cap=0)
+    with pytest.raises(cmx.CmxError) as ei:
+        other.load_state(blob)
+    assert ei.value.code == cmx.EINVAL
+    with pytest.raises(cmx.CmxError):
+        other.load_state(blob[:10])
+    other.close()
