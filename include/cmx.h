@@ -46,7 +46,10 @@ typedef enum {
     CMX_ENAN = 4,        /* the error norm became NaN or Inf on the device */
     CMX_ESTEPFAIL = 5,   /* the step size fell below dt_min */
     CMX_ETIMEOUT = 6,    /* a device-side wait (grid barrier) exceeded its time limit */
-    CMX_ESCRATCH = 7     /* cmx_eval_rhs_noalloc: the problem does not fit the fixed scratch */
+    CMX_ESCRATCH = 7,    /* cmx_eval_rhs_noalloc: the problem does not fit the fixed scratch */
+    CMX_ECHECK = 8       /* bounds-checked build (libcmx_check.so) only: a device index check
+                            failed; the access was skipped and the run stopped (cmx_last_error
+                            names the site and the index) */
 } cmx_status;
 
 #define CMX_MAX_MODES 8
@@ -262,6 +265,10 @@ int cmx_get_tiling(const cmx_problem *h, int *bx, int *by, int *bz, int *blocks,
                    int *quad);
 
 const char *cmx_last_error(const cmx_problem *h);
+
+/* 1 for the bounds-checked build of this library (libcmx_check.so: every stage kernel checks
+ * its shared- and global-memory indices, CMX_ECHECK on a failed check), 0 for libcmx.so. */
+int cmx_checked_build(void);
 const char *cmx_status_string(int status);
 
 /* ------------------------------------------------------------------------------------------
@@ -337,8 +344,8 @@ int cmx_batch_create(const cmx_instance *inst, int n, const cmx_solver *solver,
                      const cmx_batch_config *cfg, void *stream, cmx_batch **out);
 int cmx_batch_destroy(cmx_batch *b);
 
-/* Batch autotuner: for every candidate launch shape (tile 32x8 or 32x16 (two sublattices:
- * 32x4), times team size automatic, 1, 2, 4, 8, 16), build a trial batch over every k-th
+/* Batch autotuner: for every candidate launch shape (tile 32x8 or 32x4, times team size
+ * automatic, 1, 2, 4, 8, 16), build a trial batch over every k-th
  * instance (k = ceil(n / sample)), time one launch of `attempts` attempts per instance with CUDA
  * events after a one-attempt warm-up launch, and destroy it.  cfg is read for use_graph and
  * blocks_per_sm and receives the fastest bx, by, team.  us (may be NULL, 12 entries) gets the

@@ -22,25 +22,31 @@ def headers():
                   glob.glob(os.path.join(HERE, "..", "include", "*.h")))
 
 
-def stale() -> bool:
-    if not os.path.exists(LIB):
+LIB_CHECK = os.path.join(HERE, "libcmx_check.so")
+
+
+def stale(lib: str = LIB) -> bool:
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return any(os.path.getmtime(f) > t for f in sources() + headers())
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    """Compile every .cu of csrc/ into one shared library (objects in parallel)."""
-    if not force and not stale():
-        return LIB
+def build(force: bool = False, verbose: bool = False, checked: bool = False) -> str:
+    """Compile every .cu of csrc/ into one shared library (objects in parallel).  checked: the
+    bounds-checked build (CMX_CHECK = 1) as libcmx_check.so."""
+    lib = LIB_CHECK if checked else LIB
+    if not force and not stale(lib):
+        return lib
     nvcc = os.environ.get("NVCC", "nvcc")
-    objdir = os.path.join(HERE, "_build")
+    objdir = os.path.join(HERE, "_build", "check") if checked else os.path.join(HERE, "_build")
     os.makedirs(objdir, exist_ok=True)
     procs, objs = [], []
     for src in sources():
         obj = os.path.join(objdir, os.path.basename(src) + ".o")
         objs.append(obj)
-        cmd = [nvcc] + ARCH + FLAGS[:-1] + ["-c", src, "-o", obj]
+        cmd = [nvcc] + ARCH + FLAGS[:-1] + (["-DCMX_CHECK=1"] if checked else []) + \
+            ["-c", src, "-o", obj]
         if verbose:
             cmd += ["-Xptxas", "-v"]
         procs.append((cmd, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))
@@ -52,12 +58,12 @@ def build(force: bool = False, verbose: bool = False) -> str:
         ok = ok and p.returncode == 0
     if not ok:
         raise RuntimeError("nvcc failed")
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib + f".tmp{os.getpid()}"
     subprocess.check_call([nvcc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart"])
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    build(force="--force" in sys.argv, verbose="-v" in sys.argv)
-    print(LIB)
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv,
+                checked="--checked" in sys.argv))

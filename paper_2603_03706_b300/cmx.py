@@ -16,7 +16,7 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libcmx.so")
 
-OK, EINVAL, ENOMEM, ECUDA, ENAN, ESTEPFAIL, ETIMEOUT, ESCRATCH = range(8)
+OK, EINVAL, ENOMEM, ECUDA, ENAN, ESTEPFAIL, ETIMEOUT, ESCRATCH, ECHECK = range(9)
 MAX_MODES = 8
 
 
@@ -118,6 +118,7 @@ SIGNATURES = {
     "cmx_plan_tiling": (C.c_int, [C.POINTER(Grid), C.c_void_p, C.c_int, C.c_int, C.c_int,
                                   C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]),
     "cmx_last_error": (C.c_char_p, [_P]),
+    "cmx_checked_build": (C.c_int, []),
     "cmx_status_string": (C.c_char_p, [C.c_int]),
     "cmx_batch_create": (C.c_int, [C.POINTER(Instance), C.c_int, C.POINTER(Solver),
                                    C.POINTER(BatchConfig), C.c_void_p, C.POINTER(C.c_void_p)]),
@@ -156,10 +157,11 @@ SIGNATURES = {
 
 
 def load(path: Optional[str] = None):
-    """Load libcmx.so (built in-tree by paper_2603_03706_b300.build)."""
+    """Load libcmx.so (built in-tree by paper_2603_03706_b300.build); the environment variable
+    CMX_LIBRARY selects another build of the same ABI (e.g. the bounds-checked libcmx_check.so)."""
     global _lib
     if _lib is None:
-        p = path or LIB_PATH
+        p = path or os.environ.get("CMX_LIBRARY") or LIB_PATH
         if not os.path.exists(p):
             raise ImportError(f"{p} not found: build it with `python -m paper_2603_03706_b300.build`"
                               " (the integrator has no CPU fallback)")

@@ -278,6 +278,9 @@ int cmx_host::device_status(cmx_problem *h, const Ctl &c)
     if (c.status == CMX_ENAN) return fail(h, CMX_ENAN, "error norm is NaN/Inf at t=%g", c.t);
     if (c.status == CMX_ESTEPFAIL)
         return fail(h, CMX_ESTEPFAIL, "step size below dt_min at t=%g", c.t);
+    if (c.status == CMX_ECHECK)
+        return fail(h, CMX_ECHECK, "device index check failed at site %d (index %lld)",
+                    c.timeout_where, c.check_value);
     return fail(h, c.status, "device status %d", c.status);
 }
 
@@ -377,11 +380,14 @@ const char *cmx_status_string(int s)
     case CMX_ESTEPFAIL: return "step size underflow";
     case CMX_ETIMEOUT: return "device wait timed out";
     case CMX_ESCRATCH: return "problem exceeds the fixed scratch of cmx_eval_rhs_noalloc";
+    case CMX_ECHECK: return "device index check failed (bounds-checked build)";
     default: return "unknown status";
     }
 }
 
 const char *cmx_last_error(const cmx_problem *h) { return h ? h->err.c_str() : "null handle"; }
+
+int cmx_checked_build(void) { return CMX_CHECK; }
 
 int cmx_create(const cmx_grid *grid, const uint8_t *mask, const cmx_material *mat,
                const cmx_modes *modes, const cmx_solver *solver, const cmx_tiling *tiling,

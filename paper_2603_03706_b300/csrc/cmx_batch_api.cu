@@ -593,7 +593,7 @@ int cmx_batch_autotune(const cmx_instance *inst, int n, const cmx_solver *solver
     std::vector<cmx_instance> sub;
     for (int i = 0; i < n; i += k) sub.push_back(inst[i]);
     const int nsub = inst[0].grid.nsub;
-    const int win[2][2] = {{32, 8}, {32, nsub == 1 ? 16 : 4}};
+    const int win[2][2] = {{32, 8}, {32, 4}};
     const int teams[6] = {0, 1, 2, 4, 8, 16};
     cmx_solver sv = *solver;
     sv.log_cap = 0;

@@ -694,8 +694,12 @@ __device__ bool integrate(const Ctx &c, const Team &tm, SM &sm, Local &L, Coef &
     if (threadIdx.x < c.nmodes) mode_constants(c, threadIdx.x, L.mc + MC * threadIdx.x);
     {
         const int sb = __ldg(&c.seg_begin[tm.rank]), se = __ldg(&c.seg_begin[tm.rank + 1]);
-        if (threadIdx.x == 0) sm.nseg = se - sb;
-        for (int t = threadIdx.x; t < se - sb; t += blockDim.x) sm.seg[t] = __ldg(&c.tiles[sb + t]);
+        const bool ok = idx_ok(c, se - sb, MAX_BLOCK_SEGMENTS + 1, 11) &&
+                        idx_ok(c, sb, (long long)c.ntiles + 1, 12) &&
+                        idx_ok(c, se, (long long)c.ntiles + 1, 13);
+        const int n = ok ? se - sb : 0;
+        if (threadIdx.x == 0) sm.nseg = n;
+        for (int t = threadIdx.x; t < n; t += blockDim.x) sm.seg[t] = __ldg(&c.tiles[sb + t]);
     }
     __syncthreads();
     stage_cache_rows(c, sm);

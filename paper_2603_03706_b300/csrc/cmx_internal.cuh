@@ -7,6 +7,12 @@
 
 #include "../../include/cmx.h"
 
+// CMX_CHECK = 1 builds the bounds-checked library: the stage kernels verify their shared- and
+// global-memory indices; a failed check skips the access and stops the run with CMX_ECHECK.
+#ifndef CMX_CHECK
+#define CMX_CHECK 0
+#endif
+
 namespace cmx {
 
 constexpr int MAXN = CMX_MAX_MODES;
@@ -107,7 +113,8 @@ struct Ctl {
     unsigned int remax[3];
     int range_error;                 // a block partial left the fixed-point range
     int skip_block;                  // test hook (see cmx_debug_skip_arrival)
-    int timeout_where;
+    int timeout_where;               // barrier or index-check site of the stopping error
+    long long check_value;           // bounds-checked build: the offending index
 };
 
 // Kernel arguments (by value).

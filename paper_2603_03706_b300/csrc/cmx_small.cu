@@ -134,7 +134,10 @@ __device__ void small_stage(const Ctx &c, int nm, const SmallBuf &b, Local &L, C
     for (int i = tid; i < nm; i += SMALL_NT) {
         int nbr[6];
 #pragma unroll
-        for (int d = 0; d < 6; d++) nbr[d] = b.nb[d * nm + i];
+        for (int d = 0; d < 6; d++) {
+            nbr[d] = b.nb[d * nm + i];
+            if (nbr[d] >= 0 && !idx_ok(c, nbr[d], nm, 14)) nbr[d] = -1;
+        }
         const float nx_ = (float)(nbr[0] >= 0) + (float)(nbr[1] >= 0);
         const float ny_ = (float)(nbr[2] >= 0) + (float)(nbr[3] >= 0);
         const float nz_ = (float)(nbr[4] >= 0) + (float)(nbr[5] >= 0);
@@ -244,6 +247,7 @@ __global__ void __launch_bounds__(SMALL_NT, 1) small_kernel(SmallArgs A)
         float *uu = b.kk + 7 * V;
         for (int i = tid; i < nm; i += SMALL_NT) {
             const int si = __ldg(A.sidx + i);
+            if (!idx_ok(c, si, c.ncell, 15)) continue;
 #pragma unroll
             for (int q = 0; q < NQ; q++) {
                 mn[q * nm + i] = gm[(size_t)q * c.ncell + si];
@@ -281,6 +285,7 @@ __global__ void __launch_bounds__(SMALL_NT, 1) small_kernel(SmallArgs A)
         float *gk1 = const_cast<float *>(slope_buffer(c, L.kphys[0]));
         for (int i = tid; i < nm; i += SMALL_NT) {
             const int si = __ldg(A.sidx + i);
+            if (!idx_ok(c, si, c.ncell, 16)) continue;
 #pragma unroll
             for (int q = 0; q < NQ; q++) {
                 gm[(size_t)q * c.ncell + si] = mn[q * nm + i];

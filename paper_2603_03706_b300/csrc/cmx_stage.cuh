@@ -52,6 +52,27 @@ __device__ __forceinline__ int ld_volatile_int(const int *p)
     return *(const volatile int *)p;
 }
 
+// Index check of the bounds-checked build (CMX_CHECK): true if 0 <= i < n; otherwise the run
+// stops with CMX_ECHECK, the site and the index are recorded, and the caller skips the access.
+// Always true in the plain build.
+__device__ __forceinline__ bool idx_ok(const Ctx &c, long long i, long long n, int site)
+{
+#if CMX_CHECK
+    if (i >= 0 && i < n) return true;
+    if (atomicCAS(&c.ctl->status, 0, (int)CMX_ECHECK) == 0) {
+        c.ctl->timeout_where = site;
+        c.ctl->check_value = i;
+    }
+    return false;
+#else
+    (void)c;
+    (void)i;
+    (void)n;
+    (void)site;
+    return true;
+#endif
+}
+
 // max that propagates NaN (a NaN error estimate must reach the controller)
 __device__ __forceinline__ float nanmax(float a, float b)
 {
@@ -144,6 +165,37 @@ __device__ __forceinline__ void cp_async4(void *smem, const void *gmem)
 {
     const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(s), "l"(gmem) : "memory");
+}
+
+// L2 eviction-priority policies: stored stage values are kept in L2 from the stage that writes
+// them to the next one that reads them (evict_last); the operands streamed once per stage from
+// DRAM are the first to leave (evict_first).
+__device__ __forceinline__ unsigned long long l2_keep()
+{
+    unsigned long long p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+
+__device__ __forceinline__ unsigned long long l2_stream()
+{
+    unsigned long long p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+
+__device__ __forceinline__ void cp_async4_hint(void *smem, const void *gmem, unsigned long long pol)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global.L2::cache_hint [%0], [%1], 4, %2;" ::"r"(s), "l"(gmem),
+                 "l"(pol)
+                 : "memory");
+}
+
+__device__ __forceinline__ void st_hint(float *gmem, float v, unsigned long long pol)
+{
+    asm volatile("st.global.L2::cache_hint.f32 [%0], %1, %2;" ::"l"(gmem), "f"(v), "l"(pol)
+                 : "memory");
 }
 
 __device__ __forceinline__ void cp_async_commit()
@@ -338,6 +390,8 @@ __device__ __forceinline__ void load_positions(const Ctx &c, SM &sm, const float
                                                float *side, int e, int idx, const float (&pres)[U])
 {
     constexpr int NQ = SM::NQ, P = SM::P;
+    if (!idx_ok(c, e, P - U + 1, 1) || !idx_ok(c, rs, SM::RING, 2)) return;
+    if (idx >= 0 && !idx_ok(c, idx, (long long)c.ncell - U + 1, 3)) idx = -1;
     if (idx >= 0) {
 #pragma unroll
         for (int k = 0; k < NQ; k++) {
@@ -407,15 +461,16 @@ __device__ __forceinline__ void issue_ops(const Ctx &c, StageSmem<NS, CX, WY, HU
     const int i = threadIdx.x;
     if (g < pp.gend) {
         const int oi = sm.oidx[g % SM::OIX][i];
-        if (oi >= 0) {
+        if (oi >= 0 && idx_ok(c, oi, (long long)c.ncell - CPT + 1, 4)) {
             float *slot = sm.pool + (size_t)(g % SM::D) * SM::OPSLOT;
+            const unsigned long long pol = l2_stream();
 #pragma unroll
             for (int a = 0; a < NO; a++) {
                 const float *src = op_source<SM, S>(c, sm, mn, a);
 #pragma unroll
                 for (int k = 0; k < NQ; k++)
-                    cp_async_unit<CPT>(slot + (a * NQ + k) * CW + CPT * i,
-                                       src + (size_t)k * c.ncell + oi);
+                    cp_async4_hint(slot + (a * NQ + k) * CW + CPT * i,
+                                   src + (size_t)k * c.ncell + oi, pol);
             }
             if (HU) {
                 float *us = sm.upool + (size_t)(g % SM::D) * SM::USLOT;
@@ -432,8 +487,8 @@ __device__ __forceinline__ void issue_ops(const Ctx &c, StageSmem<NS, CX, WY, HU
 // Stage 2: the tile values m_2 = m_n + h a_21 k_1 of the thread's positions of plane g (the
 // copies of plane g are complete; only this thread wrote these positions).
 template <int NS, int CX, int WY, bool HU, int S>
-__device__ __forceinline__ void tile_combine(StageSmem<NS, CX, WY, HU> &sm, const Coef &cf, int g,
-                                             const Pipe &pp)
+__device__ __forceinline__ void tile_combine(const Ctx &c, StageSmem<NS, CX, WY, HU> &sm,
+                                             const Coef &cf, int g, const Pipe &pp)
 {
     using SM = StageSmem<NS, CX, WY, HU>;
     constexpr int NQ = SM::NQ, P = SM::P, CPT = SM::CPT;
@@ -442,6 +497,7 @@ __device__ __forceinline__ void tile_combine(StageSmem<NS, CX, WY, HU> &sm, cons
     const float *side = sm.pool + (size_t)(g % SM::D) * SM::OPSLOT + n_ops(2) * NQ * SM::CW;
     const float c21 = cf.cf[1][0];
     const int nr = pp.rk == 1 ? CPT : (pp.rk == 2 ? 1 : 0);
+    if (!idx_ok(c, pp.eo, P - CPT + 1, 9) || (nr && !idx_ok(c, pp.er, P - nr + 1, 10))) return;
 #pragma unroll
     for (int k = 0; k < NQ; k++) {
 #pragma unroll
@@ -522,12 +578,16 @@ __device__ __forceinline__ void compute_cell(const Ctx &c, StageSmem<NS, CX, WY,
 {
     using SM = StageSmem<NS, CX, WY, HU>;
     constexpr int NQ = SM::NQ, R = SM::RING, PXS = SM::PXS, CW = SM::CW, CPT = SM::CPT;
-    constexpr int NO = n_ops(S);
+    constexpr int NO = n_ops(S), P = SM::P;
     const int i = threadIdx.x;
     const int idx = sm.oidx[p % SM::OIX][i];
     if (idx < 0) return;
     const int sp = (p + R - 1) % R, sc = p % R, sn = (p + 1) % R;
     const int e = pp.eo;
+    if (!idx_ok(c, idx, (long long)c.ncell - CPT + 1, 5) || !idx_ok(c, e - PXS, P - 2 * PXS - CPT + 1, 6))
+        return;
+    if (S >= 2 && rslot >= 0 && !idx_ok(c, rslot, c.rec_steps, 7)) return;
+    if ((S == 1 || S == 7) && tslot >= 0 && !idx_ok(c, tslot, c.traj_slots, 8)) return;
     const float *op = sm.pool + (size_t)(p % SM::D) * SM::OPSLOT;
     const int oc = CPT * i;   // the unit's first cell in the operand slot
     const float *pr = sm.v[sc][NQ];
@@ -669,8 +729,9 @@ __device__ __forceinline__ void compute_cell(const Ctx &c, StageSmem<NS, CX, WY,
                     a[u] = here[u] != 0.f ? fmaf(cf.cf[S][S - 1], kv[u][s][k], a[u]) : 0.f;
                     es[u] = here[u] != 0.f ? fmaf(cf.e[5], kv[u][s][k], es[u]) : 0.f;
                 }
-                put(c.msv[(S + 1) & 1], q, a);
-                if (S == 6) put(c.es, q, es);
+                const unsigned long long keep = l2_keep();
+                st_hint(c.msv[(S + 1) & 1] + (size_t)q * c.ncell + idx, a[0], keep);
+                if (S == 6) st_hint(c.es + (size_t)q * c.ncell + idx, es[0], keep);
             }
     }
     if (S == 7) {
@@ -778,15 +839,15 @@ __device__ void tiles_run(const Ctx &c, StageSmem<NS, CX, WY, HU> &sm, float *ko
     };
     // planes 0 and 1 (committed: 0 .. D-1; plane 0 is a halo plane: its operand slot is free)
     cp_async_wait<PEND>();
-    tile_combine<NS, CX, WY, HU, S>(sm, cf, 0, pp);
-    tile_combine<NS, CX, WY, HU, S>(sm, cf, 1, pp);
+    tile_combine<NS, CX, WY, HU, S>(c, sm, cf, 0, pp);
+    tile_combine<NS, CX, WY, HU, S>(c, sm, cf, 1, pp);
     issue_tile<NS, CX, WY, HU, S>(c, sm, mn, pp.nq, pp);
     issue_ops<NS, CX, WY, HU, S>(c, sm, mn, pp.nq, pp);
     pp.nq++;
     for (int p = 1; p <= gend - 2; p++) {
         load_rows(p + AHEAD);
         cp_async_wait<PEND>();
-        tile_combine<NS, CX, WY, HU, S>(sm, cf, p + 1, pp);
+        tile_combine<NS, CX, WY, HU, S>(c, sm, cf, p + 1, pp);
         __syncthreads();
         issue_tile<NS, CX, WY, HU, S>(c, sm, mn, pp.nq, pp);
         compute_cell<NS, CX, WY, HU, S>(c, sm, kout, mnew, cf, p, tslot, rslot, pp, acc);

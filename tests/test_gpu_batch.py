@@ -162,7 +162,7 @@ def test_batch_rejects_profiles():
 def test_batch_autotune_picks_a_runnable_shape():
     probs = small_batch(n_inst=9, seed=8)
     t = cmx.batch_autotune(probs, sample=5, attempts=4)
-    assert (t["bx"], t["by"]) in ((32, 8), (32, 16)) and t["team"] >= 1, t
+    assert (t["bx"], t["by"]) in ((32, 8), (32, 4)) and t["team"] >= 1, t
     assert len(t["us"]) == 12 and np.nanmin(t["us"]) > 0
     b = cmx.BatchSimulation(probs, log_cap=100, bx=t["bx"], by=t["by"], team=t["team"])
     st = b.run(max_attempts=50)
