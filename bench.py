@@ -86,9 +86,11 @@ def bytes_per_cell_attempt(p):
 
 # Sources that define the single-problem integrator launch (kernel, engine, stage code, the
 # host code that lays out the cells and partitions the blocks).
-KERNEL_SOURCES = ("cmx_internal.cuh", "cmx_stage.cuh", "cmx_engine.cuh",
-                  "cmx_single.cu", "cmx_kernels.h", "cmx_api.cu", "cmx_layout.cu",
-                  "cmx_layout.h", "cmx_problem.h")
+KERNEL_SOURCES = ("cmx_internal.cuh", "cmx_stage.cuh", "cmx_engine.cuh", "cmx_demag.cuh",
+                  "cmx_single_kernel.cuh", "cmx_single_t1x4.cu", "cmx_single_t1x8.cu",
+                  "cmx_single_t1x16.cu", "cmx_single_t2x4.cu", "cmx_single_t2x8.cu",
+                  "cmx_single_t2x16.cu", "cmx_single.cu", "cmx_kernels.h", "cmx_layout.cu",
+                  "cmx_layout.h")
 
 
 def kernel_source_hash():
@@ -467,6 +469,49 @@ def single_sphere_record(stream):
                       "cmx_run from t = 0 to T, synchronised"}
 
 
+def demag_record(stream):
+    """Full magnetostatic demag (FFT convolution with the Newell tensor) against the diagonal
+    factors on a 64 x 64 x 8 film (non-ellipsoidal: the diagonal factors are only approximate):
+    device time per attempt both ways on the 32 x 8 tiles, the demag passes' share, and the bytes
+    the five FFT passes move per stage (complex FP32 work array of nz planes of Ly x Lx, three
+    components, read and written once per pass; the tensor spectrum read once)."""
+    import torch
+    from paper_2603_03706_b300 import cmx
+    from paper_2603_03706_b300 import workloads as W
+    nx, ny, nz = 64, 64, 8
+    p = W.make_problem(nx, ny, nz, 3e-9, W.full_mask(nx, ny, nz), Ms=1.4e5, B0=(0.0, 0.0, 0.3),
+                       Nd=(0.0, 0.0, 1.0), omega=[2 * 3.141592653589793 * 5e9],
+                       kappa=[2 * 3.141592653589793 * 2e6], g_re=[2 * 3.141592653589793 * 50e6],
+                       g_im=[0.0], m0=W.tilted_state(1, nx, ny, nz, 2.0, 0.0), T=1.0)
+    p = p.replace(dt_max=W.stable_dt_max(p))
+    out = {"workload": "film_64x64x8 (full mask, 3 nm cells)", "cells": p.ncells}
+    for full in (False, True):
+        sim = cmx.Simulation.from_problem(p, stream=stream, tiling=(32, 8, 4))
+        sim.set_demag(full)
+        sim.run(1.0, max_attempts=5)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sim.launch(1.0, 200)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        st = sim.sync()
+        sim.close()
+        out["us_per_attempt_" + ("full" if full else "diagonal")] = e0.elapsed_time(e1) * 1e3 / 200
+    Lx, Ly, Lz = 128, 128, 16
+    c8 = 3 * 8                                   # three complex FP32 components
+    half, full = nz * ny * Lx * c8, nz * Ly * Lx * c8
+    out["fft_grid"] = [Lx, Ly, Lz]
+    # pass 1: stage values in, x lines out; 2: x lines in, y lines out; 3: y lines in and out
+    # plus the six real tensor spectra; 4: y lines in, x lines out; 5: x lines in, field out
+    out["demag_bytes_per_stage"] = ((p.ncells * 12 + half) + (half + full) +
+                                    (2 * full + 6 * Lx * Ly * Lz * 4) + (full + half) +
+                                    (half + p.ncells * 12))
+    out["demag_share"] = 1.0 - out["us_per_attempt_diagonal"] / out["us_per_attempt_full"]
+    out["timing"] = "CUDA events over one 200-attempt launch each, same tiles"
+    return out
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -546,6 +591,7 @@ def main():
                 subs.append(r)
             line["workloads"] = subs
             line["single_sphere"] = single_sphere_record(stream)
+            line["demag"] = demag_record(stream)
         if not args.no_adjoint:
             line["adjoint"] = adjoint_ratio(args.adjoint_T, args.adjoint_every, stream)
         if not args.no_batch:
