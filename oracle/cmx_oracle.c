@@ -21,6 +21,10 @@
  *                    (Sec. IV A), evaluated at each stage's time t + c_s h.
  *   extensions       optional backward coupling gb~_n of the feedback field (nonreciprocal
  *                    coupling, Sec. II: h0 = 2 g_b / gamma) and self-Kerr -i K_n |a_n|^2 a_n.
+ *   parametric pump  optional -i P_n exp(-i wp_n t) conj(a_n) added to da_n/dt at each stage's
+ *                    time (Sec. V names parametric drives as a cavity-model swap without a
+ *                    formula: this is the classical equation of the degenerate two-photon pump
+ *                    H/hbar = (P e^{-i wp t} a^dag^2 + conj) / 2).
  *   adjoint          orc_rhs_vjp / orc_adjoint: reverse-mode derivative of the replayed steps
  *                    (not in the paper; the gradient form added beside the integrator).
  *
@@ -68,6 +72,9 @@ typedef struct {
     /* 1: the cavity amplitudes are held fixed (da/dt = 0, no drive): the magnet-only
        sub-integration of the operator-split scheme (orc_run_split) */
     int cavity_frozen;
+    /* degenerate parametric pump -i P_n e^{-i wp_n t} conj(a_n) on da_n/dt, P_n = pump_re + i
+       pump_im [rad/s], pump frequency pump_w [rad/s]; pump_re == NULL: none */
+    const double *pump_re, *pump_im, *pump_w;
     /* full magnetostatic demag (NEXT-3 of the scope; Sec. II C-D, Eq. (9), (11)): the cell-pair
        demag tensor of every displacement (orc_demag_tensor); NULL: the diagonal factors Nd */
     const double *demag;
@@ -483,6 +490,28 @@ static void add_drive(const orc_problem *P, double t, double *da)
     }
 }
 
+/* Pump coefficient Q_n(t) = P_n e^{-i wp_n t} of the parametric term. */
+static void pump_coefficient(const orc_problem *P, int n, double t, double *qr, double *qi)
+{
+    const double c = cos(P->pump_w[n] * t), s = sin(P->pump_w[n] * t);
+    *qr = P->pump_re[n] * c + P->pump_im[n] * s;
+    *qi = P->pump_im[n] * c - P->pump_re[n] * s;
+}
+
+/* The parametric term at time t, -i Q_n(t) conj(a_n), added to the cavity slopes da:
+   -i (qr + i qi)(ar - i ai) = (qi ar - qr ai) - i (qr ar + qi ai). */
+static void add_pump(const orc_problem *P, double t, const double *a, double *da)
+{
+    if (!P->pump_re || P->cavity_frozen) return;
+    for (int n = 0; n < P->nmodes; n++) {
+        double qr, qi;
+        pump_coefficient(P, n, t, &qr, &qi);
+        const double ar = a[2 * n], ai = a[2 * n + 1];
+        da[2 * n] += qi * ar - qr * ai;
+        da[2 * n + 1] -= qr * ar + qi * ai;
+    }
+}
+
 /* Node c_s of stage s (0-based) of the tableau: the row sum of its couplings. */
 static double dp_node(int s)
 {
@@ -505,6 +534,7 @@ static int dp_attempt(const orc_problem *P, orc_state *S, const orc_solver *sv, 
         int rc = orc_rhs(P, S->m, S->a, S->km[0], S->ka[0], mm);
         if (rc) return rc;
         add_drive(P, S->t, S->ka[0]);
+        add_pump(P, S->t, S->a, S->ka[0]);
         S->k1_valid = 1;
     }
     for (int s = 1; s < 7; s++) {
@@ -522,6 +552,7 @@ static int dp_attempt(const orc_problem *P, orc_state *S, const orc_solver *sv, 
         int rc = orc_rhs(P, S->ym, S->ya, S->km[s], S->ka[s], mm);
         if (rc) return rc;
         add_drive(P, S->t + dp_node(s) * h, S->ka[s]);
+        add_pump(P, S->t + dp_node(s) * h, S->ya, S->ka[s]);
     }
     memcpy(S->mm7, mm, 2 * N * sizeof(double));
 
@@ -680,7 +711,32 @@ typedef struct {
     double *u;                           /* nmodes * nbox (only with profiles) */
     double *gb_re, *gb_im;               /* nmodes each, with nonreciprocal coupling */
     double *kerr;                        /* nmodes, with a Kerr term */
+    double *pump_re, *pump_im;           /* nmodes each, with a parametric pump: dL/d Re P_n, ... */
 } orc_grads;
+
+/*
+ * Transpose of the parametric term at time t (see add_pump): the slope (qi ar - qr ai,
+ * -qr ar - qi ai) has the symmetric Jacobian [[qi, -qr], [-qr, -qi]] in (ar, ai), so ga gets
+ * (qi wr - qr wi, -qr wr - qi wi); with d(qr, qi)/d(Pr) = (c, -s) and d(qr, qi)/d(Pi) = (s, c),
+ * c = cos(wp t), s = sin(wp t), the pump gradients follow from dL/dqr = -ai wr - ar wi and
+ * dL/dqi = ar wr - ai wi.
+ */
+static void pump_vjp(const orc_problem *P, double t, const double *a, const double *wa,
+                     double *ga, orc_grads *G)
+{
+    if (!P->pump_re || P->cavity_frozen) return;
+    for (int n = 0; n < P->nmodes; n++) {
+        double qr, qi;
+        pump_coefficient(P, n, t, &qr, &qi);
+        const double ar = a[2 * n], ai = a[2 * n + 1], wr = wa[2 * n], wi = wa[2 * n + 1];
+        ga[2 * n] += qi * wr - qr * wi;
+        ga[2 * n + 1] += -qr * wr - qi * wi;
+        const double lqr = -ai * wr - ar * wi, lqi = ar * wr - ai * wi;
+        const double c = cos(P->pump_w[n] * t), sn = sin(P->pump_w[n] * t);
+        if (G && G->pump_re) G->pump_re[n] += lqr * c - lqi * sn;
+        if (G && G->pump_im) G->pump_im[n] += lqr * sn + lqi * c;
+    }
+}
 
 /*
  * Vector-Jacobian product of orc_rhs at (m, a).  Given adjoint weights wm (layout of m) on the
@@ -972,6 +1028,7 @@ int orc_adjoint(const orc_problem *P, const orc_solver *sv, const double *m0, co
         for (int q = 0; q < 2 * N; q++) Fa[6][q] = la[q];
         rc = orc_rhs_vjp(P, Ym[6], Ya[6], lkm, lka, Fm[6], Fa[6], G);
         if (rc) goto done;
+        pump_vjp(P, Tst[i] + dp_node(6) * h, Ya[6], lka, Fa[6], G);
         for (int s = 5; s >= 1; s--) {
             for (long v = 0; v < nv; v++) {
                 double acc = 0.0;
@@ -985,6 +1042,7 @@ int orc_adjoint(const orc_problem *P, const orc_solver *sv, const double *m0, co
             }
             rc = orc_rhs_vjp(P, Ym[s], Ya[s], wkm, wka, Fm[s], Fa[s], G);
             if (rc) goto done;
+            pump_vjp(P, Tst[i] + dp_node(s) * h, Ya[s], wka, Fa[s], G);
         }
         for (long v = 0; v < nv; v++) {
             double sy = 0.0, sk = 0.0;
@@ -1011,6 +1069,7 @@ int orc_adjoint(const orc_problem *P, const orc_solver *sv, const double *m0, co
     if (n > 0) {
         rc = orc_rhs_vjp(P, m0, a0, lkm, lka, lm, la, G);
         if (rc) goto done;
+        pump_vjp(P, Tst[0], a0, lka, la, G);
     }
     if (gm0) memcpy(gm0, lm, nv * sizeof(double));
     if (ga0) memcpy(ga0, la, 2 * N * sizeof(double));
@@ -1067,6 +1126,7 @@ static void split_cavity_slope(const orc_problem *P, const double *a, const doub
             da[2 * n + 1] += P->drive_im[n] * env;
         }
     }
+    add_pump(P, t, a, da);
 }
 
 /*

@@ -57,6 +57,8 @@ class _Problem(C.Structure):
                 ("drive_t0", C.c_double), ("drive_sigma", C.c_double),
                 ("gb_re", C.POINTER(C.c_double)), ("gb_im", C.POINTER(C.c_double)),
                 ("kerr", C.POINTER(C.c_double)), ("cavity_frozen", C.c_int),
+                ("pump_re", C.POINTER(C.c_double)), ("pump_im", C.POINTER(C.c_double)),
+                ("pump_w", C.POINTER(C.c_double)),
                 ("demag", C.POINTER(C.c_double))]
 
 
@@ -77,7 +79,8 @@ class _Grads(C.Structure):
                 ("kappa", C.POINTER(C.c_double)), ("omega", C.POINTER(C.c_double)),
                 ("alpha", C.POINTER(C.c_double)), ("u", C.POINTER(C.c_double)),
                 ("gb_re", C.POINTER(C.c_double)), ("gb_im", C.POINTER(C.c_double)),
-                ("kerr", C.POINTER(C.c_double))]
+                ("kerr", C.POINTER(C.c_double)), ("pump_re", C.POINTER(C.c_double)),
+                ("pump_im", C.POINTER(C.c_double))]
 
 
 _lib = None
@@ -173,6 +176,16 @@ class OracleProblem:
             s.kerr = _dptr(self.kerr)
         else:
             s.kerr = C.POINTER(C.c_double)()
+        pump = getattr(p, "pump", None)
+        if pump is not None:
+            P = np.asarray(pump, complex).reshape(-1)
+            self.pump_re = np.ascontiguousarray(P.real, np.float64)
+            self.pump_im = np.ascontiguousarray(P.imag, np.float64)
+            self.pump_w = np.ascontiguousarray(np.asarray(p.pump_omega, np.float64).reshape(-1))
+            s.pump_re, s.pump_im = _dptr(self.pump_re), _dptr(self.pump_im)
+            s.pump_w = _dptr(self.pump_w)
+        else:
+            s.pump_re = s.pump_im = s.pump_w = C.POINTER(C.c_double)()
         if getattr(p, "full_demag", False):
             self.demag = demag_tensor(p.nx, p.ny, p.nz, p.cx, p.cy, p.cz)
             s.demag = _dptr(self.demag)
@@ -396,6 +409,8 @@ class Grads:
         self.gb_re, self.gb_im, self.kerr = np.zeros(N), np.zeros(N), np.zeros(N)
         s.gb_re, s.gb_im = _dptr(self.gb_re), _dptr(self.gb_im)
         s.kerr = _dptr(self.kerr)
+        self.pump_re, self.pump_im = np.zeros(N), np.zeros(N)
+        s.pump_re, s.pump_im = _dptr(self.pump_re), _dptr(self.pump_im)
         self.s = s
         self.N = op.N
 
@@ -407,6 +422,7 @@ class Grads:
         d["u"] = None if self.u is None else self.u[:N].copy()
         d["gb_re"], d["gb_im"] = self.gb_re[:N].copy(), self.gb_im[:N].copy()
         d["kerr"] = self.kerr[:N].copy()
+        d["pump_re"], d["pump_im"] = self.pump_re[:N].copy(), self.pump_im[:N].copy()
         return d
 
 

@@ -76,6 +76,10 @@ class Problem:
     # None = reciprocal (the forward g~); self-Kerr coefficients K_n [rad/s per |a|^2] or None
     g_back: Optional[np.ndarray] = None
     kerr: Optional[np.ndarray] = None
+    # degenerate parametric pump -i P_n e^{-i wp_n t} conj(a_n) on da_n/dt: complex P_n [rad/s]
+    # and the pump frequencies wp_n [rad/s]; None = no pump
+    pump: Optional[np.ndarray] = None
+    pump_omega: Optional[np.ndarray] = None
     # full magnetostatic demag (cell-pair tensor convolution) instead of the diagonal factors
     full_demag: bool = False
 
