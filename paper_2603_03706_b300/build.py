@@ -42,9 +42,14 @@ def build(force: bool = False, verbose: bool = False, checked: bool = False) -> 
     objdir = os.path.join(HERE, "_build", "check") if checked else os.path.join(HERE, "_build")
     os.makedirs(objdir, exist_ok=True)
     procs, objs = [], []
+    hdr_t = max((os.path.getmtime(f) for f in headers()), default=0.0)
     for src in sources():
         obj = os.path.join(objdir, os.path.basename(src) + ".o")
         objs.append(obj)
+        # an object newer than its source and every header is reused
+        if not force and os.path.exists(obj) and \
+                os.path.getmtime(obj) > max(os.path.getmtime(src), hdr_t):
+            continue
         cmd = [nvcc] + ARCH + FLAGS[:-1] + (["-DCMX_CHECK=1"] if checked else []) + \
             ["-c", src, "-o", obj]
         if verbose:

@@ -163,15 +163,21 @@ extern "C" int cmx_set_demag(cmx_problem *h, int mode)
         for (int k = -(nz - 1); k < nz; k++)
             for (int j = -(ny - 1); j < ny; j++)
                 for (int i = -(nx - 1); i < nx; i++) {
-                    const double X = i * cx, Y = j * cy, Z = k * cz;
+                    // evaluated at |displacement| with the component's parity applied, so
+                    // that entries of opposite displacements are exactly equal or opposite
+                    // and the spectrum is real up to the transform's rounding (the far entries
+                    // carry the cancellation error of the second differences, which differs
+                    // with the summation order)
+                    const double X = std::abs(i) * cx, Y = std::abs(j) * cy, Z = std::abs(k) * cz;
+                    const int si = (i > 0) - (i < 0), sj = (j > 0) - (j < 0), sk = (k > 0) - (k < 0);
                     double v = 0.0;
                     switch (comp) {
-                    case 0: v = nw_tensor(false, X, Y, Z, cx, cy, cz); break;   // xx
-                    case 1: v = nw_tensor(false, Y, X, Z, cy, cx, cz); break;   // yy
-                    case 2: v = nw_tensor(false, Z, Y, X, cz, cy, cx); break;   // zz
-                    case 3: v = nw_tensor(true, X, Y, Z, cx, cy, cz); break;    // xy
-                    case 4: v = nw_tensor(true, X, Z, Y, cx, cz, cy); break;    // xz
-                    default: v = nw_tensor(true, Y, Z, X, cy, cz, cx); break;   // yz
+                    case 0: v = nw_tensor(false, X, Y, Z, cx, cy, cz); break;             // xx
+                    case 1: v = nw_tensor(false, Y, X, Z, cy, cx, cz); break;             // yy
+                    case 2: v = nw_tensor(false, Z, Y, X, cz, cy, cx); break;             // zz
+                    case 3: v = si * sj * nw_tensor(true, X, Y, Z, cx, cy, cz); break;    // xy
+                    case 4: v = si * sk * nw_tensor(true, X, Z, Y, cx, cz, cy); break;    // xz
+                    default: v = sj * sk * nw_tensor(true, Y, Z, X, cy, cz, cx); break;   // yz
                     }
                     const size_t o = (((size_t)((k + Lz) % Lz)) * Ly + (size_t)((j + Ly) % Ly)) * Lx +
                                      (size_t)((i + Lx) % Lx);
