@@ -215,6 +215,16 @@ int cmx_set_backward_coupling(cmx_problem *h, const double *gb_re, const double 
 /* Self-Kerr cavity term -i K_n |a_n|^2 a_n [rad/s per |a|^2] (host, n_modes; NULL: none). */
 int cmx_set_kerr(cmx_problem *h, const double *kerr);
 
+/* Degenerate parametric pump (Sec. V lists parametric drives as a cavity-model swap without a
+ * formula; this is the classical equation of a two-photon pump): da_n/dt gains
+ * -i P_n e^{-i wp_n t} conj(a_n), P_n = p_re[n] + i p_im[n] [rad/s], pump frequency wp[n]
+ * [rad/s], phase referenced to t = 0, evaluated at each stage's time t + c_s h.  Host arrays of
+ * n_modes; p_re == NULL removes the pump.  Above threshold (|P|^2 > kappa^2 + (wp/2 - w)^2)
+ * the cavity grows exponentially, as the equation says.  The operator-split scheme takes it in
+ * its cavity step; the adjoint returns dL/d Re P_n and dL/d Im P_n (cmx_grads.pump_re/pump_im).
+ * CMX_EINVAL for a non-finite coefficient. */
+int cmx_set_pump(cmx_problem *h, const double *p_re, const double *p_im, const double *wp);
+
 /* Autotuner: time `attempts` Dormand-Prince attempts (after a one-attempt warm-up) from the
  * current state with each compiled tile (32x4, 32x8, 32x16; blocks_per_sm and bz of the
  * current tiling) and, for a grid small enough, with the single-block integrator, restore the
@@ -426,6 +436,7 @@ typedef struct {
     double *gb_re, *gb_im; /* host, n_modes each: dL/d of the backward coupling (zero unless set
                               by cmx_set_backward_coupling; otherwise in g_re, g_im) */
     double *kerr;          /* host, n_modes: dL/d K_n */
+    double *pump_re, *pump_im; /* host, n_modes each: dL/d Re P_n, dL/d Im P_n of the pump */
 } cmx_grads;
 
 /* Arm the checkpoint store for the next run: call after cmx_set_state and before any launch.

@@ -78,7 +78,7 @@ class Grads(C.Structure):
                 ("omega", C.c_void_p), ("alpha", C.c_void_p), ("a0", C.c_void_p),
                 ("m0", C.c_void_p), ("m0_on_device", C.c_int), ("u", C.c_void_p),
                 ("u_on_device", C.c_int), ("gb_re", C.c_void_p), ("gb_im", C.c_void_p),
-                ("kerr", C.c_void_p)]
+                ("kerr", C.c_void_p), ("pump_re", C.c_void_p), ("pump_im", C.c_void_p)]
 
 
 class Step(C.Structure):
@@ -139,6 +139,7 @@ SIGNATURES = {
     "cmx_set_split": (C.c_int, [_P, C.c_double]),
     "cmx_set_backward_coupling": (C.c_int, [_P, C.c_void_p, C.c_void_p]),
     "cmx_set_kerr": (C.c_int, [_P, C.c_void_p]),
+    "cmx_set_pump": (C.c_int, [_P, C.c_void_p, C.c_void_p, C.c_void_p]),
     "cmx_set_drive": (C.c_int, [_P, C.c_void_p, C.c_void_p, C.c_double, C.c_double]),
     "cmx_batch_spectrum": (C.c_int, [_P, C.c_int, C.c_double, C.c_double, C.c_int, C.c_double,
                                      C.c_void_p]),
@@ -269,6 +270,8 @@ class Simulation:
             sim.set_backward_coupling(p.g_back)
         if getattr(p, "kerr", None) is not None:
             sim.set_kerr(p.kerr)
+        if getattr(p, "pump", None) is not None:
+            sim.set_pump(p.pump, p.pump_omega)
         if getattr(p, "full_demag", False):
             sim.set_demag(True)
         return sim
@@ -454,7 +457,8 @@ class Simulation:
         if lm is not None and lm.size != 3 * self.nsub * self.nbox:
             raise ValueError("dL_dm size")
         out = {k: np.zeros(max(N, 1))
-               for k in ("g_re", "g_im", "kappa", "omega", "gb_re", "gb_im", "kerr")}
+               for k in ("g_re", "g_im", "kappa", "omega", "gb_re", "gb_im", "kerr", "pump_re",
+                         "pump_im")}
         alpha = np.zeros(1)
         a0 = np.zeros(max(2 * N, 1))
         m0 = np.zeros(3 * self.nsub * self.nbox, np.float32) if want_m0 else None
@@ -463,7 +467,8 @@ class Simulation:
                   out["omega"].ctypes.data, alpha.ctypes.data, a0.ctypes.data,
                   m0.ctypes.data if m0 is not None else None, 0,
                   u.ctypes.data if u is not None else None, 0, out["gb_re"].ctypes.data,
-                  out["gb_im"].ctypes.data, out["kerr"].ctypes.data)
+                  out["gb_im"].ctypes.data, out["kerr"].ctypes.data,
+                  out["pump_re"].ctypes.data, out["pump_im"].ctypes.data)
         self._check(load().cmx_adjoint(self.h, la.ctypes.data if la is not None else None,
                                        lm.ctypes.data if lm is not None else None, 0,
                                        C.byref(g)), "adjoint")
@@ -536,6 +541,20 @@ class Simulation:
         if k.size != self.N:
             raise ValueError("one Kerr coefficient per mode")
         self._check(load().cmx_set_kerr(self.h, k.ctypes.data), "set_kerr")
+
+    def set_pump(self, pump=None, omega_p=None):
+        """cmx_set_pump: degenerate parametric pump -i P_n e^{-i wp_n t} conj(a_n) on da_n/dt
+        (pump: N complex P_n [rad/s], omega_p: N pump frequencies [rad/s]; None: no pump)."""
+        if pump is None:
+            self._check(load().cmx_set_pump(self.h, None, None, None), "set_pump")
+            return
+        P = np.asarray(pump, complex).reshape(-1)
+        wp = _f64(omega_p)
+        if P.size != self.N or wp.size != self.N:
+            raise ValueError("one pump coefficient and frequency per mode")
+        re, im = _f64(P.real), _f64(P.imag)
+        self._check(load().cmx_set_pump(self.h, re.ctypes.data, im.ctypes.data, wp.ctypes.data),
+                    "set_pump")
 
     def set_drive(self, eta=None, t0: float = 0.1e-9, sigma: float = 20e-12):
         """cmx_set_drive: Gaussian drive eta_n exp(-(t-t0)^2/(2 sigma^2)) on da_n/dt

@@ -45,10 +45,11 @@ struct RevLocal {
     double wa[2 * MAXN];         // cavity part of the slope adjoint w_S
     double as[2 * MAXN], mm[2 * MAXN];   // a_S and <m^->_S of the recorded forward
     double mc[MC * MAXN];        // mode constants (see MC)
-    double gacc[7 * MAXN];       // per mode: Re g~, Im g~, kappa, omega, Re gb~, Im gb~, K
+    double gacc[NGRAD * MAXN];       // per mode: Re g~, Im g~, kappa, omega, Re gb~, Im gb~, K, Re P, Im P
     double galpha;
     double sums[MAXN + 1];
-    double h;
+    double h, t0;                // step size and start time of the step
+    double pc[3 * MAXN];         // per mode: pump Re P, Im P, frequency
     float cw[7], c1[7];          // h a_{S'S} and h a_{S'1} by S'-1
     float hrf[MAXN], ovr[MAXN], ovi[MAXN];
     unsigned bar_target;
@@ -480,6 +481,20 @@ __device__ bool rev_stage(const AdjArgs &A, RevSmem<NS, WX, WY> &sm, RevLocal &L
             fr += wr * 2.0 * K * ar * ai - wi * K * (3.0 * ar * ar + ai * ai);
             fi += wr * K * (ar * ar + 3.0 * ai * ai) - wi * 2.0 * K * ar * ai;
         }
+        if (c.has_pump) {
+            // parametric pump -i Q conj(a) = (qi ar - qr ai, -(qr ar + qi ai)) at the stage's
+            // time: its (symmetric) Jacobian transposed, and dL/dQ mapped to dL/d Re P, Im P
+            const double ts = S == 1 ? L.t0 : L.t0 + dp_c(S - 1) * L.h;
+            const double *pp = L.pc + 3 * n;
+            double sn, cs;
+            sincos(pp[2] * ts, &sn, &cs);
+            const double qr = pp[0] * cs + pp[1] * sn, qi = pp[1] * cs - pp[0] * sn;
+            fr += qi * wr - qr * wi;
+            fi -= qr * wr + qi * wi;
+            const double lqr = -ai * wr - ar * wi, lqi = ar * wr - ai * wi;
+            L.gacc[NGRAD * n + 7] += lqr * cs - lqi * sn;
+            L.gacc[NGRAD * n + 8] += lqr * sn + lqi * cs;
+        }
         if (S == 7) {
             fr += L.abar[2 * n];
             fi += L.abar[2 * n + 1];
@@ -487,13 +502,13 @@ __device__ bool rev_stage(const AdjArgs &A, RevSmem<NS, WX, WY> &sm, RevLocal &L
         L.Fa[S - 1][2 * n] = fr;
         L.Fa[S - 1][2 * n + 1] = fi;
         const int fb = c.has_gb ? 4 : 0;   // feedback gradients: gb~ if separate, else g~
-        L.gacc[7 * n + 0] += -mi * wr + mr * wi;
-        L.gacc[7 * n + 1] += -mr * wr - mi * wi;
-        L.gacc[7 * n + fb] += tg * ar * Sn;
-        L.gacc[7 * n + fb + 1] -= tg * ai * Sn;
-        L.gacc[7 * n + 2] += -ar * wr - ai * wi;
-        L.gacc[7 * n + 3] += ai * wr - ar * wi;
-        L.gacc[7 * n + 6] += s2 * (wr * ai - wi * ar);
+        L.gacc[NGRAD * n + 0] += -mi * wr + mr * wi;
+        L.gacc[NGRAD * n + 1] += -mr * wr - mi * wi;
+        L.gacc[NGRAD * n + fb] += tg * ar * Sn;
+        L.gacc[NGRAD * n + fb + 1] -= tg * ai * Sn;
+        L.gacc[NGRAD * n + 2] += -ar * wr - ai * wi;
+        L.gacc[NGRAD * n + 3] += ai * wr - ar * wi;
+        L.gacc[NGRAD * n + 6] += s2 * (wr * ai - wi * ar);
     }
     if (tid == 32) L.galpha += L.sums[N];
     __syncthreads();
@@ -532,8 +547,21 @@ __global__ void __launch_bounds__(WX *WY, NS == 1 ? 2 : 1) rev_kernel(AdjArgs A)
         L.abar[tid] = A.ctl->abar[tid];
         L.k1a[tid] = A.ctl->k1a[tid];
     }
-    if (tid < 7 * N) L.gacc[tid] = 0.0;
-    if (tid < N) mode_constants(c, tid, L.mc + MC * tid);
+    if (tid < NGRAD * N) L.gacc[tid] = 0.0;
+    if (tid < N) {
+        mode_constants(c, tid, L.mc + MC * tid);
+        double pr = c.pump_re[0], pi = c.pump_im[0], pw = c.pump_w[0];
+#pragma unroll
+        for (int u = 1; u < MAXN; u++)
+            if (tid == u) {
+                pr = c.pump_re[u];
+                pi = c.pump_im[u];
+                pw = c.pump_w[u];
+            }
+        L.pc[3 * tid] = pr;
+        L.pc[3 * tid + 1] = pi;
+        L.pc[3 * tid + 2] = pw;
+    }
     if (tid == 0) {
         L.galpha = 0.0;
         L.bar_target = 0;
@@ -553,7 +581,10 @@ __global__ void __launch_bounds__(WX *WY, NS == 1 ? 2 : 1) rev_kernel(AdjArgs A)
     __syncthreads();
     bool ok = true;
     for (int jj = A.nsteps - 1; jj >= 0 && ok; jj--) {
-        if (tid == 0) L.h = A.dts[jj];
+        if (tid == 0) {
+            L.h = A.dts[jj];
+            L.t0 = A.rec_t ? A.rec_t[jj] : 0.0;
+        }
         __syncthreads();
         ok = rev_stage<NS, WX, WY, HU, 7>(A, sm, L, jj) && rev_stage<NS, WX, WY, HU, 6>(A, sm, L, jj) &&
              rev_stage<NS, WX, WY, HU, 5>(A, sm, L, jj) && rev_stage<NS, WX, WY, HU, 4>(A, sm, L, jj) &&
@@ -565,7 +596,7 @@ __global__ void __launch_bounds__(WX *WY, NS == 1 ? 2 : 1) rev_kernel(AdjArgs A)
             A.ctl->abar[tid] = L.abar[tid];
             A.ctl->k1a[tid] = L.k1a[tid];
         }
-        if (tid < 7 * N) A.ctl->gacc[tid] += L.gacc[tid];
+        if (tid < NGRAD * N) A.ctl->gacc[tid] += L.gacc[tid];
         if (tid == 0) A.ctl->galpha += L.galpha;
     }
 }

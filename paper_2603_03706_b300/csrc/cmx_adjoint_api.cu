@@ -23,7 +23,7 @@ struct AdjState {
     float *rm[2] = {nullptr, nullptr}, *rk[7] = {};
     Ctl *rctl = nullptr;
     float *rec_m = nullptr;
-    double *rec_a = nullptr;
+    double *rec_a = nullptr, *rec_t = nullptr;
     double *dts = nullptr, *dl = nullptr;
     long long dts_cap = 0, dl_cap = 0;
     float *F[5] = {}, *mbar = nullptr, *k1bar = nullptr, *ubar = nullptr;
@@ -40,7 +40,7 @@ void adj_free(cmx_problem *h)
     AdjState *s = h->adj;
     if (!s) return;
     void *ptrs[] = {s->traj_m, s->traj_k, s->traj_a, s->rm[0], s->rm[1], s->rctl, s->rec_m,
-                    s->rec_a, s->dts, s->dl, s->mbar, s->k1bar, s->ubar, s->ubar64, s->actl,
+                    s->rec_a, s->rec_t, s->dts, s->dl, s->mbar, s->k1bar, s->ubar, s->ubar64, s->actl,
                     s->tiles, s->seg_begin, s->part};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -129,6 +129,7 @@ int ensure_reverse(cmx_problem *h)
     CU(dalloc(&s->rctl, 1));
     CU(dalloc(&s->rec_m, (size_t)s->every * 6 * nq * nc));
     CU(dalloc(&s->rec_a, (size_t)s->every * 7 * 4 * N));
+    CU(dalloc(&s->rec_t, (size_t)s->every));
     for (int j = 0; j < 5; j++) CU(dalloc(&s->F[j], nq * nc));
     CU(dalloc(&s->mbar, nq * nc));
     CU(dalloc(&s->k1bar, nq * nc));
@@ -216,8 +217,10 @@ int cmx_adjoint_record(cmx_problem *h, int every, long long max_steps)
         s->traj_a = nullptr;
         if (s->rec_m) cudaFree(s->rec_m);
         if (s->rec_a) cudaFree(s->rec_a);
+        if (s->rec_t) cudaFree(s->rec_t);
         s->rec_m = nullptr;
         s->rec_a = nullptr;
+        s->rec_t = nullptr;
         if (s->ready) {
             // the interval record is re-sized by ensure_reverse
             adj_free(h);
@@ -334,6 +337,7 @@ int cmx_adjoint(cmx_problem *h, const double *dL_da, const float *dL_dm, int dL_
     fc.traj_a = nullptr;
     fc.rec_m = s->rec_m;
     fc.rec_a = s->rec_a;
+    fc.rec_t = s->rec_t;
     AdjArgs A;
     memset(&A, 0, sizeof A);
     A.f = make_ctx(h);
@@ -341,6 +345,7 @@ int cmx_adjoint(cmx_problem *h, const double *dL_da, const float *dL_dm, int dL_
     A.f.seg_begin = s->seg_begin;
     A.rec_m = s->rec_m;
     A.rec_a = s->rec_a;
+    A.rec_t = s->rec_t;
     A.dL_da = (dL_da && N > 0) ? s->dl : nullptr;
     A.m_first = s->traj_m;
     A.a_first = s->traj_a;
@@ -388,13 +393,15 @@ int cmx_adjoint(cmx_problem *h, const double *dL_da, const float *dL_dm, int dL_
                     h->timeout_ns, ac.timeout_where);
     if (ac.status) return fail(h, ac.status, "reverse sweep status %d", ac.status);
     for (int k = 0; k < N; k++) {
-        if (g->g_re) g->g_re[k] = ac.gacc[7 * k + 0];
-        if (g->g_im) g->g_im[k] = ac.gacc[7 * k + 1];
-        if (g->kappa) g->kappa[k] = ac.gacc[7 * k + 2];
-        if (g->omega) g->omega[k] = ac.gacc[7 * k + 3];
-        if (g->gb_re) g->gb_re[k] = ac.gacc[7 * k + 4];
-        if (g->gb_im) g->gb_im[k] = ac.gacc[7 * k + 5];
-        if (g->kerr) g->kerr[k] = ac.gacc[7 * k + 6];
+        if (g->g_re) g->g_re[k] = ac.gacc[NGRAD * k + 0];
+        if (g->g_im) g->g_im[k] = ac.gacc[NGRAD * k + 1];
+        if (g->kappa) g->kappa[k] = ac.gacc[NGRAD * k + 2];
+        if (g->omega) g->omega[k] = ac.gacc[NGRAD * k + 3];
+        if (g->gb_re) g->gb_re[k] = ac.gacc[NGRAD * k + 4];
+        if (g->gb_im) g->gb_im[k] = ac.gacc[NGRAD * k + 5];
+        if (g->kerr) g->kerr[k] = ac.gacc[NGRAD * k + 6];
+        if (g->pump_re) g->pump_re[k] = ac.gacc[NGRAD * k + 7];
+        if (g->pump_im) g->pump_im[k] = ac.gacc[NGRAD * k + 8];
     }
     if (g->alpha) *g->alpha = ac.galpha;
     if (g->a0)

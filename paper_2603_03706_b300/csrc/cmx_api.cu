@@ -921,6 +921,28 @@ int cmx_set_kerr(cmx_problem *h, const double *kerr)
     return CMX_OK;
 }
 
+int cmx_set_pump(cmx_problem *h, const double *p_re, const double *p_im, const double *wp)
+{
+    if (!h) return CMX_EINVAL;
+    Ctx &c = h->base;
+    if (!p_re) {
+        c.has_pump = 0;
+        for (int n = 0; n < MAXN; n++) c.pump_re[n] = c.pump_im[n] = c.pump_w[n] = 0.0;
+        return CMX_OK;
+    }
+    if (!p_im || !wp) return fail(h, CMX_EINVAL, "pump: p_im and wp are needed");
+    for (int n = 0; n < h->N; n++)
+        if (!std::isfinite(p_re[n]) || !std::isfinite(p_im[n]) || !std::isfinite(wp[n]))
+            return fail(h, CMX_EINVAL, "pump: non-finite coefficient of mode %d", n);
+    for (int n = 0; n < MAXN; n++) {
+        c.pump_re[n] = n < h->N ? p_re[n] : 0.0;
+        c.pump_im[n] = n < h->N ? p_im[n] : 0.0;
+        c.pump_w[n] = n < h->N ? wp[n] : 0.0;
+    }
+    c.has_pump = 1;
+    return CMX_OK;
+}
+
 int cmx_set_drive(cmx_problem *h, const double *eta_re, const double *eta_im, double t0,
                   double sigma)
 {

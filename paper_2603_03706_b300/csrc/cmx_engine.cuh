@@ -25,7 +25,7 @@ struct Team {
 };
 
 // Per-component cavity constants: LC doubles per real component (see component_constants).
-constexpr int LC = 7;
+constexpr int LC = 10;
 
 // Block-local copy of the integrator state.
 struct Local {
@@ -174,6 +174,16 @@ __device__ __forceinline__ void cavity_rhs(const double *mc, int n, double ar, d
     di = -k * ai - w * ar + pr - k2 * ar;
 }
 
+// Parametric pump coefficient Q = P e^{-i wp t} = (qr, qi) at time t.
+__device__ __forceinline__ void pump_coefficient(double pr, double pi, double pw, double t,
+                                                 double &qr, double &qi)
+{
+    double sn, cs;
+    sincos(pw * t, &sn, &cs);
+    qr = pr * cs + pi * sn;
+    qi = pi * cs - pr * sn;
+}
+
 // Operator-split scheme: one classical RK4 step of the cavity from L.t to the next boundary
 // with the overlaps held at mm (those of the current magnetisation), on 2N real components,
 // run by one thread.  Same slope as cavity_rhs plus the drive.
@@ -203,6 +213,13 @@ static __device__ __noinline__ void split_cavity_step(const Ctx &c, Local &L, co
                 dr += er * env;
                 di += ei * env;
             }
+            if (c.has_pump) {   // -i Q conj(a) = (qi ar - qr ai, -(qr ar + qi ai))
+                double qr, qi;
+                pump_coefficient(L.lc[7][2 * n], L.lc[8][2 * n], L.lc[9][2 * n], ts, qr, qi);
+                const double yr = y[2 * n], yi = y[2 * n + 1];
+                dr += qi * yr - qr * yi;
+                di -= qr * yr + qi * yi;
+            }
             k[2 * n] = dr;
             k[2 * n + 1] = di;
         }
@@ -221,19 +238,26 @@ static __device__ __noinline__ void split_cavity_step(const Ctx &c, Local &L, co
 //     d_q = -kappa x + s (w + K |a|^2) x' - s g_r y' - g_i y,
 // x, x' the cavity values and y, y' the overlaps of lane q and of its partner q ^ 1.  lc[5] is
 // the lane's share of the feedback coefficient (2/gamma) Re[gb~ a] (pair sum of lc[5] x) and
-// lc[6] the drive amplitude of the component.
+// lc[6] the drive amplitude of the component; lc[7..9] the mode's pump Re P, Im P and frequency.
 __device__ __forceinline__ void component_constants(const Ctx &c, int q, Local &L)
 {
     double v[MC];
     mode_constants(c, q >> 1, v);
     const int n = q >> 1;
     double dre = c.drive_re[0], dim = c.drive_im[0];
+    double pr = c.pump_re[0], pi = c.pump_im[0], pw = c.pump_w[0];
 #pragma unroll
     for (int u = 1; u < MAXN; u++)
         if (n == u) {
             dre = c.drive_re[u];
             dim = c.drive_im[u];
+            pr = c.pump_re[u];
+            pi = c.pump_im[u];
+            pw = c.pump_w[u];
         }
+    L.lc[7][q] = pr;
+    L.lc[8][q] = pi;
+    L.lc[9][q] = pw;
     const bool im = q & 1;
     L.lc[0][q] = -v[1];
     L.lc[1][q] = im ? -v[0] : v[0];
@@ -314,10 +338,19 @@ __device__ void controller(const Ctx &c, const Team &tm, Local &L, Coef &cf, lon
         d = fma(L.lc[3][q], y, d);
         if (L.has_split && !L.replay) {   // operator split: cavity held during magnet steps
             d = 0.0;
-        } else if (c.has_drive) {   // the drive at this stage's time t + c_S h
+        } else {
+            // drive and parametric pump at this stage's time t + c_S h
             const double ts = S == 1 ? L.t : L.t + dp_c(S - 1) * L.h;
-            const double xe = (ts - c.drive_t0) * c.drive_inv_sigma;
-            d += L.lc[6][q] * exp(-0.5 * xe * xe);
+            if (c.has_drive) {
+                const double xe = (ts - c.drive_t0) * c.drive_inv_sigma;
+                d += L.lc[6][q] * exp(-0.5 * xe * xe);
+            }
+            if (c.has_pump) {   // -i Q conj(a): component q gets s qi x - qr x', s = +1 / -1
+                double qr, qi;
+                pump_coefficient(L.lc[7][q], L.lc[8][q], L.lc[9][q], ts, qr, qi);
+                d = fma((q & 1) ? -qi : qi, x, d);
+                d = fma(-qr, xo, d);
+            }
         }
         L.mm[q] = y;
         L.ka[S - 1][q] = d;
@@ -335,6 +368,7 @@ __device__ void controller(const Ctx &c, const Team &tm, Local &L, Coef &cf, lon
                 double *dd = c.rec_a + ((size_t)L.replay_pos * 7 + (S - 1)) * 4 * N;
                 dd[q] = L.as[q];
                 dd[2 * N + q] = y;
+                if (S == 2 && q == 0 && c.rec_t) c.rec_t[L.replay_pos] = L.t;
             }
         }
         if (S == 1) L.mm_n[q] = y;

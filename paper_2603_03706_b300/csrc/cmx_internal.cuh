@@ -127,6 +127,9 @@ struct Ctx {
     const int4 *tiles;               // segments: x0, y0, z0, z1
     const int *seg_begin;            // block b owns segments [seg_begin[b], seg_begin[b+1])
     int ntiles, bz;
+    int nxs;                         // stored row length of a dense box (nx rounded up to 8)
+    int dense;                       // 1: every row is magnetic over the whole box and the
+                                     // launch takes the dense tensor-copy stage path
     const float *u;                  // [nmodes][ncell] or NULL
     float *m[2];                     // [nsub*3][ncell]
     float *k[7];                     // [nsub*3][ncell]
@@ -151,6 +154,10 @@ struct Ctx {
     double omega[MAXN], kappa[MAXN], gre[MAXN], gim[MAXN];
     double gbre[MAXN], gbim[MAXN];   // backward (feedback) coupling; equal to g~ unless set
     double kerr[MAXN];               // self-Kerr -i K |a|^2 a (0: none)
+    // degenerate parametric pump -i P_n e^{-i wp_n t} conj(a_n) on da_n/dt, P_n = pump_re +
+    // i pump_im [rad/s] at pump frequency pump_w [rad/s]; has_pump = 0: none
+    double pump_re[MAXN], pump_im[MAXN], pump_w[MAXN];
+    int has_pump;
     int has_gb;                      // 1: nonreciprocal coupling (gradients of gb~ separate)
     double two_over_gamma, inv_nmag;
     double red_scale;                // fixed-point scale of the overlap sums (a power of two)
@@ -183,6 +190,7 @@ struct Ctx {
     // m_S (S = 2..7) and, for every stage it evaluates, a_S and <m^->_S.
     float *rec_m;                    // [j][S-2][nsub*3][ncell]
     double *rec_a;                   // [j][S-1][2][2N]
+    double *rec_t;                   // [j]: start time of replay step j
     int rec_steps;
 };
 

@@ -45,10 +45,13 @@ cudaError_t launch_batch_spectrum(const SpecInst *si, int n, double f0, double d
 
 // reverse sweep of the adjoint (cmx_adjoint.cu)
 // Scalar adjoint state in device memory, carried from one checkpoint interval to the previous.
+constexpr int NGRAD = 9;   // scalar gradients per mode (see AdjCtl::gacc)
+
 struct AdjCtl {
     double abar[2 * MAXN];           // dL/d a at the current step boundary
     double k1a[2 * MAXN];            // dL/d (cavity part of the FSAL slope)
-    double gacc[7 * MAXN];           // per mode: dL/d Re g~, Im g~, kappa, omega, Re gb~, Im gb~, K
+    double gacc[NGRAD * MAXN];           // per mode: dL/d Re g~, Im g~, kappa, omega, Re gb~, Im gb~, K,
+                                     // Re P, Im P (parametric pump)
     double galpha;                   // dL/d alpha
     unsigned int bar_count;          // arrival counter of the launch's barrier
     int status;
@@ -59,6 +62,7 @@ struct AdjArgs {
     Ctx f;                           // problem (tiles / seg_begin: the reverse partition)
     const float *rec_m;              // stage points m_S, [j][S-2][nsub*3][ncell]
     const double *rec_a;             // a_S, <m^->_S, [j][S-1][2][2N]
+    const double *rec_t;             // start time of step j of the interval (pump phase)
     const double *dts;               // step sizes of the interval
     const double *dL_da;             // [n+1][2N] by global state index, or NULL
     const float *m_first;            // initial state (stage-1 point of global step 0)

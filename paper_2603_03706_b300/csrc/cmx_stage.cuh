@@ -359,7 +359,7 @@ __device__ __forceinline__ void unit_load(const float *p, float (&o)[CPT])
 // rim element it loads (er, -1: none), a unit (rk = 1) or a single cell (rk = 2) at row rr and
 // column offset rc from the tile's x0 (rc in box cells).
 struct Pipe {
-    Cursor cr, ci;
+    Cursor cr, ci, cc;
     int nq, gend;
     int eo, er, rr, rc, rk;
 };
