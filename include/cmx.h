@@ -106,11 +106,14 @@ typedef struct {
  * two sublattices; bx = by = 0 selects 32x8.  The columns' planes are split into contiguous
  * per-block segments with balanced plane counts; bz: the fewest planes per block (0 = 4); fewer
  * blocks are used when the grid is small.  blocks_per_sm caps the resident blocks per SM (0 =
- * as many as fit).  quad: 0 or 1 (other values are rejected; kept for layout compatibility). */
+ * as many as fit).  A grid magnetic over its whole box (a film, a full box: no mask) is stored
+ * densely and its stages load each plane with tensor copies (cp.async.bulk.tensor, one thread
+ * issuing a few per plane); plain_copies = 1 keeps the per-thread copies of masked grids for it
+ * as well (0 = default; other values are rejected). */
 typedef struct {
     int bx, by, bz;
     int blocks_per_sm;   /* 0 = as many as fit */
-    int quad;            /* 0 or 1 */
+    int plain_copies;    /* 0 or 1 */
 } cmx_tiling;
 
 typedef struct {
@@ -270,9 +273,11 @@ int cmx_load_state(cmx_problem *h, const void *blob, size_t size);
 int cmx_plan_tiling(const cmx_grid *grid, const uint8_t *mask, int bx, int by, int blocks,
                     long long *n_segments, long long *n_stored);
 
-/* Launch shape actually used: bx, by, bz, grid blocks, segments; *quad = 1. */
+/* Launch shape actually used: bx, by, bz, grid blocks, segments; *dense = 1 when the stages
+ * take the tensor-copy path of dense boxes (0: per-thread copies, or the single-block
+ * integrator).  Every pointer may be NULL. */
 int cmx_get_tiling(const cmx_problem *h, int *bx, int *by, int *bz, int *blocks, int *tiles,
-                   int *quad);
+                   int *dense);
 
 const char *cmx_last_error(const cmx_problem *h);
 

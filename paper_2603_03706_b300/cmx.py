@@ -51,7 +51,7 @@ class Solver(C.Structure):
 
 class Tiling(C.Structure):
     _fields_ = [("bx", C.c_int), ("by", C.c_int), ("bz", C.c_int), ("blocks_per_sm", C.c_int),
-                ("quad", C.c_int)]
+                ("plain_copies", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -582,7 +582,7 @@ class Simulation:
     def get_tiling(self) -> dict:
         v = [C.c_int() for _ in range(6)]
         self._check(load().cmx_get_tiling(self.h, *[C.byref(x) for x in v]), "get_tiling")
-        return dict(zip(("bx", "by", "bz", "blocks", "tiles", "quad"), [x.value for x in v]))
+        return dict(zip(("bx", "by", "bz", "blocks", "tiles", "dense"), [x.value for x in v]))
 
     def last_error(self) -> str:
         return load().cmx_last_error(self.h).decode()

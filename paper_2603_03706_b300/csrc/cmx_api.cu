@@ -121,7 +121,10 @@ int setup_tiling(cmx_problem *h, const cmx_tiling *t)
         return fail(h, CMX_EINVAL,
                     "tile %dx%d is not compiled for nsub=%d (32x4, 32x8, 32x16)", bx, by,
                     h->grid.nsub);
-    int occ = single_blocks_per_sm(h->grid.nsub, bx, by, h->N > 0 && h->u != nullptr);
+    // dense boxes take the tensor-copy stage path (not with the full-demag passes, which are
+    // compiled into the per-thread-copy kernels)
+    const bool dense = h->dense_ok && !h->plain_copies && !h->base.fd;
+    int occ = single_blocks_per_sm(h->grid.nsub, bx, by, h->N > 0 && h->u != nullptr, dense);
     if (occ <= 0) return fail(h, CMX_ECUDA, "occupancy query failed for %dx%d", bx, by);
     if (bps > 0) occ = std::min(occ, bps);
     const std::vector<Column> cols = build_columns(h->lay, bx, by);
@@ -131,7 +134,9 @@ int setup_tiling(cmx_problem *h, const cmx_tiling *t)
     if (bz <= 0) bz = 4;
     const long long cap = (long long)occ * h->nsm;
     const int blocks = (int)std::max<long long>(1, std::min<long long>(cap, (P + bz - 1) / bz));
-    return install_tiling(h, cols, blocks, bx, by, bz, occ);
+    const int rc = install_tiling(h, cols, blocks, bx, by, bz, occ);
+    if (rc == CMX_OK) h->base.dense = dense ? 1 : 0;
+    return rc;
 }
 
 // Partition the columns among `blocks` blocks and upload the segments; record the shape.
@@ -208,7 +213,7 @@ int setup_small(cmx_problem *h, const cmx_tiling *t)
 
 int cmx_host::retile(cmx_problem *h, int bx, int by)
 {
-    const cmx_tiling t{bx, by, h->bz, h->bps_cap, 1};
+    const cmx_tiling t{bx, by, h->bz, h->bps_cap, h->plain_copies ? 1 : 0};
     return setup_tiling(h, &t);
 }
 
@@ -437,12 +442,23 @@ int cmx_create(const cmx_grid *grid, const uint8_t *mask, const cmx_material *ma
     if (!coop) return bail(CMX_ECUDA);
 
     // one cell per thread (the only kind of tile)
-    const int tq = tiling ? tiling->quad : 0;
+    const int tq = tiling ? tiling->plain_copies : 0;
     if (tq != 0 && tq != 1) return bail(CMX_EINVAL);
+    h->plain_copies = tq == 1;
     build_layout(h->lay, grid->nx, grid->ny, grid->nz, mask);
     h->ncell = h->lay.ncell;
     h->ncell_mag = h->lay.ncell_mag;
     h->holes = h->lay.holes;
+    {
+        // dense storage: every (y, z) row magnetic over [0, nx), rows of nx rounded up to
+        // ROW_ALIGN cells back to back
+        bool full = !h->lay.holes;
+        for (const int2 &r : h->lay.rows)
+            full = full && (r.y & 0xffff) == 0 && (int)((unsigned)r.y >> 16) == grid->nx;
+        const long long nxs = ((long long)grid->nx + ROW_ALIGN - 1) / ROW_ALIGN * ROW_ALIGN;
+        h->dense_ok = full && (long long)h->ncell == nxs * grid->ny * grid->nz;
+        h->base.nxs = (int)nxs;
+    }
     if (h->ncell_mag == 0) return bail(CMX_EINVAL);
     const int nq = 3 * grid->nsub;
     const size_t nc = (size_t)h->ncell;
@@ -505,6 +521,7 @@ int cmx_create(const cmx_grid *grid, const uint8_t *mask, const cmx_material *ma
     c.nmodes = N;
     c.ncell = h->ncell;
     c.ncell_mag = h->ncell_mag;
+    c.nxs = (grid->nx + ROW_ALIGN - 1) / ROW_ALIGN * ROW_ALIGN;
     c.rows = h->rows;
     c.active = h->holes ? h->active : nullptr;   // the row spans exclude the padding
     c.u = h->u;
@@ -1000,7 +1017,7 @@ int cmx_autotune(cmx_problem *h, int attempts, cmx_tiling *chosen, double *us_pe
     for (int ci = 0; ci <= NC; ci++) {
         double us = NAN;
         const bool small = ci == SB;
-        cmx_tiling t{small ? 0 : cand[ci][0], small ? 0 : cand[ci][1], bz, bps, 1};
+        cmx_tiling t{small ? 0 : cand[ci][0], small ? 0 : cand[ci][1], bz, bps, h->plain_copies ? 1 : 0};
         h->use_small = small;
         // full demag runs on the 32 x 8 tiles only
         const bool allowed = !h->base.fd || (!small && t.bx == 32 && t.by == 8);
@@ -1048,12 +1065,12 @@ int cmx_autotune(cmx_problem *h, int attempts, cmx_tiling *chosen, double *us_pe
                 tb = ci;
             }
     }
-    cmx_tiling t{cand[tb][0], cand[tb][1], bz, bps, 1};
+    cmx_tiling t{cand[tb][0], cand[tb][1], bz, bps, h->plain_copies ? 1 : 0};
     rc = setup_tiling(h, &t);
     if (rc) return rc;
     h->use_small = bi == SB;
     h->small_default = h->use_small;
-    if (chosen) *chosen = bi == SB ? cmx_tiling{0, 0, bz, bps, 1} : t;
+    if (chosen) *chosen = bi == SB ? cmx_tiling{0, 0, bz, bps, h->plain_copies ? 1 : 0} : t;
     return CMX_OK;
 }
 
@@ -1077,10 +1094,10 @@ int cmx_plan_tiling(const cmx_grid *grid, const uint8_t *mask, int bx, int by, i
 }
 
 int cmx_get_tiling(const cmx_problem *h, int *bx, int *by, int *bz, int *blocks, int *tiles,
-                   int *quad)
+                   int *dense)
 {
     if (!h) return CMX_EINVAL;
-    if (quad) *quad = 1;
+    if (dense) *dense = (!h->use_small && h->base.dense) ? 1 : 0;
     if (bx) *bx = h->use_small ? 0 : h->bx;
     if (by) *by = h->use_small ? 0 : h->by;
     if (bz) *bz = h->bz;

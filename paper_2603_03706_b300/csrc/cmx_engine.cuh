@@ -322,6 +322,7 @@ __device__ void controller(const Ctx &c, const Team &tm, Local &L, Coef &cf, lon
     const int N = c.nmodes;
     const int q = threadIdx.x;
     if (q >= 32) return;
+    __syncwarp();   // the lanes' shuffles below need the whole warp at the same point
     const bool own = q < 2 * N;
     const bool rec = tm.rank == 0;
     const long long li = L.log_n;

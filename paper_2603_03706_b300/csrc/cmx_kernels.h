@@ -8,7 +8,11 @@ namespace cmx {
 // persistent single-problem integrator (cmx_single.cu); tiles of bx x by cells, one thread each
 bool tile_shape_supported(int nsub, int bx, int by);
 cudaError_t launch_single(const Ctx &c, int bx, int by, int blocks, cudaStream_t s);
-int single_blocks_per_sm(int nsub, int bx, int by, bool has_u);
+int single_blocks_per_sm(int nsub, int bx, int by, bool has_u, bool dense = false);
+// tensor maps of a dense launch (cmx_dense_maps.cu): the tile and operand boxes of its buffers
+// for tiles of 32 x wy cells, in the order of the TM_* indices of cmx_dense.cuh; `map` points to
+// `count` CUtensorMap objects (128 bytes each)
+cudaError_t build_dense_maps(const Ctx &c, int wy, void *map, int count);
 
 // single-block integrator for small grids (cmx_small.cu): sidx = stored index of each of the nm
 // magnetic cells, snb = their neighbour table [-x, +x, -y, +y, -z, +z][nm] (-1: none)

@@ -26,6 +26,8 @@ struct cmx_problem {
     long long nbox = 0;
     int ncell = 0, ncell_mag = 0;
     bool holes = false;   // holes inside a row's magnetic span (stage kernels test them)
+    bool dense_ok = false;      // every row is magnetic over the whole box (dense storage)
+    bool plain_copies = false;  // cmx_tiling.plain_copies: no tensor-copy stage path
     Layout lay;
     // device buffers
     int2 *rows = nullptr;

@@ -7,7 +7,7 @@ namespace cmx {
 template <int NS, int WX, int WY>
 cudaError_t launch_tiles(const Ctx &c, int blocks, cudaStream_t s);
 template <int NS, int WX, int WY>
-int occupancy_tiles(bool has_u);
+int occupancy_tiles(bool has_u, bool dense);
 
 // Compiled tiles: 32 x 4, 32 x 8 and 32 x 16 cells for one and for two sublattices.
 #define CMX_VARIANTS(X) \
@@ -29,9 +29,9 @@ cudaError_t launch_single(const Ctx &c, int bx, int by, int blocks, cudaStream_t
     return cudaErrorInvalidValue;
 }
 
-int single_blocks_per_sm(int nsub, int bx, int by, bool has_u)
+int single_blocks_per_sm(int nsub, int bx, int by, bool has_u, bool dense)
 {
-#define X(n, a, b) if (nsub == n && bx == a && by == b) return occupancy_tiles<n, a, b>(has_u);
+#define X(n, a, b) if (nsub == n && bx == a && by == b) return occupancy_tiles<n, a, b>(has_u, dense);
     CMX_VARIANTS(X)
 #undef X
     return 0;
