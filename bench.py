@@ -86,7 +86,8 @@ def bytes_per_cell_attempt(p):
 
 # Sources that define the single-problem integrator launch (kernel, engine, stage code, the
 # host code that lays out the cells and partitions the blocks).
-KERNEL_SOURCES = ("cmx_internal.cuh", "cmx_stage.cuh", "cmx_engine.cuh", "cmx_demag.cuh",
+KERNEL_SOURCES = ("cmx_internal.cuh", "cmx_stage.cuh", "cmx_dense.cuh", "cmx_dense_maps.cu",
+                  "cmx_engine.cuh", "cmx_demag.cuh",
                   "cmx_single_kernel.cuh", "cmx_single_t1x4.cu", "cmx_single_t1x8.cu",
                   "cmx_single_t1x16.cu", "cmx_single_t2x4.cu", "cmx_single_t2x8.cu",
                   "cmx_single_t2x16.cu", "cmx_single.cu", "cmx_kernels.h", "cmx_layout.cu",

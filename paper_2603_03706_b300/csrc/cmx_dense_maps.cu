@@ -36,7 +36,7 @@ EncodeTiled encoder()
 // Map of `base` seen as (nx, ny, nz, ncomp) FP32 with rows of nxs cells, planes of nxs ny cells
 // and components ncell apart, read in boxes of bx x by x 1 x ncomp.
 cudaError_t encode(EncodeTiled enc, CUtensorMap *m, const void *base, const Ctx &c, int ncomp,
-                   int bx, int by)
+                   int bx, int by, CUtensorMapL2promotion promo)
 {
     const cuuint64_t dim[4] = {(cuuint64_t)c.nx, (cuuint64_t)c.ny, (cuuint64_t)c.nz,
                                (cuuint64_t)ncomp};
@@ -46,7 +46,7 @@ cudaError_t encode(EncodeTiled enc, CUtensorMap *m, const void *base, const Ctx 
     const cuuint32_t es[4] = {1u, 1u, 1u, 1u};
     const CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<void *>(base), dim,
                            stride, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                           CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                           CU_TENSOR_MAP_SWIZZLE_NONE, promo,
                            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
@@ -66,8 +66,13 @@ cudaError_t build_dense_maps(const Ctx &c, int wy, void *map, int count)
     const int nq = 3 * c.nsub;
     const int tx = DX, ty = wy + 2, ox = 32, oy = wy;
     cudaError_t e = cudaSuccess;
+    // L2 fills: the tile boxes' rows (160 bytes from a 16-byte offset) in 128-byte lines; the
+    // operand rows (128 bytes, aligned) without promotion, since the neighbouring tile's half of
+    // a wider line is read by another block much later and mostly evicted by then
     auto put = [&](int i, const void *base, int ncomp, int bx, int by) {
-        if (e == cudaSuccess && base) e = encode(enc, &m[i], base, c, ncomp, bx, by);
+        const CUtensorMapL2promotion promo = bx == DX ? CU_TENSOR_MAP_L2_PROMOTION_L2_128B
+                                                      : CU_TENSOR_MAP_L2_PROMOTION_NONE;
+        if (e == cudaSuccess && base) e = encode(enc, &m[i], base, c, ncomp, bx, by, promo);
     };
     for (int b = 0; b < 2; b++) {
         put(TMT_M + b, c.m[b], nq, tx, ty);
