@@ -18,9 +18,10 @@
 // A ring of RING tile slots (planes p-1, p, p+1 read by the stencil of plane p, plane p+2 in
 // flight) and D operand slots, one mbarrier each, initialised at the start of every stage.
 // Iteration p waits for plane p+1's tile (at stage 2 it forms the tile's values m_n + h a_21 k_1
-// in place), publishes it with the block barrier, lets the producer thread (lane 0 of the last
-// warp) issue plane p+2's tile and plane p+1's operands into the slots that the barrier has just
-// freed, and computes plane p, waiting for its operands where they are first used.  Halo planes
+// in place), publishes it with the block barrier, lets lane 0 of warps 1 .. NW-1 issue plane
+// p+2's tile and plane p+1's operands (dealt round-robin) into the slots that the barrier has
+// just freed, and computes plane p, waiting for its operands where they are first used.  The
+// copies at a stage's start are issued by one producer thread outside warp 0.  Halo planes
 // (the first and last plane of a segment) get a tile and no operands: their operand phase is
 // completed by a plain arrival.  (Measured and not kept: releasing slots per warp on a second
 // mbarrier instead of the block barrier, 3 % slower; L2 prefetches of the boxes two planes
@@ -253,6 +254,75 @@ __device__ __forceinline__ void dense_issue_ops(const Ctx &c, DenseSmem<NS, WY, 
     if (HU) tma_load4_hint(sm.upool[s], tmap(sm, TMO_U), cu.x0, cu.y0, z, &sm.obar[s], pol);
 }
 
+// Lane 0 of issuing warp k (of K): its share of the copies of one iteration, the tile box of
+// stream plane gt (and at stage 2 its k1 box) and the operand boxes (and profiles) of stream
+// plane go, dealt round-robin so that no warp carries all the issue work (every warp waits for
+// the slowest at the plane's block barrier).  The issuer of the tile announces the tile bytes on
+// its slot's barrier, the issuer of the first operand the operand bytes; a halo plane's operand
+// phase is completed by a plain arrival.
+template <int NS, int WY, bool HU, int S>
+__device__ __forceinline__ void dense_issue_share(const Ctx &c, DenseSmem<NS, WY, HU> &sm,
+                                                  const float *mn, int gt, int go, int k, int K,
+                                                  Pipe &pp)
+{
+    using SM = DenseSmem<NS, WY, HU>;
+    constexpr int NO = n_ops(S), NTC = S == 2 ? 2 : 1;
+    const int nt = gt < pp.gend ? NTC : 0;
+    int no = 0, zo = 0, xo = 0, yo = 0;
+    bool inner = false;
+    if (go < pp.gend) {
+        cursor_seek(sm, pp.cr, go);
+        const int q = go - pp.cr.off;
+        inner = q >= 1 && q <= pp.cr.np - 2 && (NO > 0 || HU);
+        no = inner ? NO + (HU ? 1 : 0) : 1;
+        zo = pp.cr.z0 - 1 + q;
+        xo = pp.cr.x0;
+        yo = pp.cr.y0;
+    }
+    if (k >= nt + no) return;
+    int zt = 0, xt = 0, yt = 0;
+    if (nt) {
+        cursor_seek(sm, pp.ci, gt);
+        zt = pp.ci.z0 - 1 + (gt - pp.ci.off);
+        xt = pp.ci.x0;
+        yt = pp.ci.y0;
+    }
+    const int r = gt % SM::RING, s = go % SM::D;
+    const unsigned long long pol = l2_stream();
+    for (int i = k; i < nt + no; i += K) {
+        if (i < nt) {
+            if (i == 0) {
+                mbar_arrive_expect_tx(&sm.tbar[r], (unsigned)(SM::NQ * SM::P * 4 * NTC));
+                const int src = S <= 2 ? TMT_M + (mn == c.m[0] ? 0 : 1) : TMT_MSV + (S & 1);
+                tma_load4(sm.v[r], tmap(sm, src), xt - DOFF, yt - 1, zt, &sm.tbar[r]);
+            } else {
+                tma_load4(sm.pool[gt % SM::D] + SM::SIDE,
+                          tmap(sm, TMT_K + slope_index(c, sm.kp[0])), xt - DOFF, yt - 1, zt,
+                          &sm.tbar[r]);
+            }
+            continue;
+        }
+        const int a = i - nt;
+        if (!inner) {
+            mbar_arrive(&sm.obar[s]);
+            continue;
+        }
+        if (a == 0)
+            mbar_arrive_expect_tx(&sm.obar[s], (unsigned)(NO * SM::NQ * SM::CW * 4) +
+                                                   (HU ? (unsigned)(c.nmodes * SM::CW * 4) : 0u));
+        if (a < NO) {
+            int mi;
+            if (S == 7) mi = TMO_ES;
+            else if (a == 0) mi = TMO_M + (mn == c.m[0] ? 0 : 1);
+            else mi = TMO_K + slope_index(c, sm.kp[op_slope(S, a)]);
+            tma_load4_hint(sm.pool[s] + a * SM::NQ * SM::CW, tmap(sm, mi), xo, yo, zo,
+                           &sm.obar[s], pol);
+        } else {
+            tma_load4_hint(sm.upool[s], tmap(sm, TMO_U), xo, yo, zo, &sm.obar[s], pol);
+        }
+    }
+}
+
 // Stage 2: the values m_2 = m_n + h a_21 k_1 of every position of plane g's tile box (its copies
 // are complete), spread over the block's threads; the block barrier that follows publishes them.
 template <int NS, int WY, bool HU, int S>
@@ -440,11 +510,16 @@ __device__ void dense_run(const Ctx &c, DenseSmem<NS, WY, HU> &sm, float *kout, 
     for (int p = 1; p <= gend - 2; p++) {
         mbar_wait(c, &sm.tbar[(p + 1) % R], (unsigned)(((p + 1) / R) & 1), 22);
         dense_tile_combine<NS, WY, HU, S>(sm, cf, p + 1, pp);
-        fence_proxy_async_smem();
+        // stage 2 wrote the tile in place: order those writes before later copies into the slot
+        // (reads alone are ordered by the block barrier)
+        if (S == 2) fence_proxy_async_smem();
         __syncthreads();
-        if (threadIdx.x == SM::PROD) {
-            dense_issue_tile<NS, WY, HU, S>(c, sm, mn, p + 2, pp);
-            dense_issue_ops<NS, WY, HU, S>(c, sm, mn, p + 1, pp);
+        {
+            // issuing warps 1 .. NW-1 (warp 0 runs the controller between stages)
+            const int w = threadIdx.x >> 5;
+            if ((threadIdx.x & 31) == 0 && w >= 1)
+                dense_issue_share<NS, WY, HU, S>(c, sm, mn, p + 2, p + 1, w - 1, SM::NT / 32 - 1,
+                                                 pp);
         }
         __syncwarp();
         cursor_seek(sm, pp.cc, p);
