@@ -532,12 +532,11 @@ __device__ __forceinline__ void cell_slope(const Ctx &c, const Coef &cf, const f
     float brf = 0.f;
 #pragma unroll
     for (int n = 0; n < MAXN; n++) {
-        if (n < c.nmodes) {
-            const float un = HU ? ucell[n] : 1.f;
-            brf = fmaf(un, cf.hrf[n], brf);
-            acc.re[n] = fmaf(un, hx, acc.re[n]);
-            acc.im[n] = fmaf(-un, hy, acc.im[n]);
-        }
+        if (n >= c.nmodes) break;   // leaves the unrolled chain after the problem's modes
+        const float un = HU ? ucell[n] : 1.f;
+        brf = fmaf(un, cf.hrf[n], brf);
+        acc.re[n] = fmaf(un, hx, acc.re[n]);
+        acc.im[n] = fmaf(-un, hy, acc.im[n]);
     }
 #pragma unroll
     for (int s = 0; s < NS; s++) {
