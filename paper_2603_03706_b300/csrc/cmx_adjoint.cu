@@ -74,6 +74,23 @@ __device__ __forceinline__ void red_add_release_u32(unsigned *p, unsigned v)
     asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
+// Parametric pump -i Q conj(a) = (qi ar - qr ai, -(qr ar + qi ai)), Q = P e^{-i wp t}, at time
+// t: its (symmetric) Jacobian transposed onto the slope adjoint (wr, wi) -> out[0..1], and dL/dQ
+// mapped to dL/d Re P, dL/d Im P -> out[2..3].  pp = (Re P, Im P, wp).  Out of line, so that the
+// FP64 sine and cosine do not weigh on the reverse stage when no pump is set.
+static __device__ __noinline__ void pump_adjoint(const double *pp, double t, double ar, double ai,
+                                                 double wr, double wi, double *out)
+{
+    double sn, cs;
+    sincos(pp[2] * t, &sn, &cs);
+    const double qr = pp[0] * cs + pp[1] * sn, qi = pp[1] * cs - pp[0] * sn;
+    out[0] = qi * wr - qr * wi;
+    out[1] = -(qr * wr + qi * wi);
+    const double lqr = -ai * wr - ar * wi, lqi = ar * wr - ai * wi;
+    out[2] = lqr * cs - lqi * sn;
+    out[3] = lqr * sn + lqi * cs;
+}
+
 // Barrier of all blocks of the launch (monotonic arrival counter, bounded wait; on time-out the
 // status becomes CMX_ETIMEOUT and every block leaves).
 __device__ bool rev_barrier(const AdjArgs &A, RevLocal &L, int where)
@@ -482,18 +499,13 @@ __device__ bool rev_stage(const AdjArgs &A, RevSmem<NS, WX, WY> &sm, RevLocal &L
             fi += wr * K * (ar * ar + 3.0 * ai * ai) - wi * 2.0 * K * ar * ai;
         }
         if (c.has_pump) {
-            // parametric pump -i Q conj(a) = (qi ar - qr ai, -(qr ar + qi ai)) at the stage's
-            // time: its (symmetric) Jacobian transposed, and dL/dQ mapped to dL/d Re P, Im P
             const double ts = S == 1 ? L.t0 : L.t0 + dp_c(S - 1) * L.h;
-            const double *pp = L.pc + 3 * n;
-            double sn, cs;
-            sincos(pp[2] * ts, &sn, &cs);
-            const double qr = pp[0] * cs + pp[1] * sn, qi = pp[1] * cs - pp[0] * sn;
-            fr += qi * wr - qr * wi;
-            fi -= qr * wr + qi * wi;
-            const double lqr = -ai * wr - ar * wi, lqi = ar * wr - ai * wi;
-            L.gacc[NGRAD * n + 7] += lqr * cs - lqi * sn;
-            L.gacc[NGRAD * n + 8] += lqr * sn + lqi * cs;
+            double o[4];
+            pump_adjoint(L.pc + 3 * n, ts, ar, ai, wr, wi, o);
+            fr += o[0];
+            fi += o[1];
+            L.gacc[NGRAD * n + 7] += o[2];
+            L.gacc[NGRAD * n + 8] += o[3];
         }
         if (S == 7) {
             fr += L.abar[2 * n];
