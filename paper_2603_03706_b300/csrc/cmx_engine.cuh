@@ -174,6 +174,14 @@ __device__ __forceinline__ void cavity_rhs(const double *mc, int n, double ar, d
     di = -k * ai - w * ar + pr - k2 * ar;
 }
 
+// Drive share eta exp(-(t - t0)^2 / (2 sigma^2)) of a component's cavity slope (out of line like
+// the pump term, which keeps the FP64 exponential out of the controller's inlined code).
+static __device__ __noinline__ double drive_term(double eta, double t, double t0, double inv_sigma)
+{
+    const double xe = (t - t0) * inv_sigma;
+    return eta * exp(-0.5 * xe * xe);
+}
+
 // Parametric pump coefficient Q = P e^{-i wp t} = (qr, qi) at time t.
 __device__ __forceinline__ void pump_coefficient(double pr, double pi, double pw, double t,
                                                  double &qr, double &qi)
@@ -354,10 +362,7 @@ __device__ void controller(const Ctx &c, const Team &tm, Local &L, Coef &cf, lon
         } else {
             // drive and parametric pump at this stage's time t + c_S h
             const double ts = S == 1 ? L.t : L.t + dp_c(S - 1) * L.h;
-            if (c.has_drive) {
-                const double xe = (ts - c.drive_t0) * c.drive_inv_sigma;
-                d += L.lc[6][q] * exp(-0.5 * xe * xe);
-            }
+            if (c.has_drive) d += drive_term(L.lc[6][q], ts, c.drive_t0, c.drive_inv_sigma);
             if (c.has_pump)   // -i Q conj(a): component q gets s qi x - qr x', s = +1 / -1
                 d += pump_term(L.lc[7][q], L.lc[8][q], L.lc[9][q], ts, q, x, xo);
         }
