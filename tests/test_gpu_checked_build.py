@@ -1,5 +1,6 @@
 """The bounds-checked build (libcmx_check.so, CMX_CHECK = 1) on the ragged, holed and
-two-sublattice grids of the parity tests (needs a B300).
+two-sublattice grids of the parity tests and on the dense boxes of the tensor-copy path (needs a
+B300).
 
 Every stage kernel of that build checks its shared- and global-memory indices; a failed check
 stops the run with CMX_ECHECK instead of touching memory.  The parity tests below run in a child
@@ -27,9 +28,9 @@ def test_parity_suite_runs_clean_on_the_checked_build():
         "from paper_2603_03706_b300 import cmx\n"
         "assert cmx.load().cmx_checked_build() == 1\n"
         "import pytest\n"
-        "sys.exit(pytest.main(['-q', '-p', 'no:cacheprovider', '-x', %r, '-k', %r]))\n"
+        "sys.exit(pytest.main(['-q', '-p', 'no:cacheprovider', '-x', %r, %r, '-k', %r]))\n"
         % (ROOT, os.path.join(ROOT, "tests"), os.path.join(ROOT, "tests", "test_gpu_parity.py"),
-           selection))
+           os.path.join(ROOT, "tests", "test_gpu_dense.py"), selection))
     env = dict(os.environ, CMX_LIBRARY=lib)
     r = subprocess.run([sys.executable, "-c", script], env=env, cwd=ROOT, capture_output=True,
                        text=True, timeout=1500)
