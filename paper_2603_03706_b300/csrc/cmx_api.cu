@@ -133,7 +133,10 @@ int setup_tiling(cmx_problem *h, const cmx_tiling *t)
     // bz: the fewest planes a block should get (default 4); all resident blocks otherwise
     if (bz <= 0) bz = 4;
     const long long cap = (long long)occ * h->nsm;
-    const int blocks = (int)std::max<long long>(1, std::min<long long>(cap, (P + bz - 1) / bz));
+    // with the full demag every resident block takes part in the FFT passes of each stage (their
+    // lines are spread over the blocks), whatever the number of planes
+    const int blocks = h->base.fd ? (int)std::max<long long>(1, cap)
+                                  : (int)std::max<long long>(1, std::min<long long>(cap, (P + bz - 1) / bz));
     const int rc = install_tiling(h, cols, blocks, bx, by, bz, occ);
     if (rc == CMX_OK) h->base.dense = dense ? 1 : 0;
     return rc;

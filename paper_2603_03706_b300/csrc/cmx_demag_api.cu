@@ -132,10 +132,13 @@ extern "C" int cmx_set_demag(cmx_problem *h, int mode)
     const double mu0 = 4.0e-7 * M_PI;
     if (mode == 0) {
         for (int k = 0; k < 3; k++) c.dmg[k] = (float)(mu0 * h->mat.Ms * h->mat.Ndemag[k]);
+        const bool was_full = c.fd != 0;
         c.fd = 0;
         demag_free(h);
         h->use_small = h->small_ok && h->small_default;
-        return CMX_OK;
+        // back to the launch shape of the diagonal factors (the full demag used every resident
+        // block for its FFT passes)
+        return was_full ? retile(h, h->bx, h->by) : CMX_OK;
     }
     if (h->base.traj_m)
         return fail(h, CMX_EINVAL, "the adjoint covers the diagonal demag factors only");
