@@ -126,3 +126,23 @@ def test_dense_adjoint_matches_oracle():
     go = oracle_grads(p, dts, la, wm)
     errs = compare(p, g, go)
     assert all(v <= TOL_G for v in errs.values()), errs
+
+
+def test_dense_replay_with_cavity_extensions():
+    """Drive pulse, nonreciprocal coupling, Kerr term and parametric pump on a dense box: the
+    cavity work sits in the controller, shared by both copy paths; this runs it after the dense
+    stages (1000 replayed steps against the oracle)."""
+    p = dense_problem(nsub=1, nmodes=2, seed=51)
+    p = p.replace(m0=W.tilted_state(1, p.nx, p.ny, p.nz, 4.0, 0.1), a0=np.array([2e-3, 1e-3j]),
+                  T=1e-6)
+    p = p.replace(g_back=TP * np.array([25e6 + 5e6j, 70e6 - 10e6j]),
+                  kerr=TP * np.array([4e10, -2e10]),
+                  pump=TP * np.array([3e6 + 1e6j, -2e6 + 4e6j]),
+                  pump_omega=TP * np.array([10.0e9, 10.3e9]),
+                  drive=np.array([4e7 + 1e7j, -2e7j]), drive_t0=20e-12, drive_sigma=10e-12)
+    p = p.replace(dt_max=W.stable_dt_max(p))
+    sim = sim_for(f32_state(f32_profiles(p)), log_cap=0, tiling=(32, 8, 4))
+    assert sim.get_tiling()["dense"] == 1
+    sim.close()
+    dm, da, info = replay_compare(p, 1000, tiling=(32, 8, 4))
+    assert dm <= TOL_M and da <= TOL_A, (dm, da)

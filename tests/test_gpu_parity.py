@@ -314,14 +314,19 @@ def test_autotune_restores_the_state_and_keeps_a_compiled_window():
     sim.close()
 
 
-@pytest.mark.parametrize("case", ["ragged", "single_block", "afm"])
+@pytest.mark.parametrize("case", ["ragged", "single_block", "afm", "dense_afm"])
 def test_save_and_load_state_resume_bitwise(case):
     """A run saved after some attempts and resumed in a fresh handle continues bitwise like the
-    uninterrupted run: state, cavity amplitudes, step sizes and the step log."""
+    uninterrupted run: state, cavity amplitudes, step sizes and the step log (the dense case runs
+    on the tensor-copy path of grids magnetic over their whole box)."""
     if case == "ragged":
         p = f32_state(ragged_problem(seed=17).replace(T=1e-6))
     elif case == "afm":
         p = f32_state(ragged_problem(nsub=2, seed=19).replace(T=1e-6))
+    elif case == "dense_afm":
+        p = ragged_problem(nsub=2, seed=29)
+        p = p.replace(mask=W.full_mask(p.nx, p.ny, p.nz), T=1e-6)
+        p = f32_state(p.replace(dt_max=W.stable_dt_max(p)))
     else:
         p = f32_state(W.single_sphere())
     sim = sim_for(p, log_cap=400)
