@@ -4,11 +4,12 @@
 // single-mode Rabi and anticrossing runs of Sec. IV A-B) is integrated by ONE block of 256
 // threads that keeps, for every magnetic cell, m_n and the new state, the stage value, the seven
 // slopes, the error partial, the mode profiles and a neighbour table in shared memory.  A stage is
-// two block-wide passes over the cells (stage value, then field and slope), the overlap sums are
+// one block-wide pass over the cells (field, slope and the cell's next stage value; stage 2 also
+// a pass forming its stage values), the overlap sums are
 // block sums in shared memory with the same fixed-point digits as the multi-block reduction, and
 // the cavity update and the step-size controller are the engine's own (warp 0).  No stage touches
-// global memory except for the step log and the trace, and a stage costs three block barriers
-// instead of a grid barrier through L2.  The per-cell arithmetic is the tiled kernel's
+// global memory except for the step log and the trace, and a stage costs two or three block
+// barriers instead of a grid barrier through L2.  The per-cell arithmetic is the tiled kernel's
 // (cell_slope, the same combine order), so the two integrate the same discrete system.
 #include "cmx_engine.cuh"
 #include "cmx_kernels.h"
@@ -21,7 +22,7 @@ constexpr int SMALL_NW = SMALL_NT / 32;
 size_t small_smem_bytes(int nm, int nsub, int nmodes, bool has_u)
 {
     const size_t nq = 3 * (size_t)nsub;
-    return ((2 + 1 + 1 + 7) * nq + (has_u ? (size_t)nmodes : 0)) * nm * sizeof(float) +
+    return ((2 + 2 + 1 + 7) * nq + (has_u ? (size_t)nmodes : 0)) * nm * sizeof(float) +
            6 * (size_t)nm * sizeof(int);
 }
 
@@ -84,7 +85,8 @@ __device__ void small_block_sums(const Ctx &c, const Local &L, const Acc &acc, S
 
 struct SmallBuf {
     float *mb0, *mb1;      // the two state buffers (index = the control block's mcur)
-    float *ms, *es, *kk;   // stage value, error partial, slopes [physical][q][cell]
+    float *ms[2];          // stage values: stage S reads ms[S & 1], writes m_{S+1} to the other
+    float *es, *kk;        // error partial, slopes [physical][q][cell]
     const float *uu;       // profiles [n][cell]
     const int *nb;         // neighbours [-x, +x, -y, +y, -z, +z][cell], -1 = none
 };
@@ -105,26 +107,19 @@ __device__ void small_stage(const Ctx &c, int nm, const SmallBuf &b, Local &L, C
         if (S == 2 && tid == 96) cf.h = (float)L.h;
         __syncthreads();
     }
-    // stage value m_S = m_n + sum_j (h a_Sj) k_j (and at stage 7 the error partial
-    // sum_{j<7} E_j k_j), in the tiled kernel's order of operations
-    const float *src = mn;
-    if (S >= 2) {
+    // stage values: stage 2 forms m_2 = m_n + h a_21 k_1 in a pass of its own (the step size is
+    // known only when the attempt starts); stages 2..6 form the next stage value
+    // m_{S+1} = m_n + sum_{j<=S} (h a_{S+1,j}) k_j of their cell right after its slope (and stage
+    // 6 the error partial sum_{j<=6} E_j k_j), in the tiled kernel's order of operations, so
+    // stages 3..7 need no pass and no barrier before their field pass
+    const float *src = S == 1 ? mn : b.ms[S & 1];
+    if (S == 2) {
         for (int i = tid; i < nm; i += SMALL_NT)
 #pragma unroll
-            for (int q = 0; q < NQ; q++) {
-                float a = mn[q * nm + i], e = 0.f;
-#pragma unroll
-                for (int j = 0; j < S - 1; j++)
-                    if (dp_a(S - 1, j) != 0.0 || (S == 7 && dp_e(j) != 0.0)) {
-                        const float kj = b.kk[L.kphys[j] * V + q * nm + i];
-                        if (dp_a(S - 1, j) != 0.0) a = fmaf(cf.cf[S - 1][j], kj, a);
-                        if (S == 7 && dp_e(j) != 0.0) e = fmaf(cf.e[j], kj, e);
-                    }
-                b.ms[q * nm + i] = a;
-                if (S == 7) b.es[q * nm + i] = e;
-            }
+            for (int q = 0; q < NQ; q++)
+                b.ms[0][q * nm + i] =
+                    fmaf(cf.cf[1][0], b.kk[L.kphys[0] * V + q * nm + i], mn[q * nm + i]);
         __syncthreads();
-        src = b.ms;
     }
     Acc acc;
 #pragma unroll
@@ -165,6 +160,22 @@ __device__ void small_stage(const Ctx &c, int nm, const SmallBuf &b, Local &L, C
         for (int s = 0; s < NS; s++) {
 #pragma unroll
             for (int k = 0; k < 3; k++) kout[(s * 3 + k) * nm + i] = kv[s][k];
+            if (S >= 2 && S <= 6) {
+#pragma unroll
+                for (int k = 0; k < 3; k++) {
+                    const int q = s * 3 + k;
+                    float a = mn[q * nm + i], e = 0.f;
+#pragma unroll
+                    for (int j = 0; j < S - 1; j++) {
+                        if (dp_a(S, j) == 0.0 && !(S == 6 && dp_e(j) != 0.0)) continue;
+                        const float kj = b.kk[L.kphys[j] * V + q * nm + i];
+                        if (dp_a(S, j) != 0.0) a = fmaf(cf.cf[S][j], kj, a);
+                        if (S == 6 && dp_e(j) != 0.0) e = fmaf(cf.e[j], kj, e);
+                    }
+                    b.ms[(S + 1) & 1][q * nm + i] = fmaf(cf.cf[S][S - 1], kv[s][k], a);
+                    if (S == 6) b.es[q * nm + i] = fmaf(cf.e[5], kv[s][k], e);
+                }
+            }
             if (S == 7) {
                 const float *mm = m[s];
                 const float r = rsqrtf(mm[0] * mm[0] + mm[1] * mm[1] + mm[2] * mm[2]);
@@ -209,11 +220,12 @@ __global__ void __launch_bounds__(SMALL_NT, 1) small_kernel(SmallArgs A)
     SmallBuf b;
     b.mb0 = sh;
     b.mb1 = sh + V;
-    b.ms = sh + 2 * V;
-    b.es = sh + 3 * V;
-    b.kk = sh + 4 * V;
+    b.ms[0] = sh + 2 * V;
+    b.ms[1] = sh + 3 * V;
+    b.es = sh + 4 * V;
+    b.kk = sh + 5 * V;
     b.uu = b.kk + 7 * V;
-    int *nb = reinterpret_cast<int *>(sh + 11 * V + (HU ? (size_t)c.nmodes * nm : 0));
+    int *nb = reinterpret_cast<int *>(sh + 12 * V + (HU ? (size_t)c.nmodes * nm : 0));
     b.nb = nb;
     if (tid == 0) {
         load_local(c, L);
