@@ -578,9 +578,16 @@ def main():
             "data": "synthetic", "config": config, "roofline": rec["roofline"],
             "clocks": rec["clocks"], "gpu_launches": 2 * args.steps, "e2e": e2e,
         }
-        if not args.no_cpu_baseline:
-            line["cpu_baseline"] = cpu_baseline(p, args.cpu_seconds)
-        if not args.no_sub:
+        def leg(fn, *a):
+            # a sub-record that fails reports its error instead of taking the headline line
+            # with it
+            from paper_2603_03706_b300 import cmx
+            try:
+                return fn(*a)
+            except (cmx.CmxError, RuntimeError, ValueError) as e:
+                return {"error": f"{type(e).__name__}: {e}"}
+
+        def sub_workloads():
             # the other single-problem workloads, each with its own roofline record
             subs = []
             for name in ("multimode_sphere", "full_box"):
@@ -590,13 +597,18 @@ def main():
                 r, s2, _, _ = time_workload(q, stream, 5, 3)
                 s2.close()
                 subs.append(r)
-            line["workloads"] = subs
-            line["single_sphere"] = single_sphere_record(stream)
-            line["demag"] = demag_record(stream)
+            return subs
+
+        if not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(p, args.cpu_seconds)
+        if not args.no_sub:
+            line["workloads"] = leg(sub_workloads)
+            line["single_sphere"] = leg(single_sphere_record, stream)
+            line["demag"] = leg(demag_record, stream)
         if not args.no_adjoint:
-            line["adjoint"] = adjoint_ratio(args.adjoint_T, args.adjoint_every, stream)
+            line["adjoint"] = leg(adjoint_ratio, args.adjoint_T, args.adjoint_every, stream)
         if not args.no_batch:
-            line["batch"] = batch_sweep(args.batch_n, args.batch_T, stream)
+            line["batch"] = leg(batch_sweep, args.batch_n, args.batch_T, stream)
         print(json.dumps(line))
     if world > 1:
         torch.distributed.destroy_process_group()
