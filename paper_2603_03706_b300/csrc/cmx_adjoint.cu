@@ -287,7 +287,9 @@ __device__ __forceinline__ void rev_cell(const AdjArgs &A, RevSmem<NS, WX, WY> &
             acc[n] = fmaf(un, bx, acc[n]);
             if (HU && A.ubar) {
                 float *ub = A.ubar + (size_t)n * nc + idx;
-                *ub += L.hrf[n] * bx + L.ovr[n] * mt[0] + L.ovi[n] * mt[1];
+                // fire-and-forget reduction: the cell's accumulator belongs to this thread in
+                // every stage, so the additions keep their order, and no load waits here
+                atomicAdd(ub, L.hrf[n] * bx + L.ovr[n] * mt[0] + L.ovi[n] * mt[1]);
             }
         }
     // outputs
