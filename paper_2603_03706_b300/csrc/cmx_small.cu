@@ -1,23 +1,38 @@
 // Single-block integrator for small grids (sm_103a).
 //
 // A grid of a few hundred to about a thousand magnetic cells (the 280-cell 8^3 sphere of the
-// single-mode Rabi and anticrossing runs of Sec. IV A-B) is integrated by ONE block of 256
-// threads that keeps, for every magnetic cell, m_n and the new state, the stage value, the seven
-// slopes, the error partial, the mode profiles and a neighbour table in shared memory.  A stage is
-// one block-wide pass over the cells (field, slope and the cell's next stage value; stage 2 also
-// a pass forming its stage values), the overlap sums are
-// block sums in shared memory with the same fixed-point digits as the multi-block reduction, and
-// the cavity update and the step-size controller are the engine's own (warp 0).  No stage touches
-// global memory except for the step log and the trace, and a stage costs two or three block
-// barriers instead of a grid barrier through L2.  The per-cell arithmetic is the tiled kernel's
-// (cell_slope, the same combine order), so the two integrate the same discrete system.
+// single-mode Rabi and anticrossing runs of Sec. IV A-B) is integrated by ONE block that keeps,
+// for every magnetic cell, m_n and the new state, the stage value, the seven slopes, the error
+// partial, the mode profiles and a neighbour table in shared memory.  No stage touches global
+// memory except for the step log and the trace.
+//
+// The block is split by warps.  Warp 0 runs the cavity update and the step-size controller (the
+// engine's own, in FP64: one cavity component per lane); warps 1.. (the workers) own the cells.
+// A stage S of the workers is two passes over their cells:
+//   A  the overlap partials of the stage values m_S (Eq. (18)), summed over the block as fixed-
+//      point integers (the same digits as the multi-block reduction, shared-memory atomics, so
+//      the totals do not depend on the order) -> handed to warp 0;
+//   B  once warp 0 has formed the stage's cavity value a_S and its feedback coefficients: the
+//      field, the slope and the cell's next stage value m_{S+1} (stage 6 also the error partial,
+//      stage 7 the new state and |e_m|).
+// The cavity slope of stage S needs only the overlap sums of pass A, so warp 0 runs the
+// controller of stage S while the workers run pass B of stage S and pass A of stage S + 1: the
+// FP64 cavity work, which occupies the FP64 pipe for tens of cycles per instruction, is hidden
+// behind the cell passes.  Two named barriers carry the hand-offs (sums ready: workers arrive,
+// warp 0 waits; feedback ready: warp 0 arrives, workers wait); the feedback coefficients and the
+// sums are double-buffered by stage parity.  Only the accept decision after stage 7 (which needs
+// the error maximum of pass B) is a full block barrier, once per attempt.  The per-cell
+// arithmetic is the tiled kernel's (cell_slope, the same combine order), so the two integrate
+// the same discrete system.
 #include "cmx_engine.cuh"
 #include "cmx_kernels.h"
 
 namespace cmx {
 
-constexpr int SMALL_NT = 256;
-constexpr int SMALL_NW = SMALL_NT / 32;
+constexpr int SMALL_NT = 320;               // warp 0 + nine worker warps
+constexpr int SMALL_WK = SMALL_NT - 32;     // worker threads (one cell each up to 288 cells)
+constexpr int BAR_SUMS = 1;                 // named barrier: a stage's overlap sums complete
+constexpr int BAR_FEED = 2;                 // named barrier: a stage's feedback coefficients set
 
 size_t small_smem_bytes(int nm, int nsub, int nmodes, bool has_u)
 {
@@ -26,23 +41,40 @@ size_t small_smem_bytes(int nm, int nsub, int nmodes, bool has_u)
            6 * (size_t)nm * sizeof(int);
 }
 
-// Block-level scratch of the overlap sums (fixed-point digits per warp, then per component in
-// units of 1 / red_scale) and of the error maximum.
+__device__ __forceinline__ void bar_sync_n(int id, int n)
+{
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+
+__device__ __forceinline__ void bar_arrive_n(int id, int n)
+{
+    asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+
+// Block-level scratch: the two int32 digits of the fixed-point overlap sums by stage parity
+// (see small_sums), the error maximum (bit pattern of a non-negative float; NaN is largest) and
+// the range flag.
 struct SmallRed {
-    int dig[SMALL_NW][2 * MAXN][2];
-    unsigned wmax[SMALL_NW];
-    long long sum[2 * MAXN];
+    int dig[2][2 * MAXN][2];
     unsigned emax;
     int bad;
 };
 
-// Block sums of the per-thread overlap accumulators and block max of |e_m|: each thread's FP32
+// Per-thread partials are scaled to at most 2^(SMALL_TBITS-1) in magnitude (a factor 2 of room
+// for stage values slightly off the unit sphere); one beyond 2^SMALL_TBITS is a range error, so
+// the block's integer digits stay inside int32 (SMALL_WK * 2^22 < 2^31).
+constexpr int SMALL_TBITS = 22;
+static_assert((long long)SMALL_WK << SMALL_TBITS < (1ll << 31), "digit sums must fit int32");
+
+// Workers: block sums of the per-thread overlap partials of one stage into dig[par].  Each
 // partial is scaled by L.tscale and split into two int32 digits (integer part and remainder in
-// units of 2^-20), summed exactly over the warp (redux) and the block (int64), and converted to
-// the grid units 1 / red_scale, exactly as the multi-block reduction forms one block's share.
-__device__ void small_block_sums(const Ctx &c, const Local &L, const Acc &acc, SmallRed &R)
+// units of 2^-20), summed exactly over the warp (redux); lane q adds component q's two warp
+// digits into the block's (integer atomics: exact, in any order).  A partial outside the range
+// (an unstable or non-finite state) sets `bad`.
+__device__ __forceinline__ void small_sums(const Ctx &c, const Local &L, const Acc &acc,
+                                           SmallRed &R, int par)
 {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
     const float ts = L.tscale;
     bool bad = false;
 #pragma unroll
@@ -51,36 +83,17 @@ __device__ void small_block_sums(const Ctx &c, const Local &L, const Acc &acc, S
 #pragma unroll
         for (int k = 0; k < 2; k++) {
             const float v = (k ? acc.im[n] : acc.re[n]) * ts;
-            bad |= !(fabsf(v) <= 16777216.f);
+            bad |= !(fabsf(v) <= (float)(1 << SMALL_TBITS));
             const float vh = rintf(v);
             const int dh = __reduce_add_sync(0xffffffffu, __float2int_rn(vh));
             const int dl = __reduce_add_sync(0xffffffffu, __float2int_rn((v - vh) * 1048576.f));
-            if (lane == 0) {
-                R.dig[warp][2 * n + k][0] = dh;
-                R.dig[warp][2 * n + k][1] = dl;
+            if (lane == 2 * n + k) {
+                atomicAdd(&R.dig[par][2 * n + k][0], dh);
+                atomicAdd(&R.dig[par][2 * n + k][1], dl);
             }
         }
     }
-    const unsigned e = __reduce_max_sync(0xffffffffu, __float_as_uint(acc.emax));
-    if (lane == 0) R.wmax[warp] = e;
     if (bad) atomicOr(&R.bad, 1);
-    __syncthreads();
-    if (threadIdx.x < 2 * c.nmodes) {
-        long long sh = 0, sl = 0;
-        for (int w = 0; w < SMALL_NW; w++) {
-            sh += R.dig[w][threadIdx.x][0];
-            sl += R.dig[w][threadIdx.x][1];
-        }
-        long long v = sh * (1ll << 20) + sl;
-        const int d = L.tshift;
-        R.sum[threadIdx.x] = d >= 0 ? v * (1ll << d) : (v + (1ll << (-d - 1))) >> (-d);
-    }
-    if (threadIdx.x == SMALL_NT - 1) {
-        unsigned m = 0u;
-        for (int w = 0; w < SMALL_NW; w++) m = max(m, R.wmax[w]);
-        R.emax = m;
-    }
-    __syncthreads();
 }
 
 struct SmallBuf {
@@ -91,42 +104,51 @@ struct SmallBuf {
     const int *nb;         // neighbours [-x, +x, -y, +y, -z, +z][cell], -1 = none
 };
 
-// One Dormand-Prince stage of all cells (see the file comment); the controller follows.
+// Workers (threads 32..): stage S of their cells (see the file comment).  `cw` holds the
+// attempt's coefficients and the feedback coefficients of stage S.  Stage 1 reads m_n, stage 2
+// m_2 = m_n + h a_21 k_1 (formed by the caller's pass).  Pass A reads only the worker's own
+// cells, and the feedback barrier between the passes orders every worker's stage values before
+// any neighbour read of pass B.  Stage 7 adds the workers' error maximum into R.emax.
 template <int NS, bool HU, int S>
-__device__ void small_stage(const Ctx &c, int nm, const SmallBuf &b, Local &L, Coef &cf,
-                            SmallRed &R)
+__device__ void small_work(const Ctx &c, int nm, const SmallBuf &b, const Local &L,
+                           const Coef &cw, SmallRed &R)
 {
     constexpr int NQ = 3 * NS;
-    const int tid = threadIdx.x;
+    const int wt = threadIdx.x - 32;
     const size_t V = (size_t)NQ * nm;
     const float *mn = L.mcur ? b.mb1 : b.mb0;
     float *mnew = L.mcur ? b.mb0 : b.mb1;
-    if (S <= 2) {
-        if (tid < 32) cavity_stage_value<S>(L, cf, tid, tid < 2 * c.nmodes);
-        if (S == 2 && tid >= 32 && tid < 32 + 36) attempt_coefficients(cf, L, L.h, tid - 32);
-        if (S == 2 && tid == 96) cf.h = (float)L.h;
-        __syncthreads();
-    }
-    // stage values: stage 2 forms m_2 = m_n + h a_21 k_1 in a pass of its own (the step size is
-    // known only when the attempt starts); stages 2..6 form the next stage value
-    // m_{S+1} = m_n + sum_{j<=S} (h a_{S+1,j}) k_j of their cell right after its slope (and stage
-    // 6 the error partial sum_{j<=6} E_j k_j), in the tiled kernel's order of operations, so
-    // stages 3..7 need no pass and no barrier before their field pass
     const float *src = S == 1 ? mn : b.ms[S & 1];
-    if (S == 2) {
-        for (int i = tid; i < nm; i += SMALL_NT)
+    {   // pass A: overlap partials of the stage values, in cell_slope's order of operations
+        Acc acc;
 #pragma unroll
-            for (int q = 0; q < NQ; q++)
-                b.ms[0][q * nm + i] =
-                    fmaf(cf.cf[1][0], b.kk[L.kphys[0] * V + q * nm + i], mn[q * nm + i]);
-        __syncthreads();
+        for (int n = 0; n < MAXN; n++) acc.re[n] = acc.im[n] = 0.f;
+        for (int i = wt; i < nm; i += SMALL_WK) {
+            float mt[2];
+#pragma unroll
+            for (int k = 0; k < 2; k++)
+                mt[k] = NS == 2 ? src[k * nm + i] + src[(3 + k) * nm + i] : src[k * nm + i];
+            const float hx = NS == 2 ? 0.5f * mt[0] : mt[0];
+            const float hy = NS == 2 ? 0.5f * mt[1] : mt[1];
+#pragma unroll
+            for (int n = 0; n < MAXN; n++) {
+                if (n >= c.nmodes) break;
+                const float un = HU ? b.uu[n * nm + i] : 1.f;
+                acc.re[n] = fmaf(un, hx, acc.re[n]);
+                acc.im[n] = fmaf(-un, hy, acc.im[n]);
+            }
+        }
+        small_sums(c, L, acc, R, S & 1);
     }
-    Acc acc;
+    bar_arrive_n(BAR_SUMS, SMALL_NT);
+    bar_sync_n(BAR_FEED, SMALL_NT);
+    // pass B: field, slope, next stage value
+    Acc acc;   // cell_slope's overlap partials are not used here (pass A formed them)
 #pragma unroll
     for (int n = 0; n < MAXN; n++) acc.re[n] = acc.im[n] = 0.f;
     acc.emax = 0.f;
     float *kout = b.kk + L.kphys[S - 1] * V;
-    for (int i = tid; i < nm; i += SMALL_NT) {
+    for (int i = wt; i < nm; i += SMALL_WK) {
         int nbr[6];
 #pragma unroll
         for (int d = 0; d < 6; d++) {
@@ -155,7 +177,7 @@ __device__ void small_stage(const Ctx &c, int nm, const SmallBuf &b, Local &L, C
         for (int n = 0; n < MAXN; n++) ucell[n] = (HU && n < c.nmodes) ? b.uu[n * nm + i] : 1.f;
         const float bdem[3] = {0.f, 0.f, 0.f};   // full demag runs on the tiled kernel
         float kv[NS][3];
-        cell_slope<NS, HU>(c, cf, m, B, ucell, bdem, acc, kv);
+        cell_slope<NS, HU>(c, cw, m, B, ucell, bdem, acc, kv);
 #pragma unroll
         for (int s = 0; s < NS; s++) {
 #pragma unroll
@@ -169,11 +191,11 @@ __device__ void small_stage(const Ctx &c, int nm, const SmallBuf &b, Local &L, C
                     for (int j = 0; j < S - 1; j++) {
                         if (dp_a(S, j) == 0.0 && !(S == 6 && dp_e(j) != 0.0)) continue;
                         const float kj = b.kk[L.kphys[j] * V + q * nm + i];
-                        if (dp_a(S, j) != 0.0) a = fmaf(cf.cf[S][j], kj, a);
-                        if (S == 6 && dp_e(j) != 0.0) e = fmaf(cf.e[j], kj, e);
+                        if (dp_a(S, j) != 0.0) a = fmaf(cw.cf[S][j], kj, a);
+                        if (S == 6 && dp_e(j) != 0.0) e = fmaf(cw.e[j], kj, e);
                     }
-                    b.ms[(S + 1) & 1][q * nm + i] = fmaf(cf.cf[S][S - 1], kv[s][k], a);
-                    if (S == 6) b.es[q * nm + i] = fmaf(cf.e[5], kv[s][k], e);
+                    b.ms[(S + 1) & 1][q * nm + i] = fmaf(cw.cf[S][S - 1], kv[s][k], a);
+                    if (S == 6) b.es[q * nm + i] = fmaf(cw.e[5], kv[s][k], e);
                 }
             }
             if (S == 7) {
@@ -183,19 +205,63 @@ __device__ void small_stage(const Ctx &c, int nm, const SmallBuf &b, Local &L, C
                 for (int k = 0; k < 3; k++) {
                     const int q = s * 3 + k;
                     mnew[q * nm + i] = mm[k] * r;
-                    const float e7 = cf.h * fmaf(cf.e[6], kv[s][k], b.es[q * nm + i]);
+                    const float e7 = cw.h * fmaf(cw.e[6], kv[s][k], b.es[q * nm + i]);
                     acc.emax = nanmax(acc.emax, fabsf(e7));
                 }
             }
         }
     }
-    small_block_sums(c, L, acc, R);
-    const long long sq = tid < 2 * c.nmodes ? R.sum[tid] : 0;
-    float emax = 0.f;
-    if (S == 7 && tid < 32) emax = R.bad ? __int_as_float(0x7fffffff) : __uint_as_float(R.emax);
-    const Team tm{0, 1, nullptr};
-    controller<S>(c, tm, L, cf, sq, emax);
-    __syncthreads();
+    if (S == 7) {
+        const unsigned e = __reduce_max_sync(0xffffffffu, __float_as_uint(acc.emax));
+        if ((threadIdx.x & 31) == 0) atomicMax(&R.emax, e);
+    }
+}
+
+// Warp 0, stage S: wait for the workers' overlap sums, take component q's digits (lane q < 2N),
+// clear them for stage S + 2 and convert the total to the grid units 1 / red_scale, release the
+// workers' pass B
+// (the stage's feedback coefficients were set before), then run the controller of stages
+// 1..6, which forms the next stage's cavity value and feedback coefficients into cfw[(S+1)&1].
+// Returns the lane's fixed-point sum (stage 7's controller runs after the block barrier).
+template <int S>
+__device__ long long small_control(const Ctx &c, Local &L, Coef *cfw, SmallRed &R)
+{
+    const int q = threadIdx.x;
+    bar_sync_n(BAR_SUMS, SMALL_NT);
+    long long sq = 0;
+    if (q < 2 * c.nmodes) {
+        const long long v = (long long)R.dig[S & 1][q][0] * (1ll << 20) + R.dig[S & 1][q][1];
+        R.dig[S & 1][q][0] = 0;
+        R.dig[S & 1][q][1] = 0;
+        const int d = L.tshift;
+        sq = d >= 0 ? v * (1ll << d) : (v + (1ll << (-d - 1))) >> (-d);
+    }
+    __syncwarp();
+    bar_arrive_n(BAR_FEED, SMALL_NT);
+    if (S < 7) {
+        const Team tm{0, 1, nullptr};
+        controller<S>(c, tm, L, cfw[(S + 1) & 1], sq, 0.f);
+        __syncwarp();
+    }
+    return sq;
+}
+
+// Warp 0, before stage 2 of an attempt (its size known, k_1 valid): the cavity value a_2 and
+// the feedback coefficients of stage 2 (into cfw[0]), the weights h a_Sj of the attempt and h,
+// copied into both coefficient sets.
+__device__ void small_attempt_setup(Local &L, Coef *cfw, int nmodes)
+{
+    const int q = threadIdx.x;
+    cavity_stage_value<2>(L, cfw[0], q, q < 2 * nmodes);
+    attempt_coefficients(cfw[0], L, L.h, q);
+    if (q < 4) attempt_coefficients(cfw[0], L, L.h, q + 32);
+    if (q == 0) cfw[0].h = (float)L.h;
+    __syncwarp();
+    float *d = &cfw[1].cf[0][0];
+    const float *s = &cfw[0].cf[0][0];
+    for (int k = q; k < 7 * 6; k += 32) d[k] = s[k];
+    if (q == 0) cfw[1].h = cfw[0].h;
+    __syncwarp();
 }
 
 struct SmallArgs {
@@ -210,12 +276,13 @@ __global__ void __launch_bounds__(SMALL_NT, 1) small_kernel(SmallArgs A)
 {
     extern __shared__ __align__(16) float sh[];
     __shared__ Local L;
-    __shared__ Coef cf;
+    __shared__ Coef cfw[2];   // coefficients; feedback of the stages of parity 0 / 1
     __shared__ SmallRed R;
     __shared__ int s_stop;
     constexpr int NQ = 3 * NS;
     const Ctx &c = A.c;
     const int nm = A.nm, tid = threadIdx.x;
+    const bool ctl = tid < 32;
     const size_t V = (size_t)NQ * nm;
     SmallBuf b;
     b.mb0 = sh;
@@ -239,16 +306,19 @@ __global__ void __launch_bounds__(SMALL_NT, 1) small_kernel(SmallArgs A)
             if (u < c.nmodes && c.kerr[u] != 0.0) hk = 1;
         L.has_kerr = hk;
         L.has_split = c.split_dt > 0.0;
-        // fixed-point scale of the per-thread overlap partials (ceil(nm / 256) cells each)
-        const int P = (nm + SMALL_NT - 1) / SMALL_NT;
+        // fixed-point scale of the per-thread overlap partials (ceil(nm / workers) cells each)
+        const int P = (nm + SMALL_WK - 1) / SMALL_WK;
         const float bound = 2.f * (float)(P > 1 ? P : 1) * fmaxf(c.umax, 1.f);
-        const int k = 24 - (int)ceilf(log2f(bound));
+        const int k = SMALL_TBITS - (int)ceilf(log2f(bound));
         L.tscale = ldexpf(1.f, k);
         L.tshift = ilogb(c.red_scale) - k - 20;
+        R.emax = 0u;
         R.bad = 0;
     }
+    if (tid < 2 * 2 * MAXN) R.dig[tid / (2 * MAXN)][tid % (2 * MAXN)][0] =
+                             R.dig[tid / (2 * MAXN)][tid % (2 * MAXN)][1] = 0;
     if (tid < 2 * c.nmodes) component_constants(c, tid, L);
-    if (tid >= 32 && tid < 39) cf.e[tid - 32] = (float)dp_e(tid - 32);
+    if (tid >= 32 && tid < 39) cfw[0].e[tid - 32] = cfw[1].e[tid - 32] = (float)dp_e(tid - 32);
     if (tid < c.nmodes) mode_constants(c, tid, L.mc + MC * tid);
     __syncthreads();
     {   // state, FSAL slope, profiles and neighbour table into shared memory
@@ -272,21 +342,65 @@ __global__ void __launch_bounds__(SMALL_NT, 1) small_kernel(SmallArgs A)
             for (int d = 0; d < 6; d++) nb[d * nm + i] = __ldg(A.snb + d * nm + i);
         }
     }
-    __syncthreads();
+    // Every thread passes the same sequence of block barriers (__syncthreads: attempt start,
+    // end of stage 1, end of stage 7) and, per stage, one sums and one feedback barrier; the
+    // loop conditions (s_stop, L.k1_valid) are read after a block barrier that follows their
+    // last write.
+    long long sq7 = 0;
     for (;;) {
-        if (tid == 0) {
-            s_stop = L.status != 0 || L.done;
-            if (!s_stop) attempt_size(c, L);
+        if (ctl) {   // warp 0: stage 7's controller of the previous attempt, next attempt's size
+            if (tid == 0) {
+                s_stop = L.status != 0 || L.done;
+                if (!s_stop) attempt_size(c, L);
+            }
+            __syncwarp();
+            if (!s_stop && L.k1_valid) small_attempt_setup(L, cfw, c.nmodes);
         }
         __syncthreads();
         if (s_stop) break;
-        while (!L.k1_valid) small_stage<NS, HU, 1>(c, nm, b, L, cf, R);   // twice at a split boundary
-        small_stage<NS, HU, 2>(c, nm, b, L, cf, R);
-        small_stage<NS, HU, 3>(c, nm, b, L, cf, R);
-        small_stage<NS, HU, 4>(c, nm, b, L, cf, R);
-        small_stage<NS, HU, 5>(c, nm, b, L, cf, R);
-        small_stage<NS, HU, 6>(c, nm, b, L, cf, R);
-        small_stage<NS, HU, 7>(c, nm, b, L, cf, R);
+        while (!L.k1_valid) {   // twice at an operator-split boundary (see controller<1>)
+            if (ctl) {
+                cavity_stage_value<1>(L, cfw[1], tid, tid < 2 * c.nmodes);
+                small_control<1>(c, L, cfw, R);
+                if (L.k1_valid) small_attempt_setup(L, cfw, c.nmodes);
+            } else {
+                small_work<NS, HU, 1>(c, nm, b, L, cfw[1], R);
+            }
+            __syncthreads();
+        }
+        if (ctl) {
+            small_control<2>(c, L, cfw, R);
+            small_control<3>(c, L, cfw, R);
+            small_control<4>(c, L, cfw, R);
+            small_control<5>(c, L, cfw, R);
+            small_control<6>(c, L, cfw, R);
+            sq7 = small_control<7>(c, L, cfw, R);
+        } else {
+            {   // m_2 = m_n + h a_21 k_1 of the worker's own cells
+                const float *mn = L.mcur ? b.mb1 : b.mb0;
+                const float *k1 = b.kk + L.kphys[0] * V;
+                const float c21 = cfw[0].cf[1][0];
+                for (int i = tid - 32; i < nm; i += SMALL_WK)
+#pragma unroll
+                    for (int q = 0; q < NQ; q++)
+                        b.ms[0][q * nm + i] = fmaf(c21, k1[q * nm + i], mn[q * nm + i]);
+            }
+            small_work<NS, HU, 2>(c, nm, b, L, cfw[0], R);
+            small_work<NS, HU, 3>(c, nm, b, L, cfw[1], R);
+            small_work<NS, HU, 4>(c, nm, b, L, cfw[0], R);
+            small_work<NS, HU, 5>(c, nm, b, L, cfw[1], R);
+            small_work<NS, HU, 6>(c, nm, b, L, cfw[0], R);
+            small_work<NS, HU, 7>(c, nm, b, L, cfw[1], R);
+        }
+        __syncthreads();
+        if (ctl) {   // accept decision: the workers' error maximum is complete
+            const float emax = R.bad ? __int_as_float(0x7fffffff) : __uint_as_float(R.emax);
+            __syncwarp();
+            if (tid == 0) R.emax = 0u;
+            const Team tm{0, 1, nullptr};
+            controller<7>(c, tm, L, cfw[1], sq7, emax);
+            __syncwarp();
+        }
     }
     // write back: control block, state and FSAL slope
     if (tid == 0) store_local(c, L);
