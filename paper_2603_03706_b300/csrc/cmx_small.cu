@@ -217,6 +217,124 @@ __device__ void small_work(const Ctx &c, int nm, const SmallBuf &b, const Local 
     }
 }
 
+// Register state of a worker's cell when every worker owns at most one cell (nm <= SMALL_WK):
+// the cell's m_n, current stage value, the seven slopes of the attempt by stage (k[j] = k_{j+1};
+// the FSAL swap is a copy), the error partial, the normalised stage-7 value (the new state if
+// the attempt is accepted), its profile values and neighbour table.  Only the stage values that
+// neighbours read (and the state, for stage 1 and the write-back) go through shared memory.
+template <int NS>
+struct CellReg {
+    float mn[3 * NS], ms[3 * NS], k[7][3 * NS], es[3 * NS], m7[3 * NS];
+    float u[MAXN];
+    int nbr[6];
+    int mcur;
+};
+
+// small_work for one cell per worker with the cell's state in registers (see CellReg); the same
+// operations in the same order as small_work.
+template <int NS, bool HU, int S>
+__device__ __forceinline__ void small_work_reg(const Ctx &c, int nm, const SmallBuf &b,
+                                               const Local &L, const Coef &cw, SmallRed &R,
+                                               CellReg<NS> &r)
+{
+    const int i = threadIdx.x - 32;
+    const bool own = i < nm;
+    const float *mn = L.mcur ? b.mb1 : b.mb0;
+    float *mnew = L.mcur ? b.mb0 : b.mb1;
+    const float *src = S == 1 ? mn : b.ms[S & 1];
+    const float(&mc)[3 * NS] = S == 1 ? r.mn : r.ms;   // the cell's own stage value
+    {   // pass A
+        Acc acc;
+#pragma unroll
+        for (int n = 0; n < MAXN; n++) acc.re[n] = acc.im[n] = 0.f;
+        if (own) {
+            float mt[2];
+#pragma unroll
+            for (int k = 0; k < 2; k++) mt[k] = NS == 2 ? mc[k] + mc[3 + k] : mc[k];
+            const float hx = NS == 2 ? 0.5f * mt[0] : mt[0];
+            const float hy = NS == 2 ? 0.5f * mt[1] : mt[1];
+#pragma unroll
+            for (int n = 0; n < MAXN; n++) {
+                if (n >= c.nmodes) break;
+                const float un = HU ? r.u[n] : 1.f;
+                acc.re[n] = fmaf(un, hx, acc.re[n]);
+                acc.im[n] = fmaf(-un, hy, acc.im[n]);
+            }
+        }
+        small_sums(c, L, acc, R, S & 1);
+    }
+    bar_arrive_n(BAR_SUMS, SMALL_NT);
+    bar_sync_n(BAR_FEED, SMALL_NT);
+    Acc acc;
+#pragma unroll
+    for (int n = 0; n < MAXN; n++) acc.re[n] = acc.im[n] = 0.f;
+    acc.emax = 0.f;
+    if (own) {
+        const float nx_ = (float)(r.nbr[0] >= 0) + (float)(r.nbr[1] >= 0);
+        const float ny_ = (float)(r.nbr[2] >= 0) + (float)(r.nbr[3] >= 0);
+        const float nz_ = (float)(r.nbr[4] >= 0) + (float)(r.nbr[5] >= 0);
+        float m[NS][3], B[NS][3];
+#pragma unroll
+        for (int s = 0; s < NS; s++)
+#pragma unroll
+            for (int k = 0; k < 3; k++) {
+                const float *v = src + (s * 3 + k) * nm;
+                const float cen = mc[s * 3 + k];
+                float nv[6];
+#pragma unroll
+                for (int d = 0; d < 6; d++) nv[d] = r.nbr[d] >= 0 ? v[r.nbr[d]] : 0.f;
+                m[s][k] = cen;
+                B[s][k] = c.wx * (nv[0] + nv[1] - nx_ * cen) + c.wy * (nv[2] + nv[3] - ny_ * cen) +
+                          c.wz * (nv[4] + nv[5] - nz_ * cen);
+            }
+        float ucell[MAXN];
+#pragma unroll
+        for (int n = 0; n < MAXN; n++) ucell[n] = (HU && n < c.nmodes) ? r.u[n] : 1.f;
+        const float bdem[3] = {0.f, 0.f, 0.f};
+        float kv[NS][3];
+        cell_slope<NS, HU>(c, cw, m, B, ucell, bdem, acc, kv);
+#pragma unroll
+        for (int s = 0; s < NS; s++) {
+#pragma unroll
+            for (int k = 0; k < 3; k++) r.k[S - 1][s * 3 + k] = kv[s][k];
+            if (S >= 2 && S <= 6) {
+#pragma unroll
+                for (int k = 0; k < 3; k++) {
+                    const int q = s * 3 + k;
+                    float a = r.mn[q], e = 0.f;
+#pragma unroll
+                    for (int j = 0; j < S - 1; j++) {
+                        if (dp_a(S, j) == 0.0 && !(S == 6 && dp_e(j) != 0.0)) continue;
+                        const float kj = r.k[j][q];
+                        if (dp_a(S, j) != 0.0) a = fmaf(cw.cf[S][j], kj, a);
+                        if (S == 6 && dp_e(j) != 0.0) e = fmaf(cw.e[j], kj, e);
+                    }
+                    const float nxt = fmaf(cw.cf[S][S - 1], kv[s][k], a);
+                    r.ms[q] = nxt;
+                    b.ms[(S + 1) & 1][q * nm + i] = nxt;
+                    if (S == 6) r.es[q] = fmaf(cw.e[5], kv[s][k], e);
+                }
+            }
+            if (S == 7) {
+                const float *mm = m[s];
+                const float rn = rsqrtf(mm[0] * mm[0] + mm[1] * mm[1] + mm[2] * mm[2]);
+#pragma unroll
+                for (int k = 0; k < 3; k++) {
+                    const int q = s * 3 + k;
+                    r.m7[q] = mm[k] * rn;
+                    mnew[q * nm + i] = r.m7[q];
+                    const float e7 = cw.h * fmaf(cw.e[6], kv[s][k], r.es[q]);
+                    acc.emax = nanmax(acc.emax, fabsf(e7));
+                }
+            }
+        }
+    }
+    if (S == 7) {
+        const unsigned e = __reduce_max_sync(0xffffffffu, __float_as_uint(acc.emax));
+        if ((threadIdx.x & 31) == 0) atomicMax(&R.emax, e);
+    }
+}
+
 // Warp 0, stage S: wait for the workers' overlap sums, take component q's digits (lane q < 2N),
 // clear them for stage S + 2 and convert the total to the grid units 1 / red_scale, release the
 // workers' pass B
@@ -271,7 +389,8 @@ struct SmallArgs {
     int nm;
 };
 
-template <int NS, bool HU>
+// ONE: every worker owns at most one cell, whose state stays in registers (small_work_reg).
+template <int NS, bool HU, bool ONE>
 __global__ void __launch_bounds__(SMALL_NT, 1) small_kernel(SmallArgs A)
 {
     extern __shared__ __align__(16) float sh[];
@@ -342,6 +461,28 @@ __global__ void __launch_bounds__(SMALL_NT, 1) small_kernel(SmallArgs A)
             for (int d = 0; d < 6; d++) nb[d * nm + i] = __ldg(A.snb + d * nm + i);
         }
     }
+    CellReg<NS> r;   // workers' cell in registers (ONE)
+    if (ONE) {
+        __syncthreads();
+        const int i = tid - 32;
+        r.mcur = L.mcur;
+        if (!ctl && i < nm) {
+            const float *mn = L.mcur ? b.mb1 : b.mb0;
+            const float *k1 = b.kk + L.kphys[0] * V;
+#pragma unroll
+            for (int q = 0; q < NQ; q++) {
+                r.mn[q] = mn[q * nm + i];
+                r.k[0][q] = k1[q * nm + i];
+            }
+#pragma unroll
+            for (int n = 0; n < MAXN; n++) r.u[n] = (HU && n < c.nmodes) ? b.uu[n * nm + i] : 1.f;
+#pragma unroll
+            for (int d = 0; d < 6; d++) {
+                r.nbr[d] = nb[d * nm + i];
+                if (r.nbr[d] >= 0 && !idx_ok(c, r.nbr[d], nm, 14)) r.nbr[d] = -1;
+            }
+        }
+    }
     // Every thread passes the same sequence of block barriers (__syncthreads: attempt start,
     // end of stage 1, end of stage 7) and, per stage, one sums and one feedback barrier; the
     // loop conditions (s_stop, L.k1_valid) are read after a block barrier that follows their
@@ -357,12 +498,22 @@ __global__ void __launch_bounds__(SMALL_NT, 1) small_kernel(SmallArgs A)
             if (!s_stop && L.k1_valid) small_attempt_setup(L, cfw, c.nmodes);
         }
         __syncthreads();
+        if (ONE && !ctl && L.mcur != r.mcur) {   // the last attempt was accepted: FSAL
+            r.mcur = L.mcur;
+#pragma unroll
+            for (int q = 0; q < NQ; q++) {
+                r.mn[q] = r.m7[q];
+                r.k[0][q] = r.k[6][q];
+            }
+        }
         if (s_stop) break;
         while (!L.k1_valid) {   // twice at an operator-split boundary (see controller<1>)
             if (ctl) {
                 cavity_stage_value<1>(L, cfw[1], tid, tid < 2 * c.nmodes);
                 small_control<1>(c, L, cfw, R);
                 if (L.k1_valid) small_attempt_setup(L, cfw, c.nmodes);
+            } else if (ONE) {
+                small_work_reg<NS, HU, 1>(c, nm, b, L, cfw[1], R, r);
             } else {
                 small_work<NS, HU, 1>(c, nm, b, L, cfw[1], R);
             }
@@ -375,6 +526,22 @@ __global__ void __launch_bounds__(SMALL_NT, 1) small_kernel(SmallArgs A)
             small_control<5>(c, L, cfw, R);
             small_control<6>(c, L, cfw, R);
             sq7 = small_control<7>(c, L, cfw, R);
+        } else if (ONE) {
+            const int i = tid - 32;
+            const float c21 = cfw[0].cf[1][0];
+            if (i < nm) {
+#pragma unroll
+                for (int q = 0; q < NQ; q++) {
+                    r.ms[q] = fmaf(c21, r.k[0][q], r.mn[q]);
+                    b.ms[0][q * nm + i] = r.ms[q];
+                }
+            }
+            small_work_reg<NS, HU, 2>(c, nm, b, L, cfw[0], R, r);
+            small_work_reg<NS, HU, 3>(c, nm, b, L, cfw[1], R, r);
+            small_work_reg<NS, HU, 4>(c, nm, b, L, cfw[0], R, r);
+            small_work_reg<NS, HU, 5>(c, nm, b, L, cfw[1], R, r);
+            small_work_reg<NS, HU, 6>(c, nm, b, L, cfw[0], R, r);
+            small_work_reg<NS, HU, 7>(c, nm, b, L, cfw[1], R, r);
         } else {
             {   // m_2 = m_n + h a_21 k_1 of the worker's own cells
                 const float *mn = L.mcur ? b.mb1 : b.mb0;
@@ -415,8 +582,14 @@ __global__ void __launch_bounds__(SMALL_NT, 1) small_kernel(SmallArgs A)
 #pragma unroll
             for (int q = 0; q < NQ; q++) {
                 gm[(size_t)q * c.ncell + si] = mn[q * nm + i];
-                if (L.k1_valid) gk1[(size_t)q * c.ncell + si] = k1[q * nm + i];
+                if (!ONE && L.k1_valid) gk1[(size_t)q * c.ncell + si] = k1[q * nm + i];
             }
+        }
+        if (ONE && !ctl && tid - 32 < nm && L.k1_valid) {
+            const int i = tid - 32, si = __ldg(A.sidx + i);
+            if (idx_ok(c, si, c.ncell, 16))
+#pragma unroll
+                for (int q = 0; q < NQ; q++) gk1[(size_t)q * c.ncell + si] = r.k[0][q];
         }
     }
 }
@@ -424,7 +597,7 @@ __global__ void __launch_bounds__(SMALL_NT, 1) small_kernel(SmallArgs A)
 template <int NS, bool HU>
 static cudaError_t small_launch_variant(const SmallArgs &a, cudaStream_t s)
 {
-    auto *fn = small_kernel<NS, HU>;
+    auto *fn = a.nm <= SMALL_WK ? small_kernel<NS, HU, true> : small_kernel<NS, HU, false>;
     const size_t smem = small_smem_bytes(a.nm, NS, a.c.nmodes, HU);
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
