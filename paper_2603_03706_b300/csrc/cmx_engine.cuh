@@ -335,17 +335,26 @@ __device__ __forceinline__ void attempt_coefficients(Coef &cf, Local &L, double 
 // rank 0 writes log, trace and adjoint stores.  An FP64 warp instruction occupies the FP64 pipe
 // for tens of cycles on this GPU whatever the number of active lanes, so the part is written
 // for few FP64 instructions (one component per lane, per-lane constants, no block barrier).
+//
+// The controller in two parts: controller_cavity<S> is the cavity work of stage S (everything of
+// stages 1..6; at stage 7 the cavity slope k_7 and the scaled cavity error norm, which need no
+// magnet data), controller_decide the accept decision of stage 7, which needs the magnet's error
+// maximum.  Both run on all lanes of warp 0; controller<S> runs them back to back, the
+// single-block integrator overlaps the first with the magnet's last pass.
+struct Cav7 {
+    double y, d;   // the lane's overlap component and cavity slope of stage 7
+    float e2;      // scaled cavity error norm (every lane)
+};
+
 template <int S>
-__device__ void controller(const Ctx &c, const Team &tm, Local &L, Coef &cf, long long sq,
-                           float emax)
+__device__ __forceinline__ Cav7 controller_cavity(const Ctx &c, const Team &tm, Local &L,
+                                                  Coef &cf, long long sq)
 {
     const int N = c.nmodes;
     const int q = threadIdx.x;
-    if (q >= 32) return;
     __syncwarp();   // the lanes' shuffles below need the whole warp at the same point
     const bool own = q < 2 * N;
     const bool rec = tm.rank == 0;
-    const long long li = L.log_n;
     const double y = own ? (double)sq * L.rs : 0.0;
     const double yo = __shfl_xor_sync(0xffffffffu, y, 1);
     double d = 0.0;
@@ -406,7 +415,7 @@ __device__ void controller(const Ctx &c, const Team &tm, Local &L, Coef &cf, lon
                 L.k1_valid = 0;
             }
         }
-        return;
+        return Cav7{0.0, 0.0, 0.f};
     }
 
     // stage 7: error estimate of the lane's component; magnitudes in FP32 (they only scale the
@@ -429,8 +438,20 @@ __device__ void controller(const Ctx &c, const Team &tm, Local &L, Coef &cf, lon
         an = fmaxf(an, __shfl_xor_sync(0xffffffffu, an, o));
     }
     // scaled error norm: magnet max-norm against rtol, cavity against rtol max(a_ref, |a|)
+    return Cav7{y, d, en / (L.rtolf * fmaxf(L.areff, an))};
+}
+
+__device__ __forceinline__ void controller_decide(const Ctx &c, const Team &tm, Local &L,
+                                                  const Cav7 &v, float emax)
+{
+    const int N = c.nmodes;
+    const int q = threadIdx.x;
+    const bool own = q < 2 * N;
+    const bool rec = tm.rank == 0;
+    const long long li = L.log_n;
+    const double y = v.y, d = v.d;
     const float e1 = emax * L.inv_rtolf;
-    const float e2 = en / (L.rtolf * fmaxf(L.areff, an));
+    const float e2 = v.e2;
     const float err = (e1 > e2 || e1 != e1) ? e1 : e2;
     const bool finite = isfinite(err);
     const int accepted = finite && L.status == 0 && (L.replay || err <= 1.f);
@@ -526,6 +547,15 @@ __device__ void controller(const Ctx &c, const Team &tm, Local &L, Coef &cf, lon
         L.ka[0][q] = d;
         L.mm_n[q] = y;
     }
+}
+
+template <int S>
+__device__ __forceinline__ void controller(const Ctx &c, const Team &tm, Local &L, Coef &cf,
+                                           long long sq, float emax)
+{
+    if (threadIdx.x >= 32) return;
+    const Cav7 v = controller_cavity<S>(c, tm, L, cf, sq);
+    if (S == 7) controller_decide(c, tm, L, v, emax);
 }
 
 // Block sum of the per-thread overlap accumulators and block max of |e_m|, added into

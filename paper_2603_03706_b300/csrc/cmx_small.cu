@@ -337,10 +337,9 @@ __device__ __forceinline__ void small_work_reg(const Ctx &c, int nm, const Small
 
 // Warp 0, stage S: wait for the workers' overlap sums, take component q's digits (lane q < 2N),
 // clear them for stage S + 2 and convert the total to the grid units 1 / red_scale, release the
-// workers' pass B
-// (the stage's feedback coefficients were set before), then run the controller of stages
-// 1..6, which forms the next stage's cavity value and feedback coefficients into cfw[(S+1)&1].
-// Returns the lane's fixed-point sum (stage 7's controller runs after the block barrier).
+// workers' pass B (the stage's feedback coefficients were set before), then run the controller
+// of stages 1..6, which forms the next stage's cavity value and feedback coefficients into
+// cfw[(S+1)&1].  Returns the lane's fixed-point sum (the caller runs stage 7's controller).
 template <int S>
 __device__ long long small_control(const Ctx &c, Local &L, Coef *cfw, SmallRed &R)
 {
@@ -487,9 +486,9 @@ __global__ void __launch_bounds__(SMALL_NT, 1) small_kernel(SmallArgs A)
     // end of stage 1, end of stage 7) and, per stage, one sums and one feedback barrier; the
     // loop conditions (s_stop, L.k1_valid) are read after a block barrier that follows their
     // last write.
-    long long sq7 = 0;
+    Cav7 cav7{0.0, 0.0, 0.f};
     for (;;) {
-        if (ctl) {   // warp 0: stage 7's controller of the previous attempt, next attempt's size
+        if (ctl) {   // warp 0: the next attempt's size and its stage-2 set-up
             if (tid == 0) {
                 s_stop = L.status != 0 || L.done;
                 if (!s_stop) attempt_size(c, L);
@@ -525,7 +524,10 @@ __global__ void __launch_bounds__(SMALL_NT, 1) small_kernel(SmallArgs A)
             small_control<4>(c, L, cfw, R);
             small_control<5>(c, L, cfw, R);
             small_control<6>(c, L, cfw, R);
-            sq7 = small_control<7>(c, L, cfw, R);
+            // stage 7's cavity slope and cavity error norm while the workers run pass B
+            const Team tm{0, 1, nullptr};
+            cav7 = controller_cavity<7>(c, tm, L, cfw[1], small_control<7>(c, L, cfw, R));
+            __syncwarp();
         } else if (ONE) {
             const int i = tid - 32;
             const float c21 = cfw[0].cf[1][0];
@@ -565,7 +567,7 @@ __global__ void __launch_bounds__(SMALL_NT, 1) small_kernel(SmallArgs A)
             __syncwarp();
             if (tid == 0) R.emax = 0u;
             const Team tm{0, 1, nullptr};
-            controller<7>(c, tm, L, cfw[1], sq7, emax);
+            controller_decide(c, tm, L, cav7, emax);
             __syncwarp();
         }
     }
