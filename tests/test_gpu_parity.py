@@ -166,6 +166,43 @@ def test_single_block_integrator_1000_steps(case):
     assert dm <= TOL_M and da <= TOL_A, (dm, da, info["derr"])
 
 
+def boundary_problem(ncells, nsub):
+    """A 10 x 8 x 4 box whose first `ncells` cells (x fastest) are magnetic: 288 cells is the
+    largest grid whose cells the single-block integrator keeps one per worker thread in
+    registers, 289 the smallest that takes the shared-memory form."""
+    nx, ny, nz = 10, 8, 4
+    mask = np.zeros(nx * ny * nz, np.uint8)
+    mask[:ncells] = 1
+    mask = mask.reshape(nz, ny, nx)
+    rng = np.random.default_rng(ncells + 7 * nsub)
+    u = rng.uniform(-1, 1, (2, nz, ny, nx)).astype(np.float32)
+    kw = dict(omega=TP * np.array([4.95e9, 5.05e9]), kappa=TP * np.array([2e6, 3e6]),
+              g_re=TP * np.array([40e6, 30e6]), g_im=TP * np.array([0.0, 15e6]), u=u,
+              a0=np.array([1e-3, 5e-4j]), T=1e-6)
+    if nsub == 2:
+        p = W.make_problem(nx, ny, nz, 2e-9, mask, nsub=2, Ms=4e5, Aex=5e-12, alpha=2e-3,
+                           Ku=5e4, B0=(0, 0, 1.0), Nd=(0, 0, 1), BE=50.0,
+                           m0=W.random_state(2, nx, ny, nz, 3, spread=0.05, afm=True), **kw)
+    else:
+        p = W.make_problem(nx, ny, nz, 5e-9, mask, Ku=-610.0, ku_axis=(0.6, 0.0, 0.8),
+                           B0=(0.01, 0, 0.187), Nd=(0.3, 0.3, 0.4),
+                           m0=W.tilted_state(1, nx, ny, nz, 4.0, 0.2), **kw)
+    return p.replace(dt_max=W.stable_dt_max(p))
+
+
+@pytest.mark.parametrize("nsub", [1, 2])
+@pytest.mark.parametrize("ncells", [288, 289])
+def test_single_block_register_and_shared_forms(ncells, nsub):
+    """Both forms of the single-block integrator at the boundary between them (288 cells: one
+    cell per worker, state in registers; 289: cells in shared memory), with profiles and a
+    complex coupling: 1000 replayed attempts against the oracle."""
+    p = boundary_problem(ncells, nsub)
+    assert int(p.mask.sum()) == ncells
+    dm, da, info = replay_compare(p, 1000)
+    assert info["tiling"]["blocks"] == 1 and info["tiling"]["bx"] == 0, info["tiling"]
+    assert dm <= TOL_M and da <= TOL_A, (dm, da, info["derr"])
+
+
 def test_single_block_and_tiled_kernels_agree():
     """The same 8^3 sphere on the single-block integrator and on the tiled multi-block kernel
     (tile forced): both replays match the oracle."""
