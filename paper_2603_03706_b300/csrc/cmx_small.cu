@@ -7,7 +7,9 @@
 // memory except for the step log and the trace.
 //
 // The block is split by warps.  Warp 0 runs the cavity update and the step-size controller (the
-// engine's own, in FP64: one cavity component per lane); warps 1.. (the workers) own the cells.
+// engine's own, in FP64: one cavity component per lane), warp 1 (the helper) the part of the
+// cavity update of stages 2..6 that needs no overlap sums (small_prepare); warps 2.. (the
+// workers) own the cells.
 // A stage S of the workers is two passes over their cells:
 //   A  the overlap partials of the stage values m_S (Eq. (18)), summed over the block as fixed-
 //      point integers (the same digits as the multi-block reduction, shared-memory atomics, so
@@ -29,10 +31,15 @@
 
 namespace cmx {
 
-constexpr int SMALL_NT = 320;               // warp 0 + nine worker warps
-constexpr int SMALL_WK = SMALL_NT - 32;     // worker threads (one cell each up to 288 cells)
-constexpr int BAR_SUMS = 1;                 // named barrier: a stage's overlap sums complete
-constexpr int BAR_FEED = 2;                 // named barrier: a stage's feedback coefficients set
+constexpr int SMALL_NT = 352;               // warp 0, warp 1 (helper), nine worker warps
+constexpr int SMALL_W0 = 64;                // first worker thread
+constexpr int SMALL_WK = SMALL_NT - SMALL_W0;   // worker threads (one cell each up to 288 cells)
+// named barriers: warp 0 with the workers (SMALL_WK + 32 threads) and warp 0 with the helper (64)
+constexpr int BAR_SUMS = 1;                 // a stage's overlap sums complete (workers arrive)
+constexpr int BAR_FEED = 2;                 // a stage's feedback coefficients set (warp 0 arrives)
+constexpr int BAR_PRE = 3;                  // the helper's part of a stage's cavity update ready
+constexpr int BAR_HELP = 4;                 // the previous stage's cavity update done (warp 0)
+constexpr int BAR_CW = SMALL_WK + 32;
 
 size_t small_smem_bytes(int nm, int nsub, int nmodes, bool has_u)
 {
@@ -104,7 +111,7 @@ struct SmallBuf {
     const int *nb;         // neighbours [-x, +x, -y, +y, -z, +z][cell], -1 = none
 };
 
-// Workers (threads 32..): stage S of their cells (see the file comment).  `cw` holds the
+// Workers (threads SMALL_W0..): stage S of their cells (see the file comment).  `cw` holds the
 // attempt's coefficients and the feedback coefficients of stage S.  Stage 1 reads m_n, stage 2
 // m_2 = m_n + h a_21 k_1 (formed by the caller's pass).  Pass A reads only the worker's own
 // cells, and the feedback barrier between the passes orders every worker's stage values before
@@ -114,7 +121,7 @@ __device__ void small_work(const Ctx &c, int nm, const SmallBuf &b, const Local 
                            const Coef &cw, SmallRed &R)
 {
     constexpr int NQ = 3 * NS;
-    const int wt = threadIdx.x - 32;
+    const int wt = threadIdx.x - SMALL_W0;
     const size_t V = (size_t)NQ * nm;
     const float *mn = L.mcur ? b.mb1 : b.mb0;
     float *mnew = L.mcur ? b.mb0 : b.mb1;
@@ -140,8 +147,8 @@ __device__ void small_work(const Ctx &c, int nm, const SmallBuf &b, const Local 
         }
         small_sums(c, L, acc, R, S & 1);
     }
-    bar_arrive_n(BAR_SUMS, SMALL_NT);
-    bar_sync_n(BAR_FEED, SMALL_NT);
+    bar_arrive_n(BAR_SUMS, BAR_CW);
+    bar_sync_n(BAR_FEED, BAR_CW);
     // pass B: field, slope, next stage value
     Acc acc;   // cell_slope's overlap partials are not used here (pass A formed them)
 #pragma unroll
@@ -237,7 +244,7 @@ __device__ __forceinline__ void small_work_reg(const Ctx &c, int nm, const Small
                                                const Local &L, const Coef &cw, SmallRed &R,
                                                CellReg<NS> &r)
 {
-    const int i = threadIdx.x - 32;
+    const int i = threadIdx.x - SMALL_W0;
     const bool own = i < nm;
     const float *mn = L.mcur ? b.mb1 : b.mb0;
     float *mnew = L.mcur ? b.mb0 : b.mb1;
@@ -263,8 +270,8 @@ __device__ __forceinline__ void small_work_reg(const Ctx &c, int nm, const Small
         }
         small_sums(c, L, acc, R, S & 1);
     }
-    bar_arrive_n(BAR_SUMS, SMALL_NT);
-    bar_sync_n(BAR_FEED, SMALL_NT);
+    bar_arrive_n(BAR_SUMS, BAR_CW);
+    bar_sync_n(BAR_FEED, BAR_CW);
     Acc acc;
 #pragma unroll
     for (int n = 0; n < MAXN; n++) acc.re[n] = acc.im[n] = 0.f;
@@ -344,7 +351,7 @@ template <int S>
 __device__ long long small_control(const Ctx &c, Local &L, Coef *cfw, SmallRed &R)
 {
     const int q = threadIdx.x;
-    bar_sync_n(BAR_SUMS, SMALL_NT);
+    bar_sync_n(BAR_SUMS, BAR_CW);
     long long sq = 0;
     if (q < 2 * c.nmodes) {
         const long long v = (long long)R.dig[S & 1][q][0] * (1ll << 20) + R.dig[S & 1][q][1];
@@ -354,13 +361,111 @@ __device__ long long small_control(const Ctx &c, Local &L, Coef *cfw, SmallRed &
         sq = d >= 0 ? v * (1ll << d) : (v + (1ll << (-d - 1))) >> (-d);
     }
     __syncwarp();
-    bar_arrive_n(BAR_FEED, SMALL_NT);
+    bar_arrive_n(BAR_FEED, BAR_CW);
     if (S < 7) {
         const Team tm{0, 1, nullptr};
         controller<S>(c, tm, L, cfw[(S + 1) & 1], sq, 0.f);
         __syncwarp();
     }
     return sq;
+}
+
+// The helper warp's part of the cavity update of stage S (2..6), the terms that do not need the
+// stage's overlap sums (lane q < 2N, component q): d0 = fma(t, x', -kappa-term x) of the cavity
+// slope with the Kerr-shifted frequency t, and P = a_n + sum_{j < S-1} (h a_{S+1,j}) k^a_j of
+// the next stage's cavity value, in the order of operations of controller_cavity<S> and
+// cavity_stage_value<S+1>, so that warp 0 finishes both with the same roundings.  An FP64 warp
+// instruction occupies a warp for about 64 cycles, while four warps of an SM can run them at
+// once: moving these 2 + S - 1 instructions to a second warp shortens warp 0's stage.
+struct SmallPre {
+    double d0[2 * MAXN], P[2 * MAXN];
+};
+
+template <int S>
+__device__ void small_prepare(const Ctx &c, const Local &L, SmallPre &pre)
+{
+    const int q = threadIdx.x - 32;
+    if (q < 2 * c.nmodes) {
+        const double x = L.as[q], xo = L.as[q ^ 1];
+        double t = L.lc[1][q];
+        if (L.has_kerr) t = fma(L.lc[4][q], fma(x, x, xo * xo), t);
+        double d = L.lc[0][q] * x;
+        d = fma(t, xo, d);
+        pre.d0[q] = d;
+        double v = L.a[q];
+#pragma unroll
+        for (int j = 0; j < S - 1; j++)
+            if (dp_a(S, j) != 0.0) v += L.hw[S][j] * L.ka[j][q];
+        pre.P[q] = v;
+    }
+    __syncwarp();
+    bar_arrive_n(BAR_PRE, 64);
+}
+
+// Warp 0: controller_cavity<S> for S = 2..6 of the single-block integrator (which records no
+// adjoint data and has no checkpoints), finishing the helper's terms: the overlap <m^->_n of
+// component q (Eq. (18)), the cavity slope (Eq. (12), (19), drive and pump), the next stage's
+// cavity value and the feedback coefficients into cf.hrf.
+template <int S>
+__device__ void small_cavity(const Ctx &c, Local &L, Coef &cf, long long sq, const SmallPre &pre)
+{
+    const int N = c.nmodes;
+    const int q = threadIdx.x;
+    __syncwarp();
+    const bool own = q < 2 * N;
+    const double y = own ? (double)sq * L.rs : 0.0;
+    const double yo = __shfl_xor_sync(0xffffffffu, y, 1);
+    double d = 0.0;
+    if (own) {
+        const double x = L.as[q], xo = L.as[q ^ 1];
+        d = pre.d0[q];
+        d = fma(L.lc[2][q], yo, d);
+        d = fma(L.lc[3][q], y, d);
+        if (L.has_split && !L.replay) {
+            d = 0.0;
+        } else {
+            const double ts = L.t + dp_c(S - 1) * L.h;
+            if (c.has_drive) d += drive_term(L.lc[6][q], ts, c.drive_t0, c.drive_inv_sigma);
+            if (c.has_pump) d += pump_term(L.lc[7][q], L.lc[8][q], L.lc[9][q], ts, q, x, xo);
+        }
+        L.mm[q] = y;
+        L.ka[S - 1][q] = d;
+    }
+    __syncwarp();   // every lane has read the stage's cavity values before they are replaced
+    double v = 0.0;
+    if (own) {
+        v = pre.P[q];
+        v += L.hw[S][S - 1] * d;
+        L.as[q] = v;
+    }
+    double p = own ? L.lc[5][q] * v : 0.0;
+    p += __shfl_xor_sync(0xffffffffu, p, 1);
+    if (own && !(q & 1)) cf.hrf[q >> 1] = (float)p;
+    if (q == 0) L.rhs_evals += 1;
+}
+
+// Warp 0, stage S = 2..6 with the helper: as small_control, with the cavity update finished from
+// the helper's terms; afterwards the helper may prepare stage S + 1.
+template <int S>
+__device__ void small_control_pre(const Ctx &c, Local &L, Coef *cfw, SmallRed &R,
+                                  const SmallPre &pre)
+{
+    const int q = threadIdx.x;
+    bar_sync_n(BAR_SUMS, BAR_CW);
+    long long sq = 0;
+    if (q < 2 * c.nmodes) {
+        const long long v = (long long)R.dig[S & 1][q][0] * (1ll << 20) + R.dig[S & 1][q][1];
+        R.dig[S & 1][q][0] = 0;
+        R.dig[S & 1][q][1] = 0;
+        const int d = L.tshift;
+        sq = d >= 0 ? v * (1ll << d) : (v + (1ll << (-d - 1))) >> (-d);
+    }
+    __syncwarp();
+    bar_arrive_n(BAR_FEED, BAR_CW);
+    bar_sync_n(BAR_PRE, 64);
+    small_cavity<S>(c, L, cfw[(S + 1) & 1], sq, pre);
+    __syncwarp();
+    if (S < 6) bar_arrive_n(BAR_HELP, 64);
 }
 
 // Warp 0, before stage 2 of an attempt (its size known, k_1 valid): the cavity value a_2 and
@@ -396,11 +501,12 @@ __global__ void __launch_bounds__(SMALL_NT, 1) small_kernel(SmallArgs A)
     __shared__ Local L;
     __shared__ Coef cfw[2];   // coefficients; feedback of the stages of parity 0 / 1
     __shared__ SmallRed R;
+    __shared__ SmallPre pre;
     __shared__ int s_stop;
     constexpr int NQ = 3 * NS;
     const Ctx &c = A.c;
     const int nm = A.nm, tid = threadIdx.x;
-    const bool ctl = tid < 32;
+    const bool ctl = tid < 32, helper = tid >= 32 && tid < SMALL_W0, worker = tid >= SMALL_W0;
     const size_t V = (size_t)NQ * nm;
     SmallBuf b;
     b.mb0 = sh;
@@ -463,9 +569,9 @@ __global__ void __launch_bounds__(SMALL_NT, 1) small_kernel(SmallArgs A)
     CellReg<NS> r;   // workers' cell in registers (ONE)
     if (ONE) {
         __syncthreads();
-        const int i = tid - 32;
+        const int i = tid - SMALL_W0;
         r.mcur = L.mcur;
-        if (!ctl && i < nm) {
+        if (worker && i < nm) {
             const float *mn = L.mcur ? b.mb1 : b.mb0;
             const float *k1 = b.kk + L.kphys[0] * V;
 #pragma unroll
@@ -497,7 +603,7 @@ __global__ void __launch_bounds__(SMALL_NT, 1) small_kernel(SmallArgs A)
             if (!s_stop && L.k1_valid) small_attempt_setup(L, cfw, c.nmodes);
         }
         __syncthreads();
-        if (ONE && !ctl && L.mcur != r.mcur) {   // the last attempt was accepted: FSAL
+        if (ONE && worker && L.mcur != r.mcur) {   // the last attempt was accepted: FSAL
             r.mcur = L.mcur;
 #pragma unroll
             for (int q = 0; q < NQ; q++) {
@@ -511,25 +617,34 @@ __global__ void __launch_bounds__(SMALL_NT, 1) small_kernel(SmallArgs A)
                 cavity_stage_value<1>(L, cfw[1], tid, tid < 2 * c.nmodes);
                 small_control<1>(c, L, cfw, R);
                 if (L.k1_valid) small_attempt_setup(L, cfw, c.nmodes);
-            } else if (ONE) {
-                small_work_reg<NS, HU, 1>(c, nm, b, L, cfw[1], R, r);
-            } else {
-                small_work<NS, HU, 1>(c, nm, b, L, cfw[1], R);
+            } else if (worker) {
+                if (ONE) small_work_reg<NS, HU, 1>(c, nm, b, L, cfw[1], R, r);
+                else small_work<NS, HU, 1>(c, nm, b, L, cfw[1], R);
             }
             __syncthreads();
         }
         if (ctl) {
-            small_control<2>(c, L, cfw, R);
-            small_control<3>(c, L, cfw, R);
-            small_control<4>(c, L, cfw, R);
-            small_control<5>(c, L, cfw, R);
-            small_control<6>(c, L, cfw, R);
+            small_control_pre<2>(c, L, cfw, R, pre);
+            small_control_pre<3>(c, L, cfw, R, pre);
+            small_control_pre<4>(c, L, cfw, R, pre);
+            small_control_pre<5>(c, L, cfw, R, pre);
+            small_control_pre<6>(c, L, cfw, R, pre);
             // stage 7's cavity slope and cavity error norm while the workers run pass B
             const Team tm{0, 1, nullptr};
             cav7 = controller_cavity<7>(c, tm, L, cfw[1], small_control<7>(c, L, cfw, R));
             __syncwarp();
+        } else if (helper) {   // the cavity terms of stages 2..6 known before their sums
+            small_prepare<2>(c, L, pre);
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                bar_sync_n(BAR_HELP, 64);
+                if (k == 0) small_prepare<3>(c, L, pre);
+                if (k == 1) small_prepare<4>(c, L, pre);
+                if (k == 2) small_prepare<5>(c, L, pre);
+                if (k == 3) small_prepare<6>(c, L, pre);
+            }
         } else if (ONE) {
-            const int i = tid - 32;
+            const int i = tid - SMALL_W0;
             const float c21 = cfw[0].cf[1][0];
             if (i < nm) {
 #pragma unroll
@@ -549,7 +664,7 @@ __global__ void __launch_bounds__(SMALL_NT, 1) small_kernel(SmallArgs A)
                 const float *mn = L.mcur ? b.mb1 : b.mb0;
                 const float *k1 = b.kk + L.kphys[0] * V;
                 const float c21 = cfw[0].cf[1][0];
-                for (int i = tid - 32; i < nm; i += SMALL_WK)
+                for (int i = tid - SMALL_W0; i < nm; i += SMALL_WK)
 #pragma unroll
                     for (int q = 0; q < NQ; q++)
                         b.ms[0][q * nm + i] = fmaf(c21, k1[q * nm + i], mn[q * nm + i]);
@@ -587,8 +702,8 @@ __global__ void __launch_bounds__(SMALL_NT, 1) small_kernel(SmallArgs A)
                 if (!ONE && L.k1_valid) gk1[(size_t)q * c.ncell + si] = k1[q * nm + i];
             }
         }
-        if (ONE && !ctl && tid - 32 < nm && L.k1_valid) {
-            const int i = tid - 32, si = __ldg(A.sidx + i);
+        if (ONE && worker && tid - SMALL_W0 < nm && L.k1_valid) {
+            const int i = tid - SMALL_W0, si = __ldg(A.sidx + i);
             if (idx_ok(c, si, c.ncell, 16))
 #pragma unroll
                 for (int q = 0; q < NQ; q++) gk1[(size_t)q * c.ncell + si] = r.k[0][q];
