@@ -462,17 +462,24 @@ __device__ bool rev_stage(const AdjArgs &A, RevSmem<NS, WX, WY> &sm, RevLocal &L
         L.cw[t] = (S != 1 && S != 7 && t + 1 > S) ? (float)(L.h * dp_a(t, S - 1)) : 0.f;
         L.c1[t] = (float)(L.h * dp_a(t, 0));
     }
+    // FP64 scalar work is spread over warps: a warp holds an FP64 instruction for about 64
+    // cycles, while several warps of an SM run them at once
+    if (tid >= 64 && tid < 64 + N) {   // feedback coefficient of mode n at a_S (Eq. (5), (13))
+        const int n = tid - 64;
+        const double *ra = (S == 1) ? A.a_first : A.rec_a + ((size_t)jj * 7 + (S - 1)) * 4 * N;
+        const double *q = L.mc + MC * n;
+        L.hrf[n] = (float)(c.two_over_gamma * (q[4] * ra[2 * n] - q[5] * ra[2 * n + 1]));
+    }
     __syncthreads();
     if (tid < N) {
         const double *q = L.mc + MC * tid;
-        const double gr = q[2], gi = q[3], gbr = q[4], gbi = q[5];
+        const double gr = q[2], gi = q[3];
         const double wr = L.wa[2 * tid], wi = L.wa[2 * tid + 1];
         // adjoint of <m^->_n from da/dt = ... + i g~ <m^->
         const double mbr = -gi * wr + gr * wi, mbi = -gr * wr - gi * wi;
         const double sc = c.inv_nmag / NS;
         L.ovr[tid] = (float)(sc * mbr);
         L.ovi[tid] = (float)(-sc * mbi);
-        L.hrf[tid] = (float)(c.two_over_gamma * (gbr * L.as[2 * tid] - gbi * L.as[2 * tid + 1]));
     }
     __syncthreads();
     float acc[MAXN + 1];
@@ -489,13 +496,11 @@ __device__ bool rev_stage(const AdjArgs &A, RevSmem<NS, WX, WY> &sm, RevLocal &L
         const double w = q[0], k = q[1], gbr = q[4], gbi = q[5], K = q[6];
         const double wr = L.wa[2 * n], wi = L.wa[2 * n + 1];
         const double ar = L.as[2 * n], ai = L.as[2 * n + 1];
-        const double mr = L.mm[2 * n], mi = L.mm[2 * n + 1];
         // feedback field adjoint through gb~ (the backward coupling), then the cavity equation
         double fr = -k * wr - w * wi + tg * gbr * Sn;
         double fi = w * wr - k * wi - tg * gbi * Sn;
         // self-Kerr -i K |a|^2 a = (K |a|^2 ai, -K |a|^2 ar); its Jacobian terms vanish at K = 0,
         // and FP64 instructions are expensive on this part of the stage
-        const double s2 = ar * ar + ai * ai;
         if (K != 0.0) {
             fr += wr * 2.0 * K * ar * ai - wi * K * (3.0 * ar * ar + ai * ai);
             fi += wr * K * (ar * ar + 3.0 * ai * ai) - wi * 2.0 * K * ar * ai;
@@ -515,27 +520,43 @@ __device__ bool rev_stage(const AdjArgs &A, RevSmem<NS, WX, WY> &sm, RevLocal &L
         }
         L.Fa[S - 1][2 * n] = fr;
         L.Fa[S - 1][2 * n + 1] = fi;
-        const int fb = c.has_gb ? 4 : 0;   // feedback gradients: gb~ if separate, else g~
-        L.gacc[NGRAD * n + 0] += -mi * wr + mr * wi;
-        L.gacc[NGRAD * n + 1] += -mr * wr - mi * wi;
-        L.gacc[NGRAD * n + fb] += tg * ar * Sn;
-        L.gacc[NGRAD * n + fb + 1] -= tg * ai * Sn;
-        L.gacc[NGRAD * n + 2] += -ar * wr - ai * wi;
-        L.gacc[NGRAD * n + 3] += ai * wr - ar * wi;
-        L.gacc[NGRAD * n + 6] += s2 * (wr * ai - wi * ar);
     }
-    if (tid == 32) L.galpha += L.sums[N];
+    // the gradient sums of the stage, beside warp 0's cavity adjoint: g~ (and gb~) on warp 1,
+    // kappa, omega and K on warp 2
+    if ((tid >= 32 && tid < 32 + N) || (tid >= 64 && tid < 64 + N)) {
+        const int n = tid & 31;
+        const double Sn = L.sums[n], tg = c.two_over_gamma;
+        const double wr = L.wa[2 * n], wi = L.wa[2 * n + 1];
+        const double ar = L.as[2 * n], ai = L.as[2 * n + 1];
+        if (tid < 64) {
+            const double mr = L.mm[2 * n], mi = L.mm[2 * n + 1];
+            const int fb = c.has_gb ? 4 : 0;   // feedback gradients: gb~ if separate, else g~
+            L.gacc[NGRAD * n + 0] += -mi * wr + mr * wi;
+            L.gacc[NGRAD * n + 1] += -mr * wr - mi * wi;
+            L.gacc[NGRAD * n + fb] += tg * ar * Sn;
+            L.gacc[NGRAD * n + fb + 1] -= tg * ai * Sn;
+        } else {
+            const double s2 = ar * ar + ai * ai;
+            L.gacc[NGRAD * n + 2] += -ar * wr - ai * wi;
+            L.gacc[NGRAD * n + 3] += ai * wr - ar * wi;
+            L.gacc[NGRAD * n + 6] += s2 * (wr * ai - wi * ar);
+        }
+    }
+    if (tid == 32 + MAXN) L.galpha += L.sums[N];
     __syncthreads();
     if (S == 2 && tid < 2 * N) {
-        double sy = 0.0, sk = 0.0;
+        double sy = 0.0;
 #pragma unroll
-        for (int s = 2; s <= 7; s++) {
-            sy += L.Fa[s - 1][tid];
-            sk += L.h * dp_a(s - 1, 0) * L.Fa[s - 1][tid];
-        }
+        for (int s = 2; s <= 7; s++) sy += L.Fa[s - 1][tid];
         if (A.dL_da) sy += A.dL_da[(size_t)(A.step0 + jj) * 2 * N + tid];
         L.abar[tid] = sy;
-        L.k1a[tid] = sk;
+    }
+    if (S == 2 && tid >= 32 && tid < 32 + 2 * N) {   // warp 1, beside the sum above
+        const int q = tid - 32;
+        double sk = 0.0;
+#pragma unroll
+        for (int s = 2; s <= 7; s++) sk += L.h * dp_a(s - 1, 0) * L.Fa[s - 1][q];
+        L.k1a[q] = sk;
     }
     if (S == 1 && tid < 2 * N) L.abar[tid] += L.Fa[0][tid];
     __syncthreads();
