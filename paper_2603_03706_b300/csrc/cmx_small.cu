@@ -3,8 +3,9 @@
 // A grid of a few hundred to about a thousand magnetic cells (the 280-cell 8^3 sphere of the
 // single-mode Rabi and anticrossing runs of Sec. IV A-B) is integrated by ONE block that keeps,
 // for every magnetic cell, m_n and the new state, the stage value, the seven slopes, the error
-// partial, the mode profiles and a neighbour table in shared memory.  No stage touches global
-// memory except for the step log and the trace.
+// partial, the mode profiles and a neighbour table in shared memory (up to 288 cells, each
+// worker's cell in its registers instead, with only the values neighbours read in shared
+// memory: CellReg).  No stage touches global memory except for the step log and the trace.
 //
 // The block is split by warps.  Warp 0 runs the cavity update and the step-size controller (the
 // engine's own, in FP64: one cavity component per lane), warp 1 (the helper) the part of the
@@ -19,10 +20,10 @@
 //      stage 7 the new state and |e_m|).
 // The cavity slope of stage S needs only the overlap sums of pass A, so warp 0 runs the
 // controller of stage S while the workers run pass B of stage S and pass A of stage S + 1: the
-// FP64 cavity work, which occupies the FP64 pipe for tens of cycles per instruction, is hidden
-// behind the cell passes.  Two named barriers carry the hand-offs (sums ready: workers arrive,
-// warp 0 waits; feedback ready: warp 0 arrives, workers wait); the feedback coefficients and the
-// sums are double-buffered by stage parity.  Only the accept decision after stage 7 (which needs
+// FP64 cavity work, which holds a warp for about 64 cycles per instruction, is hidden behind the
+// cell passes.  Named barriers carry the hand-offs (sums ready: workers arrive, warp 0 waits;
+// feedback ready: warp 0 arrives, workers wait; and between warp 0 and the helper); the
+// feedback coefficients and the sums are double-buffered by stage parity.  Only the accept decision after stage 7 (which needs
 // the error maximum of pass B) is a full block barrier, once per attempt.  The per-cell
 // arithmetic is the tiled kernel's (cell_slope, the same combine order), so the two integrate
 // the same discrete system.
