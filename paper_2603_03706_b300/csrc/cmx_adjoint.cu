@@ -476,10 +476,18 @@ __device__ bool rev_stage(const AdjArgs &A, RevSmem<NS, WX, WY> &sm, RevLocal &L
         const double gr = q[2], gi = q[3];
         const double wr = L.wa[2 * tid], wi = L.wa[2 * tid + 1];
         // adjoint of <m^->_n from da/dt = ... + i g~ <m^->
-        const double mbr = -gi * wr + gr * wi, mbi = -gr * wr - gi * wi;
+        const double mbr = -gi * wr + gr * wi;
         const double sc = c.inv_nmag / NS;
         L.ovr[tid] = (float)(sc * mbr);
-        L.ovi[tid] = (float)(-sc * mbi);
+    }
+    if (tid >= 96 && tid < 96 + N) {   // its imaginary part on warp 3
+        const int n = tid - 96;
+        const double *q = L.mc + MC * n;
+        const double gr = q[2], gi = q[3];
+        const double wr = L.wa[2 * n], wi = L.wa[2 * n + 1];
+        const double mbi = -gr * wr - gi * wi;
+        const double sc = c.inv_nmag / NS;
+        L.ovi[n] = (float)(-sc * mbi);
     }
     __syncthreads();
     float acc[MAXN + 1];
@@ -522,8 +530,8 @@ __device__ bool rev_stage(const AdjArgs &A, RevSmem<NS, WX, WY> &sm, RevLocal &L
         L.Fa[S - 1][2 * n + 1] = fi;
     }
     // the gradient sums of the stage, beside warp 0's cavity adjoint: g~ (and gb~) on warp 1,
-    // kappa, omega and K on warp 2
-    if ((tid >= 32 && tid < 32 + N) || (tid >= 64 && tid < 64 + N)) {
+    // kappa and omega on warp 2, K on warp 3
+    if ((tid >= 32 && tid < 32 + N) || (tid >= 64 && tid < 64 + N) || (tid >= 96 && tid < 96 + N)) {
         const int n = tid & 31;
         const double Sn = L.sums[n], tg = c.two_over_gamma;
         const double wr = L.wa[2 * n], wi = L.wa[2 * n + 1];
@@ -535,10 +543,11 @@ __device__ bool rev_stage(const AdjArgs &A, RevSmem<NS, WX, WY> &sm, RevLocal &L
             L.gacc[NGRAD * n + 1] += -mr * wr - mi * wi;
             L.gacc[NGRAD * n + fb] += tg * ar * Sn;
             L.gacc[NGRAD * n + fb + 1] -= tg * ai * Sn;
-        } else {
-            const double s2 = ar * ar + ai * ai;
+        } else if (tid < 96) {
             L.gacc[NGRAD * n + 2] += -ar * wr - ai * wi;
             L.gacc[NGRAD * n + 3] += ai * wr - ar * wi;
+        } else {
+            const double s2 = ar * ar + ai * ai;
             L.gacc[NGRAD * n + 6] += s2 * (wr * ai - wi * ar);
         }
     }
