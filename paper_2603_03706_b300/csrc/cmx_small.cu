@@ -344,12 +344,10 @@ __device__ __forceinline__ void small_work_reg(const Ctx &c, int nm, const Small
 }
 
 // Warp 0, stage S: wait for the workers' overlap sums, take component q's digits (lane q < 2N),
-// clear them for stage S + 2 and convert the total to the grid units 1 / red_scale, release the
-// workers' pass B (the stage's feedback coefficients were set before), then run the controller
-// of stages 1..6, which forms the next stage's cavity value and feedback coefficients into
-// cfw[(S+1)&1].  Returns the lane's fixed-point sum (the caller runs stage 7's controller).
+// clear them for stage S + 2, convert the total to the grid units 1 / red_scale and release the
+// workers' pass B (the stage's feedback coefficients were set before).
 template <int S>
-__device__ long long small_control(const Ctx &c, Local &L, Coef *cfw, SmallRed &R)
+__device__ __forceinline__ long long small_take_sums(const Ctx &c, const Local &L, SmallRed &R)
 {
     const int q = threadIdx.x;
     bar_sync_n(BAR_SUMS, BAR_CW);
@@ -363,6 +361,16 @@ __device__ long long small_control(const Ctx &c, Local &L, Coef *cfw, SmallRed &
     }
     __syncwarp();
     bar_arrive_n(BAR_FEED, BAR_CW);
+    return sq;
+}
+
+// Warp 0, stage S: the sums (small_take_sums), then the controller of stages 1..6, which forms
+// the next stage's cavity value and feedback coefficients into cfw[(S+1)&1].  Returns the lane's
+// fixed-point sum (the caller runs stage 7's controller).
+template <int S>
+__device__ long long small_control(const Ctx &c, Local &L, Coef *cfw, SmallRed &R)
+{
+    const long long sq = small_take_sums<S>(c, L, R);
     if (S < 7) {
         const Team tm{0, 1, nullptr};
         controller<S>(c, tm, L, cfw[(S + 1) & 1], sq, 0.f);
@@ -451,18 +459,7 @@ template <int S>
 __device__ void small_control_pre(const Ctx &c, Local &L, Coef *cfw, SmallRed &R,
                                   const SmallPre &pre)
 {
-    const int q = threadIdx.x;
-    bar_sync_n(BAR_SUMS, BAR_CW);
-    long long sq = 0;
-    if (q < 2 * c.nmodes) {
-        const long long v = (long long)R.dig[S & 1][q][0] * (1ll << 20) + R.dig[S & 1][q][1];
-        R.dig[S & 1][q][0] = 0;
-        R.dig[S & 1][q][1] = 0;
-        const int d = L.tshift;
-        sq = d >= 0 ? v * (1ll << d) : (v + (1ll << (-d - 1))) >> (-d);
-    }
-    __syncwarp();
-    bar_arrive_n(BAR_FEED, BAR_CW);
+    const long long sq = small_take_sums<S>(c, L, R);
     bar_sync_n(BAR_PRE, 64);
     small_cavity<S>(c, L, cfw[(S + 1) & 1], sq, pre);
     __syncwarp();
