@@ -49,6 +49,7 @@ struct RevLocal {
     double galpha;
     double sums[MAXN + 1];
     double h, t0;                // step size and start time of the step
+    double hA[7][6];             // h a_ij of the step (rows 1..6)
     double pc[3 * MAXN];         // per mode: pump Re P, Im P, frequency
     float cw[7], c1[7];          // h a_{S'S} and h a_{S'1} by S'-1
     float hrf[MAXN], ovr[MAXN], ovi[MAXN];
@@ -453,7 +454,7 @@ __device__ bool rev_stage(const AdjArgs &A, RevSmem<NS, WX, WY> &sm, RevLocal &L
         } else {
 #pragma unroll
             for (int t = S + 1; t <= 7; t++)
-                if (dp_a(t - 1, S - 1) != 0.0) w += L.h * dp_a(t - 1, S - 1) * L.Fa[t - 1][tid];
+                if (dp_a(t - 1, S - 1) != 0.0) w += L.hA[t - 1][S - 1] * L.Fa[t - 1][tid];
         }
         L.wa[tid] = w;
     }
@@ -564,7 +565,7 @@ __device__ bool rev_stage(const AdjArgs &A, RevSmem<NS, WX, WY> &sm, RevLocal &L
         const int q = tid - 32;
         double sk = 0.0;
 #pragma unroll
-        for (int s = 2; s <= 7; s++) sk += L.h * dp_a(s - 1, 0) * L.Fa[s - 1][q];
+        for (int s = 2; s <= 7; s++) sk += L.hA[s - 1][0] * L.Fa[s - 1][q];
         L.k1a[q] = sk;
     }
     if (S == 1 && tid < 2 * N) L.abar[tid] += L.Fa[0][tid];
@@ -628,6 +629,16 @@ __global__ void __launch_bounds__(WX *WY, NS == 1 ? 2 : 1) rev_kernel(AdjArgs A)
         if (tid == 0) {
             L.h = A.dts[jj];
             L.t0 = A.rec_t ? A.rec_t[jj] : 0.0;
+        }
+        if (tid >= 32 && tid < 32 + 36) {   // the step's weights h a_ij, once for its six stages
+            const int q = tid - 32;
+            double a = 0.0;
+#pragma unroll
+            for (int i = 1; i < 7; i++)
+#pragma unroll
+                for (int j = 0; j < 6; j++)
+                    if (q == (i - 1) * 6 + j) a = dp_a(i, j);
+            L.hA[1 + q / 6][q % 6] = A.dts[jj] * a;
         }
         __syncthreads();
         ok = rev_stage<NS, WX, WY, HU, 7>(A, sm, L, jj) && rev_stage<NS, WX, WY, HU, 6>(A, sm, L, jj) &&
